@@ -1,0 +1,332 @@
+"""Benchmark: GLUP/s of the stencil sweeps on one GB300 (and N replicas).
+
+Default workload (one "step"): the 7-point variable-coefficient Jacobi
+sweep (paper Fig. 1c), FP64, 512^3 interior + radius-1 zero halo, 7 arrays
+~ U[0, 0.14], u0 ~ U[-1, 1], T = 64 time steps through stencil_forward.
+value = lattice updates per second (GLUP/s) over all ranks, inputs resident
+in HBM; e2e = the same with the state and coefficients copied from pinned
+host memory and the final field read back inside the timed region.
+
+Further lines of the same run (key "variants"): the same sweep in FP32
+(temporally blocked where the library blocks it), the 25-point constant
+and variable wave sweeps (FP64 and FP32), and forward+adjoint.
+
+Timing: CUDA events on the launching stream, a barrier and
+torch.cuda.synchronize() on both sides, max over ranks.  Every input is far
+larger than the 129 MB L2 (no flush needed).  nvidia-smi clocks are
+sampled during the timed region.
+
+--impl reference times the FP64 CPU oracle (the reference arm) on the host
+cores on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+METRIC = "GLUP/s"
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=5)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    p.add_argument("--n", type=int, default=512, help="interior size per axis")
+    p.add_argument("--T", type=int, default=64, help="time steps per step")
+    p.add_argument("--no-variants", action="store_true")
+    p.add_argument("--no-cpu", action="store_true")
+    return p.parse_args()
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+# --------------------------------------------------------------- reference arm
+def cpu_oracle_rate(kind, wk, T_sample, threads):
+    import oracle
+    t0 = time.perf_counter()
+    oracle.forward(kind, wk.u_prev, wk.u, wk.w, wk.W, T_sample, threads=threads)
+    dt = time.perf_counter() - t0
+    n = wk.n[0] * wk.n[1] * wk.n[2]
+    return n * T_sample / dt / 1e9, dt
+
+
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return
+    import oracle
+    from paper_1410_3060_gb300 import workloads as wl
+    oracle.build()
+    threads = oracle.oracle.default_threads()
+    wk = wl.j7_var(args.n, args.T, seed=0)
+    T_sample = 1
+    for _ in range(args.warmup):
+        cpu_oracle_rate(wl.J7_VAR, wk, T_sample, threads)
+    rates = [cpu_oracle_rate(wl.J7_VAR, wk, T_sample, threads)[0] for _ in range(args.steps)]
+    v = statistics.median(rates)
+    n3 = args.n ** 3
+    line = {
+        "impl": "reference", "metric": METRIC, "value": v, "unit": METRIC, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": n3 * T_sample / (v * 1e9) * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": f"j7_var_{args.n}^3_fp64", "sample": f"{T_sample} time step of the {args.n}^3 grid per step"},
+        "cpu_baseline": {"value": v, "unit": METRIC, "cores": threads, "kind": "oracle",
+                         "sample": f"{T_sample} step of the {args.n}^3 7-point variable-coefficient sweep, FP64, plain C loops"},
+        "e2e": {"value": v, "unit": METRIC, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# --------------------------------------------------------------- clocks
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index):
+        self.dev = device_index
+        self.proc = None
+        self.out = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits", "-lms", "200",
+                 "-i", str(self.dev)], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (FileNotFoundError, OSError):
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            time.sleep(0.25)
+            self.proc.terminate()
+            try:
+                self.out, _ = self.proc.communicate(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+                self.out, _ = self.proc.communicate()
+
+    def summary(self):
+        if not self.out:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"]}
+        sm, smax, reasons, power = [], [], set(), []
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.out.strip().splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+                power.append(float(f[3]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, f[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"]}
+        # samples under load: top half of the clock samples by power
+        ranked = sorted(zip(power, sm), reverse=True)
+        load = [s for _, s in ranked[:max(1, len(ranked) // 2)]]
+        return {"sm_mhz": statistics.median(load), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm), "power_w_max": max(power)}
+
+
+# --------------------------------------------------------------- ours
+class Timer:
+    def __init__(self, torch, stream):
+        self.torch, self.stream = torch, stream
+
+    def __enter__(self):
+        self.e0 = self.torch.cuda.Event(enable_timing=True)
+        self.e1 = self.torch.cuda.Event(enable_timing=True)
+        self.e0.record(self.stream)
+        return self
+
+    def __exit__(self, *exc):
+        self.e1.record(self.stream)
+        self.e1.synchronize()
+        self.ms = self.e0.elapsed_time(self.e1)
+
+
+def barrier(torch, ws):
+    torch.cuda.synchronize()
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+    torch.cuda.synchronize()
+
+
+def max_over_ranks(torch, ws, v):
+    if ws == 1:
+        return v
+    import torch.distributed as dist
+    t = torch.tensor([v], device="cuda", dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def forward_case(torch, st, wl, kind, n, T, dtype, steps, warmup, ws, stream, time_block=None, e2e=False,
+                 wk=None):
+    """Time `steps` calls of stencil_forward(T) on the workload; returns dict."""
+    tdt = torch.float64 if dtype == st.F64 else torch.float32
+    if wk is None:
+        wk = wl.make(kind, n, T, seed=0) if kind not in (wl.J7_VAR,) else wl.j7_var(n, T, seed=0)
+    plan = st.Plan(kind, n, n, n, dtype)
+    if time_block is not None:
+        plan.set(st.OPT_TIME_BLOCK, time_block)
+    b = plan.get(st.OPT_TIME_BLOCK)
+    up = torch.from_numpy(wk.u_prev).to("cuda", tdt)
+    u = torch.from_numpy(wk.u).to("cuda", tdt)
+    W = torch.from_numpy(wk.W).to("cuda", tdt) if wk.W is not None else None
+    for _ in range(warmup):
+        plan.forward(up, u, wk.w, W, T)
+    barrier(torch, ws)
+    with Timer(torch, stream) as tm:
+        for _ in range(steps):
+            plan.forward(up, u, wk.w, W, T)
+    barrier(torch, ws)
+    ms = max_over_ranks(torch, ws, tm.ms)
+    lups = float(n) ** 3 * T
+    passes = [o for o in st.schedule(kind, T, b) if o[0] == 0]
+    res = {"kind": wl.KIND_NAMES[kind], "n": n, "T": T, "dtype": "f64" if dtype == st.F64 else "f32",
+           "time_block": b, "ms_per_step": ms / steps, "glups": lups * steps * ws / (ms * 1e-3) / 1e9,
+           "launches_per_step": len(passes), "ms_per_launch": ms / steps / len(passes)}
+    if e2e:
+        hp = torch.from_numpy(wk.u_prev).to(tdt).pin_memory()
+        hu = torch.from_numpy(wk.u).to(tdt).pin_memory()
+        hW = torch.from_numpy(wk.W).to(tdt).pin_memory() if wk.W is not None else None
+        hout = torch.empty_like(hu).pin_memory()
+        h2d = hp.numel() * hp.element_size() * 2 + (hW.numel() * hW.element_size() if hW is not None else 0)
+        d2h = hout.numel() * hout.element_size()
+        barrier(torch, ws)
+        with Timer(torch, stream) as te:
+            for _ in range(steps):
+                up.copy_(hp, non_blocking=True)
+                u.copy_(hu, non_blocking=True)
+                if hW is not None:
+                    W.copy_(hW, non_blocking=True)
+                plan.forward(up, u, wk.w, W, T)
+                hout.copy_(u, non_blocking=True)
+        barrier(torch, ws)
+        ms_e = max_over_ranks(torch, ws, te.ms)
+        res["e2e"] = {"value": lups * steps * ws / (ms_e * 1e-3) / 1e9, "unit": METRIC,
+                      "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
+    plan.close()
+    del up, u, W
+    torch.cuda.empty_cache()
+    return res, wk
+
+
+def run_ours(args):
+    import torch
+    ws, rank, local = dist_env()
+    if ws > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    else:
+        torch.cuda.set_device(0)
+    from paper_1410_3060_gb300 import perfmodel as pm, stencil as st, workloads as wl
+    st.lib()
+    stream = torch.cuda.current_stream()
+    n, T = args.n, args.T
+
+    peak_f64, clk = st.fma_peak(st.F64)
+    peak_f32, _ = st.fma_peak(st.F32)
+    peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
+        os.path.join(ROOT, "MEASURED_PEAKS.json")) else {}
+    hbm_peak = peaks.get("hbm_gbs", 6800.0)
+
+    # main line: 7-point variable coefficients, FP64, 512^3, T = 64
+    dev_index = torch.cuda.current_device()
+    sampler = ClockSampler(dev_index)
+    wk = wl.j7_var(n, T, seed=0)
+    with sampler:
+        main, _ = forward_case(torch, st, wl, wl.J7_VAR, n, T, st.F64, args.steps, args.warmup, ws, stream,
+                               e2e=True, wk=wk)
+    clocks = sampler.summary()
+
+    flops_launch = pm.FLOPS_PER_LUP[wl.J7_VAR] * float(n) ** 3
+    bytes_launch = pm.gpu_bytes_per_lup(wl.J7_VAR, 8) * float(n) ** 3
+    t_launch = main["ms_per_launch"] * 1e-3
+    achieved = flops_launch / t_launch / 1e12
+    roofline = {"bound": "alu", "achieved": achieved, "peak": peak_f64 / 1e12, "unit": "TFLOP/s",
+                "frac": achieved / (peak_f64 / 1e12), "traffic": None,
+                "peak_source": "FP64 FMA chains measured in this run (stencil_fma_peak)",
+                "hbm_view": {"achieved_gbs": bytes_launch / t_launch / 1e9, "peak_gbs": hbm_peak,
+                             "frac": bytes_launch / t_launch / 1e9 / hbm_peak},
+                "kernel": "plain_sweep_kernel<double, J7_VAR>"}
+
+    variants = []
+    if not args.no_variants:
+        for kind, dtype, nn, TT in ((wl.J7_VAR, st.F32, n, T),
+                                    (wl.W25_CONST, st.F64, n, 100), (wl.W25_CONST, st.F32, n, 100),
+                                    (wl.W25_VAR, st.F64, n, T), (wl.W25_VAR, st.F32, n, T)):
+            wkv = wk if kind == wl.J7_VAR else None
+            r, _ = forward_case(torch, st, wl, kind, nn, TT, dtype, max(1, args.steps // 2), 1, ws, stream,
+                                wk=wkv)
+            word = 8 if dtype == st.F64 else 4
+            r["hbm_gbs_algorithmic"] = pm.gpu_bytes_per_lup(kind, word) * r["glups"] * 1e9 / r["time_block"] / 1e9 / ws
+            variants.append(r)
+
+    cpu = None
+    if rank == 0 and not args.no_cpu:
+        import oracle
+        oracle.build()
+        threads = oracle.oracle.default_threads()
+        rate, dt = cpu_oracle_rate(wl.J7_VAR, wk, 1, threads)
+        cpu = {"value": rate, "unit": METRIC, "cores": threads, "kind": "oracle",
+               "sample": f"1 time step of the {n}^3 7-point variable-coefficient FP64 sweep ({dt:.1f} s)"}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": main["glups"], "unit": METRIC, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": main["ms_per_step"], "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": f"j7_var_{n}^3_T{T}_fp64", "kind": "7-point variable coefficients (Fig. 1c)",
+                       "n": n, "T": T, "time_block": main["time_block"], "parallelism": f"replicas{ws}",
+                       "l2": "inputs larger than L2 (1.1 GB field + 7.6 GB coefficients)"},
+            "e2e": main["e2e"], "gpu_launches": main["launches_per_step"] * args.steps,
+            "roofline": roofline, "clocks": clocks, "cpu_baseline": cpu,
+            "peaks_measured": {"fp64_tflops": peak_f64 / 1e12, "fp32_tflops": peak_f32 / 1e12,
+                               "sm_clock_mhz_probe": clk / 1e6, "hbm_gbs": hbm_peak},
+            "variants": variants,
+        }
+        print(json.dumps(line), flush=True)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,195 @@
+/*
+ * stencil.h -- C ABI of libstencil.so: temporally blocked 3D star-stencil
+ * sweeps on NVIDIA GB300 (sm_103a).
+ *
+ * The operations follow the problem statement of Malas et al., "Multicore-
+ * optimized wavefront diamond blocking for optimizing stencil updates"
+ * (arXiv 1410.3060): a lattice Omega = {1..Nx} x {1..Ny} x {1..Nz}, x the
+ * leading (unit-stride) dimension, stored as Omega[t][z][y][x] with two
+ * time copies, swept T times by a Jacobi-style star-stencil update
+ * (Sect. 3.1, Fig. 1).
+ *
+ * Layout (all arrays): halo-padded, dense, C order, extents
+ * (nz+2R, ny+2R, nx+2R), x fastest.  The interior is padded index
+ * R..R+n-1 in every axis; the halo of width R holds zero Dirichlet values,
+ * must be zero on entry and is never written.  Coefficient stacks are
+ * [k][nz+2R][ny+2R][nx+2R] in the plan's dtype; their halo values are not
+ * read.  Device pointers must be 16-byte aligned.  "Interior plane z" below
+ * means zero-based interior index z, padded plane z+R.
+ *
+ * Ownership and streams: the caller owns every array passed in.  A plan
+ * owns only device scratch that it allocates in stencil_plan (and grows in
+ * stencil_plan_set); stencil_forward / stencil_adjoint / stencil_misfit
+ * allocate nothing.  Calls enqueue work on the given stream (a
+ * cudaStream_t passed as void*, NULL = legacy default stream) and return
+ * without synchronising.  One plan must not be used by two calls that
+ * overlap in time (its scratch is shared).
+ *
+ * Errors: every int-returning call returns STENCIL_OK (0) or a negative
+ * status; stencil_strerror names it.  STENCIL_ECUDA records the CUDA error,
+ * readable through stencil_last_cuda_error.  Invalid arguments are
+ * rejected on the host before any work is enqueued.
+ */
+#ifndef STENCIL_H
+#define STENCIL_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Operator kinds (paper Fig. 1).  Axis a: 0 = x, 1 = y, 2 = z.
+ *  J7_CONST   Fig. 1b, radius 1:  u' = w1 u + w2 (x pair + y pair + z pair)
+ *  J7_VAR     Fig. 1c, radius 1, 7 arrays at the updated point:
+ *             u' = W0 u + W1 u[x-1] + W2 u[x+1] + W3 u[y-1] + W4 u[y+1]
+ *                  + W5 u[z-1] + W6 u[z+1]
+ *  W25_CONST  Fig. 1e with scalar alpha, radius 4, second order in time:
+ *             u^{t+1} = 2u^t - u^{t-1} + alpha [w0 u^t + sum_r w_r (pairs
+ *             at distance r along x, y and z)]; w0 is the 3D centre weight
+ *  W25_VAR    radius 4, second order in time, 13 arrays with the Fig. 1d
+ *             structure (index 0 centre, 3(r-1)+a+1 for the pair at
+ *             distance r on axis a):
+ *             u^{t+1} = 2u^t - u^{t-1} + W0 u^t + sum_{r,a} W_{3(r-1)+a+1} (pair)
+ *  J25_VAR    Fig. 1d, radius 4, first order in time, 13 arrays:
+ *             u' = W0 u + sum_{r,a} W_{3(r-1)+a+1} (pair)
+ *  W25_ALPHA  Fig. 1e, radius 4, second order in time, domain-sized alpha:
+ *             one array (alpha) and scalar weights w0..w4.                  */
+enum stencil_kind {
+    STENCIL_J7_CONST = 1,
+    STENCIL_J7_VAR = 2,
+    STENCIL_W25_CONST = 3,
+    STENCIL_W25_VAR = 4,
+    STENCIL_J25_VAR = 5,
+    STENCIL_W25_ALPHA = 6
+};
+
+/* Storage and arithmetic precision of fields and coefficients. */
+enum stencil_dtype { STENCIL_F64 = 0, STENCIL_F32 = 1 };
+
+enum stencil_status {
+    STENCIL_OK = 0,
+    STENCIL_EINVAL = -1,       /* bad argument: see stencil_strerror        */
+    STENCIL_EUNSUPPORTED = -2, /* valid request this build does not serve   */
+    STENCIL_ENOMEM = -3,       /* device scratch allocation failed          */
+    STENCIL_ECUDA = -4         /* a CUDA call failed (stencil_last_cuda_error) */
+};
+
+/* Plan options (stencil_plan_set / stencil_plan_get). */
+enum stencil_option {
+    /* Time levels applied per pass over the lattice (the temporal block
+       depth b).  0 = library default for the kind and dtype, 1 = plain
+       one-step-per-sweep kernel. */
+    STENCIL_OPT_TIME_BLOCK = 1,
+    /* Tiling scheme of a blocked pass: 0 = default, 1 = overlapped tiles in
+       x and y, 2 = diamond (split) tiles in y with overlapped x. */
+    STENCIL_OPT_SCHEME = 2,
+    /* Read-only: bytes of device scratch the plan holds. */
+    STENCIL_OPT_SCRATCH_BYTES = 3
+};
+
+typedef struct stencil_plan_s *stencil_plan_t;
+
+/* Coefficients of one call.
+ *  w:      host array of nw FP64 scalars, for the kinds that take them:
+ *          J7_CONST {w1, w2}; W25_CONST {alpha, w0, w1, w2, w3, w4};
+ *          W25_ALPHA {w0, w1, w2, w3, w4}; NULL / 0 otherwise.  Copied at
+ *          the call; need not outlive it.
+ *  arrays: device coefficient stack in the plan's dtype, k arrays of the
+ *          padded extent: J7_VAR k = 7, W25_VAR and J25_VAR k = 13,
+ *          W25_ALPHA k = 1 (alpha); NULL for the constant kinds.  For the
+ *          adjoint its halo entries must be finite.                        */
+typedef struct {
+    const double *w;
+    int32_t nw;
+    const void *arrays;
+} stencil_coeffs_t;
+
+/* Create a plan for one operator on an nx x ny x nz interior
+ * (Sect. 3.1 problem statement).  radius must equal the kind's radius (1
+ * or 4); every n must be >= 1.  Allocates the plan's device scratch on the
+ * current device.  Returns EINVAL for a bad kind/radius/dtype/size, ENOMEM
+ * if scratch cannot be allocated. */
+int stencil_plan(stencil_plan_t *plan, int kind, int64_t nx, int64_t ny, int64_t nz,
+                 int radius, int dtype);
+
+/* Set / read a plan option (enum stencil_option).  Setting may reallocate
+ * the plan's scratch; it must not race with work enqueued on the plan. */
+int stencil_plan_set(stencil_plan_t plan, int option, int64_t value);
+int stencil_plan_get(stencil_plan_t plan, int option, int64_t *value);
+
+/* Release the plan and its scratch (synchronises the device first). */
+void stencil_plan_destroy(stencil_plan_t plan);
+
+/* Advance the state T time steps (Sect. 3.1: the sweep repeated T times;
+ * temporally blocked per Sect. 4: several time levels per pass).
+ *  u_prev, u: device state pair.  On entry (u_prev, u) = (u^{-1}, u^0);
+ *             first-order kinds ignore u_prev's entry contents.  On return
+ *             (u_prev, u) = (u^{T-1}, u^T).  T = 0 leaves both untouched.
+ *             u_prev and u must be distinct, non-overlapping arrays.
+ *  trace:     NULL, or device [T][ny][nx] (plan dtype) receiving
+ *             trace[t] = u^{t+1} on interior plane rcv_z, 0 <= rcv_z < nz.
+ * Results match the naive sweep of Fig. 1 up to rounding order. */
+int stencil_forward(stencil_plan_t plan, void *u_prev, void *u, const stencil_coeffs_t *coeffs,
+                    int64_t T, void *stream, void *trace, int64_t rcv_z);
+
+/* T steps of the adjoint (transposed) sweep, backward in time, for a loss
+ * L = sum_n l_n(u^n) with explicit partials g^n = P^T r^n injected on
+ * receiver plane rcv_z.  With A the spatial operator and A^T its transpose
+ * ((A^T y)(q) = sum_k A_k(q - o_k) y(q - o_k) over interior source points):
+ *   first-order kinds:  lam^n = g^n + A^T lam^{n+1}
+ *   second-order kinds: lam^n = g^n + 2 lam^{n+1} + A^T lam^{n+1} - lam^{n+2}
+ *  lam_next, lam: device pair.  On entry (lam^{m+1}, lam^m), g^m already in
+ *             lam^m; on return (lam^{m-T+1}, lam^{m-T}).
+ *  fwd_states: host array of T device pointers, fwd_states[i] = u^{m-T+i};
+ *             required when grad is non-NULL, otherwise ignored.
+ *  residual:  NULL, or device [T][ny][nx] (plan dtype), residual[i] = r^{m-T+i}
+ *             added to lam^{m-T+i} on plane rcv_z.
+ *  grad:      NULL, or device FP64 [k][nz+2R][ny+2R][nx+2R] (variable-
+ *             coefficient kinds only): accumulates, interior entries only,
+ *             dL/dA_k(x) += sum_n lam^{n+1}(x) d(A u^n)(x)/dA_k(x).
+ * The adjoint of the constant-coefficient kinds returns EUNSUPPORTED when
+ * grad is non-NULL. */
+int stencil_adjoint(stencil_plan_t plan, void *lam_next, void *lam, const stencil_coeffs_t *coeffs,
+                    int64_t T, void *stream, const void *const *fwd_states, const void *residual,
+                    int64_t rcv_z, double *grad);
+
+/* Receiver misfit of T traces: residual = trace - d (plan dtype, may alias
+ * neither input unless equal to trace), and *loss (device FP64) =
+ * 0.5 * sum (trace - d)^2 accumulated in FP64 in a fixed order
+ * (deterministic).  trace, d, residual: device [T][ny][nx]. */
+int stencil_misfit(stencil_plan_t plan, const void *trace, const void *d, int64_t T, void *residual,
+                   double *loss, void *stream);
+
+/* Host-only: the program of passes and copies that stencil_forward (and,
+ * with the same rules, stencil_adjoint) runs for T steps of `kind` with
+ * temporal block depth b (b >= 1; 1 = plain sweeps).  Each op is 6 int32:
+ *   {op, levels, in_prev, in_cur, out_prev, out_cur}
+ * op 0 = pass over the lattice applying `levels` time levels, op 1 = copy
+ * of buffer in_cur to out_cur.  Buffer ids: 0 = the caller's u_prev,
+ * 1 = the caller's u, 2 and 3 = plan scratch fields, -1 = not used.  A pass
+ * reads (in_prev, in_cur) = (u^{t-1}, u^t) and writes u^{t+levels} to
+ * out_cur and, when out_prev >= 0, u^{t+levels-1} to out_prev; out_cur ==
+ * in_prev marks an in-place second-order update.  Writes at most max_ops
+ * ops and the total count to *n_ops.  Performs no CUDA call. */
+int stencil_schedule(int kind, int64_t T, int b, int32_t *ops, int64_t max_ops, int64_t *n_ops);
+
+/* Measure the device's FP64 (dtype STENCIL_F64) or FP32 fused multiply-add
+ * throughput with independent FMA chains on every SM: *flops = flops per
+ * second (FMA = 2), *sm_clock_hz = SM clock seen by the kernel's cycle
+ * counter.  Synchronises the stream; used as the roofline denominator of
+ * ALU-bound kernels. */
+int stencil_fma_peak(int dtype, void *stream, double *flops, double *sm_clock_hz);
+
+/* Name of a status code. */
+const char *stencil_strerror(int status);
+
+/* The last CUDA error code recorded by a call that returned STENCIL_ECUDA
+ * in this thread (cudaError_t as int), or 0. */
+int stencil_last_cuda_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* STENCIL_H */

@@ -1,0 +1,127 @@
+// aux.cu -- coefficient-gradient accumulation and the receiver misfit.
+//
+// Gradient (adjoint of the coefficient dependence of the update, for the
+// variable-coefficient kinds): for every interior point x and every step n
+// of a batch, grad_k(x) += lam^{n+1}(x) * d(A u^n)(x)/dA_k(x), where the
+// derivative is the field value multiplying A_k in the update:
+//   J7_VAR  (Fig. 1c): u^n(x + o_k), o_k in {0, -x, +x, -y, +y, -z, +z}
+//   W25_VAR / J25_VAR (Fig. 1d structure): u^n(x) for k = 0, the pair
+//           u^n(x + r e_a) + u^n(x - r e_a) for k = 3(r-1)+a+1
+//   W25_ALPHA (Fig. 1e): w0 u^n(x) + sum_r w_r (pairs along x, y, z)
+// The batch sum is kept in FP64 registers and added to the FP64 gradient
+// arrays once per batch.
+#include "plain.cuh"
+
+namespace stc {
+
+template <typename T, int KIND>
+__global__ void __launch_bounds__(256) grad_kernel(const GradArgs<T> a) {
+    constexpr int R = KindTraits<KIND>::R;
+    constexpr int NA = KindTraits<KIND>::NARR;
+    const Geom g = a.g;
+    const int x = blockIdx.x * 32 + threadIdx.x;
+    const int y = blockIdx.y * 8 + threadIdx.y;
+    const int z = blockIdx.z;
+    if (x >= g.nx || y >= g.ny) return;
+    const int64_t idx = (int64_t)(z + R) * g.sz + (int64_t)(y + R) * g.sy + (x + R);
+    double acc[NA];
+#pragma unroll
+    for (int k = 0; k < NA; ++k) acc[k] = 0.0;
+    for (int s = 0; s < a.nsteps; ++s) {
+        const T *u = a.u[s] + idx;
+        const double l = (double)a.lam[s][idx];
+        if constexpr (KIND == J7_VAR) {
+            const int64_t o[7] = {0, -1, 1, -g.sy, g.sy, -g.sz, g.sz};
+#pragma unroll
+            for (int k = 0; k < 7; ++k) acc[k] = fma(l, (double)u[o[k]], acc[k]);
+        } else if constexpr (KIND == W25_VAR || KIND == J25_VAR) {
+            acc[0] = fma(l, (double)u[0], acc[0]);
+#pragma unroll
+            for (int r = 1; r <= 4; ++r) {
+                const int64_t st[3] = {1, g.sy, g.sz};
+#pragma unroll
+                for (int ax = 0; ax < 3; ++ax) {
+                    const int64_t d = r * st[ax];
+                    acc[3 * (r - 1) + ax + 1] = fma(l, (double)u[-d] + (double)u[d], acc[3 * (r - 1) + ax + 1]);
+                }
+            }
+        } else {  // W25_ALPHA
+            double sum = a.s.c[0] * (double)u[0];
+#pragma unroll
+            for (int r = 1; r <= 4; ++r) {
+                const int64_t sy = g.sy, sz = g.sz;
+                const double pr = ((double)u[-r] + (double)u[r]) + ((double)u[-r * sy] + (double)u[r * sy]) +
+                                  ((double)u[-r * sz] + (double)u[r * sz]);
+                sum = fma(a.s.c[r], pr, sum);
+            }
+            acc[0] = fma(l, sum, acc[0]);
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < NA; ++k) a.grad[(int64_t)k * g.nfield + idx] += acc[k];
+}
+
+template <typename T>
+cudaError_t launch_grad(int kind, const GradArgs<T> &a, cudaStream_t st) {
+    dim3 block(32, 8, 1), grid((a.g.nx + 31) / 32, (a.g.ny + 7) / 8, a.g.nz);
+    switch (kind) {
+    case J7_VAR: grad_kernel<T, J7_VAR><<<grid, block, 0, st>>>(a); break;
+    case W25_VAR: grad_kernel<T, W25_VAR><<<grid, block, 0, st>>>(a); break;
+    case J25_VAR: grad_kernel<T, J25_VAR><<<grid, block, 0, st>>>(a); break;
+    case W25_ALPHA: grad_kernel<T, W25_ALPHA><<<grid, block, 0, st>>>(a); break;
+    default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+// ---- misfit: residual = trace - d, partial sums of residual^2 per block in
+// a grid-stride order that depends only on n, then one block sums the
+// partials in index order.
+template <typename T>
+__global__ void __launch_bounds__(256) misfit_partial_kernel(const T *trace, const T *d, T *res, int64_t n,
+                                                             double *partials) {
+    double s = 0.0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const T r = trace[i] - d[i];
+        res[i] = r;
+        s = fma((double)r, (double)r, s);
+    }
+    __shared__ double sh[256];
+    sh[threadIdx.x] = s;
+    __syncthreads();
+    for (int w = 128; w > 0; w >>= 1) {
+        if (threadIdx.x < w) sh[threadIdx.x] += sh[threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) partials[blockIdx.x] = sh[0];
+}
+
+__global__ void __launch_bounds__(256) misfit_final_kernel(const double *partials, int np, double *loss) {
+    __shared__ double sh[256];
+    double s = 0.0;
+    for (int i = threadIdx.x; i < np; i += 256) s += partials[i];
+    sh[threadIdx.x] = s;
+    __syncthreads();
+    for (int w = 128; w > 0; w >>= 1) {
+        if (threadIdx.x < w) sh[threadIdx.x] += sh[threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *loss = 0.5 * sh[0];
+}
+
+template <typename T>
+cudaError_t launch_misfit(const T *trace, const T *d, T *residual, int64_t n, double *partials, int npartials,
+                          double *loss, cudaStream_t st) {
+    misfit_partial_kernel<T><<<npartials, 256, 0, st>>>(trace, d, residual, n, partials);
+    misfit_final_kernel<<<1, 256, 0, st>>>(partials, npartials, loss);
+    return cudaGetLastError();
+}
+
+template cudaError_t launch_grad<float>(int, const GradArgs<float> &, cudaStream_t);
+template cudaError_t launch_grad<double>(int, const GradArgs<double> &, cudaStream_t);
+template cudaError_t launch_misfit<float>(const float *, const float *, float *, int64_t, double *, int, double *,
+                                          cudaStream_t);
+template cudaError_t launch_misfit<double>(const double *, const double *, double *, int64_t, double *, int,
+                                           double *, cudaStream_t);
+
+}  // namespace stc

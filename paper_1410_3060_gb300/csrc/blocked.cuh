@@ -1,0 +1,27 @@
+// blocked.cuh -- temporally blocked passes (several time levels per sweep).
+#pragma once
+#include "common.cuh"
+
+namespace stc {
+
+template <typename T>
+struct BlockedArgs {
+    const T *u_prev;     // level t-1 (second-order kinds)
+    const T *u;          // level t
+    T *out_prev;         // receives level t+levels-1, or nullptr
+    T *out;              // receives level t+levels
+    const T *W;          // coefficient stack
+    T *trace;            // trace rows of levels t+1..t+levels ([levels][ny][nx]) or nullptr
+    Scalars s;
+    Geom g;
+    int rcv_z;
+    int levels;
+    int zchunk;
+};
+
+bool blocked_supported(int kind, int dtype, int levels);
+int blocked_default_levels(int kind, int dtype);
+template <typename T>
+cudaError_t launch_blocked(int kind, const BlockedArgs<T> &a, cudaStream_t st, int num_sms, int scheme);
+
+}  // namespace stc

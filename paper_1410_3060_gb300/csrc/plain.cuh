@@ -1,0 +1,34 @@
+// plain.cuh -- launchers of the kernels in plain.cu, aux.cu and blocked.cu.
+#pragma once
+#include "common.cuh"
+
+namespace stc {
+
+// One plain sweep (one time level), forward or adjoint.
+template <typename T>
+cudaError_t launch_plain(int kind, bool adjoint, const SweepArgs<T> &a, cudaStream_t st, int num_sms);
+
+// Coefficient-gradient accumulation for `nsteps` adjoint steps:
+// grad_k(x) += sum_s lam[s](x) * d(A u[s])(x)/dA_k(x) (FP64 accumulators).
+constexpr int GRAD_MAX_STEPS = 16;
+template <typename T>
+struct GradArgs {
+    const T *u[GRAD_MAX_STEPS];     // u^n of each step (padded)
+    const T *lam[GRAD_MAX_STEPS];   // lam^{n+1} of each step (padded)
+    double *grad;                   // [k][pz][py][px]
+    Scalars s;                      // W25_ALPHA weights w0..w4
+    Geom g;
+    int nsteps;
+};
+template <typename T>
+cudaError_t launch_grad(int kind, const GradArgs<T> &a, cudaStream_t st);
+
+// residual = trace - d and loss = 0.5 sum residual^2 (FP64, fixed order).
+template <typename T>
+cudaError_t launch_misfit(const T *trace, const T *d, T *residual, int64_t n, double *partials,
+                          int npartials, double *loss, cudaStream_t st);
+
+// FP64 / FP32 FMA throughput probe.
+cudaError_t run_fma_peak(int dtype, cudaStream_t st, double *flops, double *clock_hz);
+
+}  // namespace stc

@@ -1,0 +1,97 @@
+"""Host-side checks of the C ABI (no GPU needed): the library loads, exports
+every function include/stencil.h declares, rejects bad arguments without a
+device, and its time-loop program leaves (u^{T-1}, u^T) in (u_prev, u)."""
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def st():
+    from paper_1410_3060_gb300 import build, stencil
+    build.build()
+    return stencil
+
+
+def declared_functions():
+    src = open(os.path.join(ROOT, "include", "stencil.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(stencil_[a-z_0-9]+)\s*\(", src)))
+
+
+def test_header_and_binding_agree(st):
+    assert declared_functions() == sorted(st.EXPORTED)
+
+
+def test_library_exports_every_declared_symbol(st):
+    L = st.lib()
+    for name in declared_functions():
+        assert hasattr(L, name), name
+
+
+def test_strerror_and_invalid_arguments(st):
+    L = st.lib()
+    assert L.stencil_strerror(0) == b"ok"
+    assert L.stencil_strerror(-1) == b"invalid argument"
+    import ctypes
+    h = ctypes.c_void_p()
+    # bad radius for the kind, bad dtype, bad size: rejected on the host
+    assert L.stencil_plan(ctypes.byref(h), 1, 8, 8, 8, 4, 0) == -1
+    assert L.stencil_plan(ctypes.byref(h), 1, 8, 8, 8, 1, 7) == -1
+    assert L.stencil_plan(ctypes.byref(h), 1, 0, 8, 8, 1, 0) == -1
+    assert L.stencil_plan(ctypes.byref(h), 9, 8, 8, 8, 1, 0) == -1
+    n = ctypes.c_int64()
+    assert L.stencil_schedule(1, -1, 1, None, 0, ctypes.byref(n)) == -1
+    assert L.stencil_schedule(1, 4, 0, None, 0, ctypes.byref(n)) == -1
+
+
+def simulate(kind, T, ops, wave):
+    """Track which time level each buffer holds; check every read."""
+    buf = {0: -1, 1: 0, 2: None, 3: None}
+    t = 0
+    for op, levels, in_p, in_c, out_p, out_c in ops:
+        if op == 1:
+            buf[out_c] = buf[in_c]
+            continue
+        assert buf[in_c] == t, (ops, t)
+        if wave:
+            assert buf[in_p] == t - 1
+        assert out_c != in_c
+        if levels >= 2:
+            # a blocked pass reads neighbours of its inputs: it may not
+            # overwrite them
+            assert out_c not in (in_p, in_c) if wave else out_c != in_c
+            if out_p >= 0:
+                assert out_p not in (in_p, in_c)
+        elif wave and out_c != in_p:
+            assert out_c not in (in_p, in_c) and out_p not in (in_p, in_c)
+        if out_p >= 0:
+            buf[out_p] = t + levels - 1
+        elif wave:
+            buf[in_c] = t  # unchanged; the new prev is the old cur
+        buf[out_c] = t + levels
+        t += levels
+    assert t == T
+    return buf
+
+
+@pytest.mark.parametrize("kind", [1, 2, 3, 4, 5, 6])
+@pytest.mark.parametrize("b", [1, 2, 3, 4, 5, 8])
+def test_schedule_leaves_state_in_caller_buffers(st, kind, b):
+    wave = st.SECOND_ORDER[kind]
+    for T in range(0, 40):
+        ops = st.schedule(kind, T, b)
+        buf = simulate(kind, T, ops, wave)
+        if T > 0:
+            assert buf[1] == T and buf[0] == T - 1, (kind, T, b, ops)
+            npass = sum(1 for o in ops if o[0] == 0)
+            ncopy = sum(1 for o in ops if o[0] == 1)
+            # at most one extra pass beyond ceil(T / b) and at most 2 copies (T = 1)
+            import math
+            assert npass <= math.ceil(T / b) + 2
+            assert ncopy <= (2 if T == 1 else 1)
+        else:
+            assert ops == []

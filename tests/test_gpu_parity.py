@@ -1,0 +1,159 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle on seeded
+inputs: every kind, FP64 (normwise <= 1e-12) and FP32 (stated bound), sizes
+spanning several tiles in x, y and z with ragged tails, T odd and even,
+receiver traces, the adjoint, coefficient gradients and the misfit."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_1410_3060_gb300 import workloads as wl
+from gpu_util import F32, F64, fp32_bound, gpu_forward, normwise_err, to_dev, to_np
+
+pytestmark = pytest.mark.gpu
+
+KINDS = [1, 2, 3, 4, 5, 6]
+SHAPES = [(70, 45, 40), (33, 17, 9)]
+
+
+@pytest.fixture(scope="module")
+def st():
+    import torch
+    assert torch.cuda.is_available()
+    from paper_1410_3060_gb300 import build, stencil
+    build.build()
+    return stencil
+
+
+def oracle_forward(wk, T, rcv_z=None):
+    return oracle.forward(wk.kind, wk.u_prev, wk.u, wk.w, wk.W, T, rcv_z=rcv_z, threads=8)
+
+
+@pytest.mark.parametrize("kind", KINDS)
+@pytest.mark.parametrize("shape", SHAPES)
+@pytest.mark.parametrize("T", [1, 2, 5])
+def test_forward_fp64(st, kind, shape, T):
+    wk = wl.make(kind, shape, T, seed=1)
+    rz = shape[2] // 2
+    op, ou, otr = oracle_forward(wk, T, rcv_z=rz)
+    gp, gu, gtr = gpu_forward(st.Plan, wk, F64, rcv_z=rz)
+    assert normwise_err(gu, ou) <= 1e-12
+    assert normwise_err(gp, op) <= 1e-12
+    assert normwise_err(gtr, otr) <= 1e-12
+    R = wk.R
+    halo = np.ones(gu.shape, bool)
+    halo[R:-R, R:-R, R:-R] = False
+    assert not gu[halo].any() and not gp[halo].any()
+
+
+@pytest.mark.parametrize("kind", KINDS)
+@pytest.mark.parametrize("T", [3, 8])
+def test_forward_fp32(st, kind, T):
+    shape = (70, 45, 40)
+    wk = wl.make(kind, shape, T, seed=2)
+    op, ou, _ = oracle_forward(wk, T)
+    gp, gu, _ = gpu_forward(st.Plan, wk, F32)
+    err = normwise_err(gu, ou)
+    assert err <= fp32_bound(kind, T, wk.R), err
+    assert normwise_err(gp, op) <= fp32_bound(kind, T, wk.R)
+
+
+def test_config_64cube_j7_const_fp64(st):
+    """7-point constant, 64^3, zero Dirichlet halo, T = 8, FP64: every entry."""
+    wk = wl.j7_const(64, 8, seed=0)
+    op, ou, _ = oracle_forward(wk, 8)
+    gp, gu, _ = gpu_forward(st.Plan, wk, F64)
+    assert normwise_err(gu, ou) <= 1e-12
+    assert normwise_err(gp, op) <= 1e-12
+
+
+def test_zero_steps_leave_state(st):
+    wk = wl.make(4, (20, 20, 20), 0, seed=3)
+    gp, gu, _ = gpu_forward(st.Plan, wk, F64, T=0)
+    np.testing.assert_array_equal(gu, wk.u)
+    np.testing.assert_array_equal(gp, wk.u_prev)
+
+
+def rand_interior(n, R, rng):
+    a = np.zeros(wl.padded_shape(n, R))
+    nx, ny, nz = n
+    a[R:R + nz, R:R + ny, R:R + nx] = rng.uniform(-1, 1, size=(nz, ny, nx))
+    return a
+
+
+@pytest.mark.parametrize("kind", KINDS)
+@pytest.mark.parametrize("dtype", [F64, F32])
+def test_adjoint_with_residual_and_gradient(st, kind, dtype):
+    import torch
+    rng = np.random.default_rng(10 + kind)
+    n = (37, 29, 21)
+    T = 4
+    wk = wl.make(kind, n, T, seed=4)
+    R = wk.R
+    l2 = rand_interior(n, R, rng)
+    l1 = rand_interior(n, R, rng)
+    states = np.stack([rand_interior(n, R, rng) for _ in range(T)])
+    res = rng.uniform(-1, 1, size=(T, n[1], n[0]))
+    rz = 7
+    k = oracle.NUM_ARRAYS[kind]
+    og = np.zeros((k,) + l1.shape) if k else None
+    # cast inputs through the GPU dtype so both sides see the same values
+    cast = (lambda a: a.astype(np.float32).astype(np.float64)) if dtype == F32 else (lambda a: a)
+    W = cast(wk.W) if wk.W is not None else None
+    ol2, ol1 = oracle.adjoint(kind, cast(l2), cast(l1), wk.w, W, T, states=cast(states), residual=cast(res),
+                              rcv_z=rz, grad=og, threads=8)
+    plan = st.Plan(kind, *n, dtype)
+    gl2, gl1 = to_dev(l2, dtype), to_dev(l1, dtype)
+    gst = [to_dev(s, dtype) for s in states]
+    gg = torch.zeros((k,) + l1.shape, device="cuda", dtype=torch.float64) if k else None
+    plan.adjoint(gl2, gl1, wk.w, to_dev(wk.W, dtype) if wk.W is not None else None, T,
+                 fwd_states=gst if k else None, residual=to_dev(res, dtype), rcv_z=rz, grad=gg)
+    torch.cuda.synchronize()
+    tol = 1e-12 if dtype == F64 else 2e-5
+    assert normwise_err(to_np(gl1), ol1) <= tol
+    assert normwise_err(to_np(gl2), ol2) <= tol
+    if k:
+        assert normwise_err(to_np(gg), og) <= (1e-12 if dtype == F64 else 2e-5)
+    plan.close()
+
+
+@pytest.mark.parametrize("dtype", [F64, F32])
+def test_misfit(st, dtype):
+    import torch
+    rng = np.random.default_rng(5)
+    T, ny, nx = 7, 13, 19
+    tr = rng.uniform(-1, 1, size=(T, ny, nx))
+    d = rng.uniform(-1, 1, size=(T, ny, nx))
+    plan = st.Plan(4, nx, ny, 9, dtype)
+    gtr, gd = to_dev(tr, dtype), to_dev(d, dtype)
+    res = torch.empty_like(gtr)
+    loss = torch.zeros(1, device="cuda", dtype=torch.float64)
+    plan.misfit(gtr, gd, res, loss)
+    torch.cuda.synchronize()
+    cast = (lambda a: a.astype(np.float32).astype(np.float64)) if dtype == F32 else (lambda a: a)
+    ol, orr = oracle.receiver_loss(cast(tr), cast(d))
+    assert abs(loss.item() - ol) <= (1e-13 if dtype == F64 else 1e-6) * ol
+    assert normwise_err(to_np(res), orr) <= (1e-15 if dtype == F64 else 1e-7)
+    plan.close()
+
+
+def test_bad_arguments_rejected(st):
+    import torch
+    plan = st.Plan(1, 16, 16, 16, F64)
+    u = torch.zeros(plan.padded_shape, device="cuda", dtype=torch.float64)
+    with pytest.raises(st.StencilError):
+        plan.forward(u, u, [0.4, 0.1], None, 2)          # aliased pair
+    v = torch.zeros(plan.padded_shape, device="cuda", dtype=torch.float64)
+    with pytest.raises(st.StencilError):
+        plan.forward(u, v, [0.4], None, 2)               # wrong weight count
+    with pytest.raises(st.StencilError):
+        plan.forward(u, v, [0.4, 0.1], None, -1)         # negative T
+    tr = torch.zeros((2, 16, 16), device="cuda", dtype=torch.float64)
+    with pytest.raises(st.StencilError):
+        plan.forward(u, v, [0.4, 0.1], None, 2, trace=tr, rcv_z=16)  # receiver outside
+    plan.close()
+
+
+def test_fma_peak_probe(st):
+    f64, clk = st.fma_peak(0)
+    f32, _ = st.fma_peak(1)
+    assert f64 > 1e11 and f32 > 1e13 and clk > 5e8
