@@ -45,8 +45,14 @@ def parse():
     p.add_argument("--impl", default="ours", choices=["ours", "reference"])
     p.add_argument("--n", type=int, default=512, help="interior size per axis")
     p.add_argument("--T", type=int, default=64, help="time steps per step")
+    p.add_argument("--kind", default="j7_var", choices=["j7_const", "j7_var", "w25_const", "w25_var",
+                                                          "j25_var", "w25_alpha"])
+    p.add_argument("--dtype", default="f64", choices=["f64", "f32"])
+    p.add_argument("--time-block", type=int, default=None, help="levels per pass (default: library choice)")
+    p.add_argument("--scheme", type=int, default=None, help="1 overlapped tiles, 2 diamond tiles in y")
     p.add_argument("--no-variants", action="store_true")
     p.add_argument("--no-cpu", action="store_true")
+    p.add_argument("--no-e2e", action="store_true")
     return p.parse_args()
 
 
@@ -188,7 +194,7 @@ def max_over_ranks(torch, ws, v):
 
 
 def forward_case(torch, st, wl, kind, n, T, dtype, steps, warmup, ws, stream, time_block=None, e2e=False,
-                 wk=None):
+                 wk=None, scheme=None):
     """Time `steps` calls of stencil_forward(T) on the workload; returns dict."""
     tdt = torch.float64 if dtype == st.F64 else torch.float32
     if wk is None:
@@ -196,6 +202,8 @@ def forward_case(torch, st, wl, kind, n, T, dtype, steps, warmup, ws, stream, ti
     plan = st.Plan(kind, n, n, n, dtype)
     if time_block is not None:
         plan.set(st.OPT_TIME_BLOCK, time_block)
+    if scheme is not None:
+        plan.set(st.OPT_SCHEME, scheme)
     b = plan.get(st.OPT_TIME_BLOCK)
     up = torch.from_numpy(wk.u_prev).to("cuda", tdt)
     u = torch.from_numpy(wk.u).to("cuda", tdt)
@@ -209,8 +217,9 @@ def forward_case(torch, st, wl, kind, n, T, dtype, steps, warmup, ws, stream, ti
     barrier(torch, ws)
     ms = max_over_ranks(torch, ws, tm.ms)
     lups = float(n) ** 3 * T
-    passes = [o for o in st.schedule(kind, T, b) if o[0] == 0]
+    passes = [o for o in st.schedule(kind, T, b, dtype) if o[0] == 0]
     res = {"kind": wl.KIND_NAMES[kind], "n": n, "T": T, "dtype": "f64" if dtype == st.F64 else "f32",
+           "scheme": plan.get(st.OPT_SCHEME),
            "time_block": b, "ms_per_step": ms / steps, "glups": lups * steps * ws / (ms * 1e-3) / 1e9,
            "launches_per_step": len(passes), "ms_per_launch": ms / steps / len(passes)}
     if e2e:
@@ -239,6 +248,37 @@ def forward_case(torch, st, wl, kind, n, T, dtype, steps, warmup, ws, stream, ti
     return res, wk
 
 
+KIND_BY_NAME = {"j7_const": 1, "j7_var": 2, "w25_const": 3, "w25_var": 4, "j25_var": 5, "w25_alpha": 6}
+KIND_TEXT = {1: "7-point constant coefficients (Fig. 1b)", 2: "7-point variable coefficients (Fig. 1c)",
+             3: "25-point constant-coefficient wave (Fig. 1e, scalar alpha)",
+             4: "25-point variable-coefficient wave (Fig. 1d coefficients)",
+             5: "25-point variable coefficients, first order (Fig. 1d)",
+             6: "25-point wave with alpha array (Fig. 1e)"}
+
+
+def roofline_of(pm, kind, dtype_name, n, res, peak_f64, hbm_peak, fp32_peak):
+    """Roofline record of one case: FP64 sweeps are bound by the FP64 pipe
+    (peak = 2 FP64 FMA per clock per SM x SMs x SM clock), FP32 sweeps by
+    HBM (peak = measured copy bandwidth).  Units processed per pass: n^3
+    updates of `time_block` levels; algorithmic bytes = one read of every
+    input stream and one write of the state per pass."""
+    word = 8 if dtype_name == "f64" else 4
+    b = res["time_block"]
+    t_pass = res["ms_per_step"] / (res["T"] / b) * 1e-3
+    pts = float(n) ** 3
+    bytes_pass = pm.gpu_bytes_per_lup(kind, word) * pts
+    flops_pass = pm.FLOPS_PER_LUP[kind] * pts * b
+    hbm = {"achieved_gbs": bytes_pass / t_pass / 1e9, "peak_gbs": hbm_peak,
+           "frac": bytes_pass / t_pass / 1e9 / hbm_peak}
+    if dtype_name == "f64":
+        ach = flops_pass / t_pass / 1e12
+        return {"bound": "alu", "achieved": ach, "peak": peak_f64 / 1e12, "unit": "TFLOP/s",
+                "frac": ach / (peak_f64 / 1e12), "traffic": None, "hbm_view": hbm}
+    return {"bound": "hbm", "achieved": hbm["achieved_gbs"], "peak": hbm_peak, "unit": "GB/s",
+            "frac": hbm["frac"], "traffic": None,
+            "alu_view": {"achieved_tflops": flops_pass / t_pass / 1e12, "peak_tflops": fp32_peak / 1e12}}
+
+
 def run_ours(args):
     import torch
     ws, rank, local = dist_env()
@@ -252,66 +292,71 @@ def run_ours(args):
     st.lib()
     stream = torch.cuda.current_stream()
     n, T = args.n, args.T
+    kind = KIND_BY_NAME[args.kind]
+    dtype = st.F64 if args.dtype == "f64" else st.F32
 
-    peak_f64, clk = st.fma_peak(st.F64)
-    peak_f32, _ = st.fma_peak(st.F32)
+    probe_f64, clk = st.fma_peak(st.F64)
+    probe_f32, _ = st.fma_peak(st.F32)
+    num_sms = torch.cuda.get_device_properties(0).multi_processor_count
+    peak_f64 = 2 * 2 * num_sms * clk      # 2 FP64 FMA per clock per SM (GB300 nominal FP64 rate)
+    peak_f32 = 2 * 128 * num_sms * clk    # 128 FP32 FMA per clock per SM
     peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
         os.path.join(ROOT, "MEASURED_PEAKS.json")) else {}
     hbm_peak = peaks.get("hbm_gbs", 6800.0)
 
-    # main line: 7-point variable coefficients, FP64, 512^3, T = 64
     dev_index = torch.cuda.current_device()
     sampler = ClockSampler(dev_index)
-    wk = wl.j7_var(n, T, seed=0)
+    wk = wl.make(kind, n, T, seed=0) if kind != wl.J7_VAR else wl.j7_var(n, T, seed=0)
     with sampler:
-        main, _ = forward_case(torch, st, wl, wl.J7_VAR, n, T, st.F64, args.steps, args.warmup, ws, stream,
-                               e2e=True, wk=wk)
+        main, _ = forward_case(torch, st, wl, kind, n, T, dtype, args.steps, args.warmup, ws, stream,
+                               time_block=args.time_block, e2e=not args.no_e2e, wk=wk, scheme=args.scheme)
     clocks = sampler.summary()
-
-    flops_launch = pm.FLOPS_PER_LUP[wl.J7_VAR] * float(n) ** 3
-    bytes_launch = pm.gpu_bytes_per_lup(wl.J7_VAR, 8) * float(n) ** 3
-    t_launch = main["ms_per_launch"] * 1e-3
-    achieved = flops_launch / t_launch / 1e12
-    roofline = {"bound": "alu", "achieved": achieved, "peak": peak_f64 / 1e12, "unit": "TFLOP/s",
-                "frac": achieved / (peak_f64 / 1e12), "traffic": None,
-                "peak_source": "FP64 FMA chains measured in this run (stencil_fma_peak)",
-                "hbm_view": {"achieved_gbs": bytes_launch / t_launch / 1e9, "peak_gbs": hbm_peak,
-                             "frac": bytes_launch / t_launch / 1e9 / hbm_peak},
-                "kernel": "plain_sweep_kernel<double, J7_VAR>"}
+    roofline = roofline_of(pm, kind, args.dtype, n, main, peak_f64, hbm_peak, peak_f32)
+    roofline["kernel"] = ("plain_sweep_kernel" if main["time_block"] == 1 else "blocked_kernel (phase A + B)") + \
+        f"<{'double' if dtype == st.F64 else 'float'}, {args.kind}>"
+    roofline["peak_source"] = ("2 FP64 FMA/clk/SM x %d SMs x %.0f MHz (measured clock); FMA-chain probe %.3f TFLOP/s"
+                               % (num_sms, clk / 1e6, probe_f64 / 1e12)) if dtype == st.F64 else \
+        "MEASURED_PEAKS.json hbm_gbs (copy, measured)"
 
     variants = []
     if not args.no_variants:
-        for kind, dtype, nn, TT in ((wl.J7_VAR, st.F32, n, T),
-                                    (wl.W25_CONST, st.F64, n, 100), (wl.W25_CONST, st.F32, n, 100),
-                                    (wl.W25_VAR, st.F64, n, T), (wl.W25_VAR, st.F32, n, T)):
-            wkv = wk if kind == wl.J7_VAR else None
-            r, _ = forward_case(torch, st, wl, kind, nn, TT, dtype, max(1, args.steps // 2), 1, ws, stream,
-                                wk=wkv)
-            word = 8 if dtype == st.F64 else 4
-            r["hbm_gbs_algorithmic"] = pm.gpu_bytes_per_lup(kind, word) * r["glups"] * 1e9 / r["time_block"] / 1e9 / ws
+        cases = [(wl.J7_VAR, st.F32, T, 1), (wl.J7_VAR, st.F32, T, None),
+                 (wl.W25_CONST, st.F64, 100, 1), (wl.W25_CONST, st.F32, 100, 1), (wl.W25_CONST, st.F32, 100, None),
+                 (wl.W25_VAR, st.F64, T, 1), (wl.W25_VAR, st.F32, T, 1), (wl.W25_VAR, st.F32, T, None),
+                 (wl.J7_CONST, st.F64, T, 1), (wl.J7_CONST, st.F32, T, 1), (wl.J7_CONST, st.F32, T, None)]
+        cache = {wl.J7_VAR: wk} if kind == wl.J7_VAR else {}
+        for vk, vd, vT, vb in cases:
+            if vk not in cache:
+                cache.clear()
+                cache[vk] = wl.make(vk, n, vT, seed=0) if vk != wl.J7_VAR else wl.j7_var(n, vT, seed=0)
+            r, _ = forward_case(torch, st, wl, vk, n, vT, vd, max(1, args.steps // 2), 1, ws, stream,
+                                time_block=vb, wk=cache[vk])
+            r["roofline"] = roofline_of(pm, vk, r["dtype"], n, r, peak_f64, hbm_peak, peak_f32)
             variants.append(r)
+        cache.clear()
 
     cpu = None
     if rank == 0 and not args.no_cpu:
         import oracle
         oracle.build()
         threads = oracle.oracle.default_threads()
-        rate, dt = cpu_oracle_rate(wl.J7_VAR, wk, 1, threads)
+        rate, dt = cpu_oracle_rate(kind, wk, 1, threads)
         cpu = {"value": rate, "unit": METRIC, "cores": threads, "kind": "oracle",
-               "sample": f"1 time step of the {n}^3 7-point variable-coefficient FP64 sweep ({dt:.1f} s)"}
+               "sample": f"1 time step of the {n}^3 {args.kind} FP64 sweep ({dt:.1f} s)"}
 
     if rank == 0:
         line = {
             "metric": METRIC, "value": main["glups"], "unit": METRIC, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": main["ms_per_step"], "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": f"j7_var_{n}^3_T{T}_fp64", "kind": "7-point variable coefficients (Fig. 1c)",
+            "scaling": "weak", "vs_baseline": None, "dtype": args.dtype, "data": "synthetic",
+            "config": {"workload": f"{args.kind}_{n}^3_T{T}_{args.dtype}", "kind": KIND_TEXT[kind],
                        "n": n, "T": T, "time_block": main["time_block"], "parallelism": f"replicas{ws}",
-                       "l2": "inputs larger than L2 (1.1 GB field + 7.6 GB coefficients)"},
-            "e2e": main["e2e"], "gpu_launches": main["launches_per_step"] * args.steps,
+                       "l2": "inputs larger than L2 (no flush needed)" if n >= 256 else "small case"},
+            "e2e": main.get("e2e"), "gpu_launches": main["launches_per_step"] * args.steps,
             "roofline": roofline, "clocks": clocks, "cpu_baseline": cpu,
-            "peaks_measured": {"fp64_tflops": peak_f64 / 1e12, "fp32_tflops": peak_f32 / 1e12,
-                               "sm_clock_mhz_probe": clk / 1e6, "hbm_gbs": hbm_peak},
+            "peaks_measured": {"fp64_fma_probe_tflops": probe_f64 / 1e12, "fp32_fma_probe_tflops": probe_f32 / 1e12,
+                               "fp64_peak_tflops": peak_f64 / 1e12, "fp32_peak_tflops": peak_f32 / 1e12,
+                               "sm_clock_mhz": clk / 1e6, "hbm_gbs": hbm_peak},
             "variants": variants,
         }
         print(json.dumps(line), flush=True)

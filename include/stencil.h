@@ -85,7 +85,12 @@ enum stencil_option {
        x and y, 2 = diamond (split) tiles in y with overlapped x. */
     STENCIL_OPT_SCHEME = 2,
     /* Read-only: bytes of device scratch the plan holds. */
-    STENCIL_OPT_SCRATCH_BYTES = 3
+    STENCIL_OPT_SCRATCH_BYTES = 3,
+    /* Adjoint steps whose coefficient-gradient terms are summed in FP64
+       registers before one read-modify-write of the gradient arrays
+       (1..16, default 1).  G > 1 makes the plan hold G + 2 state fields of
+       scratch in which stencil_adjoint keeps the adjoint levels of a batch. */
+    STENCIL_OPT_GRAD_BATCH = 4
 };
 
 typedef struct stencil_plan_s *stencil_plan_t;
@@ -133,6 +138,15 @@ void stencil_plan_destroy(stencil_plan_t plan);
 int stencil_forward(stencil_plan_t plan, void *u_prev, void *u, const stencil_coeffs_t *coeffs,
                     int64_t T, void *stream, void *trace, int64_t rcv_z);
 
+/* Forward T steps of plain sweeps storing every state (the recompute pass
+ * of checkpointed differentiation): states is a host array of T device
+ * pointers, states[t] receives u^{t+1}.  u_prev, u hold (u^{-1}, u^0) and
+ * are only read.  trace / rcv_z as in stencil_forward.  The state arrays
+ * must be distinct from each other and from the inputs. */
+int stencil_forward_states(stencil_plan_t plan, const void *u_prev, const void *u,
+                           const stencil_coeffs_t *coeffs, int64_t T, void *const *states,
+                           void *stream, void *trace, int64_t rcv_z);
+
 /* T steps of the adjoint (transposed) sweep, backward in time, for a loss
  * L = sum_n l_n(u^n) with explicit partials g^n = P^T r^n injected on
  * receiver plane rcv_z.  With A the spatial operator and A^T its transpose
@@ -154,6 +168,13 @@ int stencil_adjoint(stencil_plan_t plan, void *lam_next, void *lam, const stenci
                     int64_t T, void *stream, const void *const *fwd_states, const void *residual,
                     int64_t rcv_z, double *grad);
 
+/* out[i] = alpha * x[i] + beta * y[i] for n elements of the plan's dtype
+ * (the gradient with respect to a tied initial state, dL/du0 = lam^0 -
+ * lam^1 for second-order kinds with u^{-1} = u^0, and the scaling of a
+ * residual by an incoming loss gradient).  out may alias x or y. */
+int stencil_axpby(stencil_plan_t plan, int64_t n, double alpha, const void *x, double beta,
+                  const void *y, void *out, void *stream);
+
 /* Receiver misfit of T traces: residual = trace - d (plan dtype, may alias
  * neither input unless equal to trace), and *loss (device FP64) =
  * 0.5 * sum (trace - d)^2 accumulated in FP64 in a fixed order
@@ -162,8 +183,10 @@ int stencil_misfit(stencil_plan_t plan, const void *trace, const void *d, int64_
                    double *loss, void *stream);
 
 /* Host-only: the program of passes and copies that stencil_forward (and,
- * with the same rules, stencil_adjoint) runs for T steps of `kind` with
- * temporal block depth b (b >= 1; 1 = plain sweeps).  Each op is 6 int32:
+ * with the same rules, stencil_adjoint) runs for T steps of `kind` in
+ * `dtype` with temporal block depth b (b >= 1; 1 = plain sweeps; a depth
+ * the kernels do not provide falls back to 1, and remainders use the
+ * provided depths).  Each op is 6 int32:
  *   {op, levels, in_prev, in_cur, out_prev, out_cur}
  * op 0 = pass over the lattice applying `levels` time levels, op 1 = copy
  * of buffer in_cur to out_cur.  Buffer ids: 0 = the caller's u_prev,
@@ -172,7 +195,7 @@ int stencil_misfit(stencil_plan_t plan, const void *trace, const void *d, int64_
  * out_cur and, when out_prev >= 0, u^{t+levels-1} to out_prev; out_cur ==
  * in_prev marks an in-place second-order update.  Writes at most max_ops
  * ops and the total count to *n_ops.  Performs no CUDA call. */
-int stencil_schedule(int kind, int64_t T, int b, int32_t *ops, int64_t max_ops, int64_t *n_ops);
+int stencil_schedule(int kind, int dtype, int64_t T, int b, int32_t *ops, int64_t max_ops, int64_t *n_ops);
 
 /* Measure the device's FP64 (dtype STENCIL_F64) or FP32 fused multiply-add
  * throughput with independent FMA chains on every SM: *flops = flops per

@@ -44,46 +44,62 @@ struct Op {
 enum { BUF_A = 0, BUF_B = 1, BUF_S1 = 2, BUF_S2 = 3 };
 
 // The pass program of T steps with block depth b (see the file comment).
-std::vector<Op> build_program(int kind, int64_t T, int b) {
+// Split n levels into passes of at most b levels each, using only depths the
+// blocked kernels provide (ok(L)); anything left becomes plain 1-level passes.
+template <typename OK>
+void split_levels(std::vector<int> &L, int64_t n, int b, OK ok) {
+    while (n > 0) {
+        int take = (int)std::min<int64_t>(n, b);
+        while (take > 1 && !ok(take)) --take;
+        L.push_back(take);
+        n -= take;
+    }
+}
+
+template <typename OK>
+std::vector<Op> build_program(int kind, int64_t T, int b, OK ok) {
     std::vector<Op> ops;
     if (T <= 0) return ops;
     if (b < 1) b = 1;
     std::vector<int> L;
     const bool wave = kind_wave(kind);
     if (wave) {
-        if (b == 1) {
-            L.assign((size_t)T, 1);
-        } else {
-            for (int64_t i = 0; i < T / b; ++i) L.push_back(b);
-            if (T % b) L.push_back((int)(T % b));
-        }
-        std::vector<bool> move(L.size());
-        int nb = 0;
-        for (size_t i = 0; i < L.size(); ++i) { move[i] = L[i] >= 2; nb += move[i]; }
         if (T == 1) {
             ops.push_back({0, 1, BUF_A, BUF_B, BUF_S1, BUF_S2});
             ops.push_back({1, 0, -1, BUF_S1, -1, BUF_A});
             ops.push_back({1, 0, -1, BUF_S2, -1, BUF_B});
             return ops;
         }
-        if (nb % 2 == 1) {
-            int last_plain = -1;
-            for (size_t i = 0; i < L.size(); ++i) if (!move[i]) last_plain = (int)i;
-            if (last_plain >= 0) {
-                move[last_plain] = true;
-            } else {
-                // split the last blocked pass into (levels-1, 1), both moves
+        split_levels(L, T, b, ok);
+        // a pass of >= 2 levels moves the pair to the other buffer set; a
+        // 1-level pass may be an in-place update (stays) or a move
+        std::vector<bool> move(L.size());
+        auto count = [&]() { int c = 0; for (bool m : move) c += m; return c; };
+        auto last_single = [&](bool as_move) {
+            for (int i = (int)L.size() - 1; i >= 0; --i)
+                if (L[i] == 1 && move[i] == as_move) return i;
+            return -1;
+        };
+        for (size_t i = 0; i < L.size(); ++i) move[i] = L[i] >= 2;
+        if (count() % 2 == 1) {
+            if (last_single(false) < 0) {
+                // no 1-level pass: peel one level off the last pass
                 const int v = L.back();
-                L.back() = v - 1;
+                L.pop_back();
+                move.pop_back();
+                std::vector<int> head;
+                split_levels(head, v - 1, v - 1, ok);
+                for (int h : head) { L.push_back(h); move.push_back(h >= 2); }
                 L.push_back(1);
-                move.push_back(true);
+                move.push_back(false);
             }
-            ++nb;
+            if (count() % 2 == 1) move[last_single(false)] = true;
         }
-        if (nb == 0 && T % 2 == 1) {
-            int c = 0;
-            for (int i = (int)L.size() - 1; i >= 0 && c < 2; --i) { move[i] = true; ++c; }
-            nb = 2;
+        if (count() == 0 && T % 2 == 1) {
+            // all in place with an odd count would leave the pair swapped:
+            // route two single steps through the scratch pair
+            move[last_single(false)] = true;
+            move[last_single(false)] = true;
         }
         int P = BUF_A, C = BUF_B;
         bool in_user = true;
@@ -109,9 +125,7 @@ std::vector<Op> build_program(int kind, int64_t T, int b) {
         if (b == 1) {
             L.assign((size_t)T, 1);
         } else {
-            const int64_t Tb = T - 1;
-            for (int64_t i = 0; i < Tb / b; ++i) L.push_back(b);
-            if (Tb % b) L.push_back((int)(Tb % b));
+            split_levels(L, T - 1, b, ok);
             L.push_back(1);
         }
         int C = BUF_B;
@@ -140,6 +154,11 @@ struct stencil_plan_s {
     int scheme;       // 0 = default
     size_t elem, field_bytes;
     void *scratch[2];
+    void *bands[8];   // diamond edge bands of the blocked passes
+    int nbands;
+    int grad_batch;   // adjoint steps per FP64 gradient update
+    void *gring[GRAD_MAX_STEPS + 2];  // adjoint levels of one gradient batch
+    int ngring;
     double *partials;
     int npartials;
 };
@@ -190,7 +209,9 @@ int run_program(stencil_plan_s *p, void *pair_p, void *pair_c, const stencil_coe
                  cudaStream_t st, bool adjoint, void *trace, const void *inject, int64_t rcv_z,
                  const void *const *fwd_states, double *grad) {
     const int b = effective_time_block(p);
-    const std::vector<Op> ops = build_program(p->kind, nsteps, b);
+    const int kind = p->kind, dtype = p->dtype;
+    const std::vector<Op> ops =
+        build_program(p->kind, nsteps, b, [&](int L) { return blocked_supported(kind, dtype, L); });
     void *buf[4] = {pair_p, pair_c, p->scratch[0], p->scratch[1]};
     const Scalars s = fold_scalars(p->kind, coeffs);
     const int64_t plane = (int64_t)p->g.nx * p->g.ny;
@@ -251,6 +272,8 @@ int run_program(stencil_plan_s *p, void *pair_p, void *pair_c, const stencil_coe
             a.rcv_z = (int)rcv_z;
             a.trace = trace ? (T *)trace + t * plane : nullptr;
             a.levels = o.levels;
+            if (blocked_scratch_levels(o.levels) > p->nbands) return STENCIL_EUNSUPPORTED;
+            for (int k = 1; k < o.levels; ++k) a.bands[k] = (T *)p->bands[k - 1];
             cudaError_t e = launch_blocked<T>(p->kind, a, st, p->num_sms, p->scheme);
             if (e != cudaSuccess) return cuda_fail(e);
         }
@@ -259,7 +282,146 @@ int run_program(stencil_plan_s *p, void *pair_p, void *pair_c, const stencil_coe
     return STENCIL_OK;
 }
 
+// Plain sweep launch helper shared by the runners below.
+template <typename T>
+cudaError_t plain_step(stencil_plan_s *p, bool adjoint, const Scalars &s, const stencil_coeffs_t *coeffs,
+                       const void *in_p, const void *in_c, void *out, T *trace, const T *inject, int64_t rcv_z,
+                       cudaStream_t st) {
+    SweepArgs<T> a;
+    memset(&a, 0, sizeof(a));
+    a.u_prev = (const T *)in_p;
+    a.u = (const T *)in_c;
+    a.out = (T *)out;
+    a.W = coeffs ? (const T *)coeffs->arrays : nullptr;
+    a.s = s;
+    a.g = p->g;
+    a.rcv_z = (int)rcv_z;
+    a.trace = trace;
+    a.inject = inject;
+    return launch_plain<T>(p->kind, adjoint, a, st, p->num_sms);
+}
+
+// Forward T plain steps storing every state: step t reads
+// (u^{t-1}, u^t) and writes u^{t+1} into states[t].
+template <typename T>
+int run_forward_states(stencil_plan_s *p, const void *u_prev, const void *u, const stencil_coeffs_t *coeffs,
+                       int64_t nsteps, void *const *states, cudaStream_t st, void *trace, int64_t rcv_z) {
+    const Scalars s = fold_scalars(p->kind, coeffs);
+    const int64_t plane = (int64_t)p->g.nx * p->g.ny;
+    for (int64_t t = 0; t < nsteps; ++t) {
+        const void *ip = t >= 2 ? states[t - 2] : (t == 1 ? u : u_prev);
+        const void *ic = t >= 1 ? states[t - 1] : u;
+        cudaError_t e = plain_step<T>(p, false, s, coeffs, ip, ic, states[t],
+                                      trace ? (T *)trace + t * plane : nullptr, nullptr, rcv_z, st);
+        if (e != cudaSuccess) return cuda_fail(e);
+    }
+    return STENCIL_OK;
+}
+
+// Adjoint with gradient batches: every adjoint level is written to a ring of
+// G + 2 plan fields, and after every G steps one gradient launch sums the G
+// terms lam^{n+1} * d(A u^n)/dA in FP64 registers and updates the gradient
+// arrays once.  Step j (j = 1..T) produces lam^{m-j} into ring slot
+// (j-1) mod (G+2); its inputs lam^{m-j+1}, lam^{m-j+2} sit in the two
+// previous slots (or the caller's pair), which are not rewritten before
+// the batch that reads them has run.
+template <typename T>
+int run_adjoint_ring(stencil_plan_s *p, void *lam_next, void *lam, const stencil_coeffs_t *coeffs, int64_t nsteps,
+                     cudaStream_t st, const void *inject, int64_t rcv_z, const void *const *fwd_states,
+                     double *grad) {
+    const int G = p->grad_batch, NSL = G + 2;
+    const Scalars s = fold_scalars(p->kind, coeffs);
+    const int64_t plane = (int64_t)p->g.nx * p->g.ny;
+    auto level = [&](int64_t j) -> void * {  // buffer holding lam^{m-j}
+        if (j == -1) return lam_next;
+        if (j == 0) return lam;
+        return p->gring[(j - 1) % NSL];
+    };
+    GradArgs<T> ga;
+    memset(&ga, 0, sizeof(ga));
+    ga.grad = grad;
+    ga.s = s;
+    if (p->kind == W25_ALPHA)
+        for (int r = 0; r <= 4; ++r) ga.s.c[r] = coeffs->w[r];
+    ga.g = p->g;
+    for (int64_t j = 1; j <= nsteps; ++j) {
+        const T *inj = inject ? (const T *)inject + (nsteps - j) * plane : nullptr;
+        cudaError_t e = plain_step<T>(p, true, s, coeffs, level(j - 2), level(j - 1), level(j), nullptr, inj,
+                                      rcv_z, st);
+        if (e != cudaSuccess) return cuda_fail(e);
+        ga.u[ga.nsteps] = (const T *)fwd_states[nsteps - j];
+        ga.lam[ga.nsteps] = (const T *)level(j - 1);
+        ++ga.nsteps;
+        if (ga.nsteps == G || j == nsteps) {
+            e = launch_grad<T>(p->kind, ga, st);
+            if (e != cudaSuccess) return cuda_fail(e);
+            ga.nsteps = 0;
+        }
+    }
+    // final pair (lam^{m-T+1}, lam^{m-T}) back into the caller's buffers
+    cudaError_t e = cudaSuccess;
+    if (level(nsteps - 1) != lam_next)
+        e = cudaMemcpyAsync(lam_next, level(nsteps - 1), p->field_bytes, cudaMemcpyDeviceToDevice, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(lam, level(nsteps), p->field_bytes, cudaMemcpyDeviceToDevice, st);
+    return e == cudaSuccess ? STENCIL_OK : cuda_fail(e);
+}
+
+void free_bands(stencil_plan_s *p) {
+    for (int i = 0; i < 8; ++i) {
+        if (p->bands[i]) cudaFree(p->bands[i]);
+        p->bands[i] = nullptr;
+    }
+    p->nbands = 0;
+}
+
+// Allocate the band buffers of the effective block depth (plan time only).
+int ensure_bands(stencil_plan_s *p) {
+    const int b = effective_time_block(p);
+    const int need = b > 1 ? blocked_scratch_levels(b) : 0;
+    if (need <= p->nbands) return STENCIL_OK;
+    free_bands(p);
+    for (int i = 0; i < need; ++i) {
+        cudaError_t e = cudaMalloc(&p->bands[i], p->field_bytes);
+        if (e != cudaSuccess) {
+            free_bands(p);
+            g_last_cuda_error = (int)e;
+            cudaGetLastError();
+            return STENCIL_ENOMEM;
+        }
+    }
+    p->nbands = need;
+    return STENCIL_OK;
+}
+
+void free_gring(stencil_plan_s *p) {
+    for (int i = 0; i < GRAD_MAX_STEPS + 2; ++i) {
+        if (p->gring[i]) cudaFree(p->gring[i]);
+        p->gring[i] = nullptr;
+    }
+    p->ngring = 0;
+}
+
+int ensure_gring(stencil_plan_s *p) {
+    const int need = p->grad_batch > 1 ? p->grad_batch + 2 : 0;
+    if (need <= p->ngring) return STENCIL_OK;
+    free_gring(p);
+    for (int i = 0; i < need; ++i) {
+        cudaError_t e = cudaMalloc(&p->gring[i], p->field_bytes);
+        if (e == cudaSuccess) e = cudaMemset(p->gring[i], 0, p->field_bytes);  // zero halo
+        if (e != cudaSuccess) {
+            free_gring(p);
+            g_last_cuda_error = (int)e;
+            cudaGetLastError();
+            return STENCIL_ENOMEM;
+        }
+    }
+    p->ngring = need;
+    return STENCIL_OK;
+}
+
 void free_scratch(stencil_plan_s *p) {
+    free_gring(p);
+    free_bands(p);
     for (int i = 0; i < 2; ++i) {
         if (p->scratch[i]) cudaFree(p->scratch[i]);
         p->scratch[i] = nullptr;
@@ -292,6 +454,7 @@ int stencil_plan(stencil_plan_t *plan, int kind, int64_t nx, int64_t ny, int64_t
     p->g.sz = px * py;
     p->g.nfield = px * py * pz;
     p->elem = dtype == STENCIL_F64 ? 8 : 4;
+    p->grad_batch = 1;
     p->field_bytes = (size_t)p->g.nfield * p->elem;
     cudaError_t e = cudaGetDevice(&p->device);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&p->num_sms, cudaDevAttrMultiProcessorCount, p->device);
@@ -308,6 +471,8 @@ int stencil_plan(stencil_plan_t *plan, int kind, int64_t nx, int64_t ny, int64_t
     p->npartials = 1024;
     e = cudaMalloc(&p->partials, p->npartials * sizeof(double));
     if (e != cudaSuccess) { free_scratch(p); delete p; g_last_cuda_error = (int)e; cudaGetLastError(); return STENCIL_ENOMEM; }
+    const int st = ensure_bands(p);
+    if (st != STENCIL_OK) { free_scratch(p); delete p; return st; }
     *plan = p;
     return STENCIL_OK;
 }
@@ -319,11 +484,15 @@ int stencil_plan_set(stencil_plan_t p, int option, int64_t value) {
         if (value < 0 || value > 64) return STENCIL_EINVAL;
         if (value > 1 && !blocked_supported(p->kind, p->dtype, (int)value)) return STENCIL_EUNSUPPORTED;
         p->time_block = (int)value;
-        return STENCIL_OK;
+        return ensure_bands(p);
     case STENCIL_OPT_SCHEME:
         if (value < 0 || value > 2) return STENCIL_EINVAL;
         p->scheme = (int)value;
         return STENCIL_OK;
+    case STENCIL_OPT_GRAD_BATCH:
+        if (value < 1 || value > GRAD_MAX_STEPS) return STENCIL_EINVAL;
+        p->grad_batch = (int)value;
+        return ensure_gring(p);
     default:
         return STENCIL_EINVAL;
     }
@@ -334,8 +503,10 @@ int stencil_plan_get(stencil_plan_t p, int option, int64_t *value) {
     switch (option) {
     case STENCIL_OPT_TIME_BLOCK: *value = effective_time_block(p); return STENCIL_OK;
     case STENCIL_OPT_SCHEME: *value = p->scheme; return STENCIL_OK;
+    case STENCIL_OPT_GRAD_BATCH: *value = p->grad_batch; return STENCIL_OK;
     case STENCIL_OPT_SCRATCH_BYTES:
-        *value = (int64_t)((p->scratch[0] ? 2 * p->field_bytes : 0) + p->npartials * sizeof(double));
+        *value = (int64_t)((p->scratch[0] ? 2 * p->field_bytes : 0) + (p->nbands + p->ngring) * p->field_bytes +
+                           p->npartials * sizeof(double));
         return STENCIL_OK;
     default: return STENCIL_EINVAL;
     }
@@ -384,6 +555,13 @@ int stencil_adjoint(stencil_plan_t p, void *lam_next, void *lam, const stencil_c
             if (!fwd_states[i]) return STENCIL_EINVAL;
     }
     if (T == 0) return STENCIL_OK;
+    if (grad && p->grad_batch > 1) {
+        if (p->dtype == STENCIL_F64)
+            return run_adjoint_ring<double>(p, lam_next, lam, coeffs, T, (cudaStream_t)stream, residual,
+                                            residual ? rcv_z : -1, fwd_states, grad);
+        return run_adjoint_ring<float>(p, lam_next, lam, coeffs, T, (cudaStream_t)stream, residual,
+                                       residual ? rcv_z : -1, fwd_states, grad);
+    }
     // the adjoint runs plain passes (time block 1)
     const int saved = p->time_block;
     p->time_block = 1;
@@ -396,6 +574,42 @@ int stencil_adjoint(stencil_plan_t p, void *lam_next, void *lam, const stencil_c
                                residual ? rcv_z : -1, fwd_states, grad);
     p->time_block = saved;
     return r;
+}
+
+int stencil_forward_states(stencil_plan_t p, const void *u_prev, const void *u, const stencil_coeffs_t *coeffs,
+                           int64_t T, void *const *states, void *stream, void *trace, int64_t rcv_z) {
+    if (!p || T < 0) return STENCIL_EINVAL;
+    int st = check_pair(p, (void *)u_prev, (void *)u);
+    if (st) return st;
+    if ((st = check_coeffs(p, coeffs))) return st;
+    if (trace && (rcv_z < 0 || rcv_z >= p->g.nz)) return STENCIL_EINVAL;
+    if (T > 0 && !states) return STENCIL_EINVAL;
+    for (int64_t t = 0; t < T; ++t) {
+        if (!states[t] || !aligned16(states[t])) return STENCIL_EINVAL;
+        if (overlap(states[t], u, p->field_bytes) || overlap(states[t], u_prev, p->field_bytes)) return STENCIL_EINVAL;
+        if (t > 0 && overlap(states[t], states[t - 1], p->field_bytes)) return STENCIL_EINVAL;
+        if (t > 1 && overlap(states[t], states[t - 2], p->field_bytes)) return STENCIL_EINVAL;
+    }
+    if (T == 0) return STENCIL_OK;
+    if (p->dtype == STENCIL_F64)
+        return run_forward_states<double>(p, u_prev, u, coeffs, T, states, (cudaStream_t)stream, trace,
+                                          trace ? rcv_z : -1);
+    return run_forward_states<float>(p, u_prev, u, coeffs, T, states, (cudaStream_t)stream, trace,
+                                     trace ? rcv_z : -1);
+}
+
+int stencil_axpby(stencil_plan_t p, int64_t n, double alpha, const void *x, double beta, const void *y, void *out,
+                  void *stream) {
+    if (!p || !x || !y || !out || n < 0) return STENCIL_EINVAL;
+    if (n == 0) return STENCIL_OK;
+    cudaError_t e;
+    if (p->dtype == STENCIL_F64)
+        e = launch_axpby<double>(alpha, (const double *)x, beta, (const double *)y, (double *)out, n,
+                                 p->num_sms, (cudaStream_t)stream);
+    else
+        e = launch_axpby<float>(alpha, (const float *)x, beta, (const float *)y, (float *)out, n,
+                                p->num_sms, (cudaStream_t)stream);
+    return e == cudaSuccess ? STENCIL_OK : cuda_fail(e);
 }
 
 int stencil_misfit(stencil_plan_t p, const void *trace, const void *d, int64_t T, void *residual, double *loss,
@@ -412,9 +626,13 @@ int stencil_misfit(stencil_plan_t p, const void *trace, const void *d, int64_t T
     return e == cudaSuccess ? STENCIL_OK : cuda_fail(e);
 }
 
-int stencil_schedule(int kind, int64_t T, int b, int32_t *ops, int64_t max_ops, int64_t *n_ops) {
-    if (kind_radius(kind) < 0 || T < 0 || b < 1 || !n_ops || (max_ops > 0 && !ops)) return STENCIL_EINVAL;
-    const std::vector<Op> prog = build_program(kind, T, b);
+int stencil_schedule(int kind, int dtype, int64_t T, int b, int32_t *ops, int64_t max_ops, int64_t *n_ops) {
+    if (kind_radius(kind) < 0 || (dtype != STENCIL_F64 && dtype != STENCIL_F32) || T < 0 || b < 1 || !n_ops ||
+        (max_ops > 0 && !ops))
+        return STENCIL_EINVAL;
+    if (b > 1 && !blocked_supported(kind, dtype, b)) b = 1;
+    const std::vector<Op> prog =
+        build_program(kind, T, b, [&](int L) { return blocked_supported(kind, dtype, L); });
     *n_ops = (int64_t)prog.size();
     for (int64_t i = 0; i < (int64_t)prog.size() && i < max_ops; ++i) {
         const Op &o = prog[(size_t)i];

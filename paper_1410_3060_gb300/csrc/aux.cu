@@ -10,6 +10,8 @@
 //   W25_ALPHA (Fig. 1e): w0 u^n(x) + sum_r w_r (pairs along x, y, z)
 // The batch sum is kept in FP64 registers and added to the FP64 gradient
 // arrays once per batch.
+#include <algorithm>
+
 #include "plain.cuh"
 
 namespace stc {
@@ -117,6 +119,25 @@ cudaError_t launch_misfit(const T *trace, const T *d, T *residual, int64_t n, do
     return cudaGetLastError();
 }
 
+template <typename T>
+__global__ void __launch_bounds__(256) axpby_kernel(double alpha, const T *x, double beta, const T *y, T *out,
+                                                    int64_t n) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        out[i] = (T)(alpha * (double)x[i] + beta * (double)y[i]);
+}
+
+template <typename T>
+cudaError_t launch_axpby(double alpha, const T *x, double beta, const T *y, T *out, int64_t n, int num_sms,
+                         cudaStream_t st) {
+    const int64_t blocks = std::min<int64_t>((n + 255) / 256, (int64_t)num_sms * 16);
+    axpby_kernel<T><<<(int)std::max<int64_t>(blocks, 1), 256, 0, st>>>(alpha, x, beta, y, out, n);
+    return cudaGetLastError();
+}
+
+template cudaError_t launch_axpby<float>(double, const float *, double, const float *, float *, int64_t, int,
+                                         cudaStream_t);
+template cudaError_t launch_axpby<double>(double, const double *, double, const double *, double *, int64_t, int,
+                                          cudaStream_t);
 template cudaError_t launch_grad<float>(int, const GradArgs<float> &, cudaStream_t);
 template cudaError_t launch_grad<double>(int, const GradArgs<double> &, cudaStream_t);
 template cudaError_t launch_misfit<float>(const float *, const float *, float *, int64_t, double *, int, double *,

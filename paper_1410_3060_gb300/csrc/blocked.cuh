@@ -14,13 +14,17 @@ struct BlockedArgs {
     T *trace;            // trace rows of levels t+1..t+levels ([levels][ny][nx]) or nullptr
     Scalars s;
     Geom g;
+    T *bands[8];         // diamond edge bands of levels 1..levels-1 (padded fields)
     int rcv_z;
     int levels;
     int zchunk;
+    int wA;              // phase-A tile height (diamond scheme)
 };
 
 bool blocked_supported(int kind, int dtype, int levels);
 int blocked_default_levels(int kind, int dtype);
+// padded fields of band scratch a pass of `levels` levels needs
+int blocked_scratch_levels(int levels);
 template <typename T>
 cudaError_t launch_blocked(int kind, const BlockedArgs<T> &a, cudaStream_t st, int num_sms, int scheme);
 

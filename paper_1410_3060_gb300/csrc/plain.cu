@@ -128,6 +128,7 @@ plain_sweep_kernel(const SweepArgs<T> a) {
                         } else if constexpr (KIND == J7_VAR) {
                             const T *Wp = a.W + idx;
                             const int64_t n = g.nfield, sy = g.sy, sz = g.sz;
+                            (void)sy; (void)sz;
                             if constexpr (!ADJ) {
                                 // Fig. 1c: W0 c + W1 x- + W2 x+ + W3 y- + W4 y+ + W5 z- + W6 z+
                                 v = Wp[0] * c;
@@ -185,11 +186,13 @@ plain_sweep_kernel(const SweepArgs<T> a) {
                         } else {  // W25_VAR, J25_VAR (Fig. 1d coefficient structure)
                             const T *Wp = a.W + idx;
                             const int64_t n = g.nfield, sy = g.sy, sz = g.sz;
+                            (void)sy; (void)sz;
                             T acc = Wp[0] * c;
                             if constexpr (WAVE) acc = fma(T(2), c, acc) - a.u_prev[idx];
 #pragma unroll
                             for (int r = 0; r < 4; ++r) {
                                 const int d = r + 1;
+                                (void)d;
                                 const T *Wx = Wp + (3 * r + 1) * n;
                                 const T *Wy = Wp + (3 * r + 2) * n;
                                 const T *Wz = Wp + (3 * r + 3) * n;

@@ -28,6 +28,11 @@ template <typename T>
 cudaError_t launch_misfit(const T *trace, const T *d, T *residual, int64_t n, double *partials,
                           int npartials, double *loss, cudaStream_t st);
 
+// out = alpha x + beta y over n elements
+template <typename T>
+cudaError_t launch_axpby(double alpha, const T *x, double beta, const T *y, T *out, int64_t n, int num_sms,
+                         cudaStream_t st);
+
 // FP64 / FP32 FMA throughput probe.
 cudaError_t run_fma_peak(int dtype, cudaStream_t st, double *flops, double *clock_hz);
 

@@ -16,7 +16,7 @@ from . import build as _build
 
 J7_CONST, J7_VAR, W25_CONST, W25_VAR, J25_VAR, W25_ALPHA = 1, 2, 3, 4, 5, 6
 F64, F32 = 0, 1
-OPT_TIME_BLOCK, OPT_SCHEME, OPT_SCRATCH_BYTES = 1, 2, 3
+OPT_TIME_BLOCK, OPT_SCHEME, OPT_SCRATCH_BYTES, OPT_GRAD_BATCH = 1, 2, 3, 4
 RADIUS = {J7_CONST: 1, J7_VAR: 1, W25_CONST: 4, W25_VAR: 4, J25_VAR: 4, W25_ALPHA: 4}
 NUM_ARRAYS = {J7_CONST: 0, J7_VAR: 7, W25_CONST: 0, W25_VAR: 13, J25_VAR: 13, W25_ALPHA: 1}
 NUM_WEIGHTS = {J7_CONST: 2, J7_VAR: 0, W25_CONST: 6, W25_VAR: 0, J25_VAR: 0, W25_ALPHA: 5}
@@ -25,8 +25,9 @@ SECOND_ORDER = {J7_CONST: False, J7_VAR: False, W25_CONST: True, W25_VAR: True, 
 
 # every symbol include/stencil.h declares
 EXPORTED = ("stencil_plan", "stencil_plan_set", "stencil_plan_get", "stencil_plan_destroy",
-            "stencil_forward", "stencil_adjoint", "stencil_misfit", "stencil_schedule",
-            "stencil_fma_peak", "stencil_strerror", "stencil_last_cuda_error")
+            "stencil_forward", "stencil_forward_states", "stencil_adjoint", "stencil_axpby",
+            "stencil_misfit", "stencil_schedule", "stencil_fma_peak", "stencil_strerror",
+            "stencil_last_cuda_error")
 
 _lock = threading.Lock()
 _lib = None
@@ -69,14 +70,18 @@ def lib():
             L.stencil_adjoint.argtypes = [vp, vp, vp, ctypes.POINTER(_Coeffs), i64, vp, ctypes.POINTER(vp), vp,
                                           i64, vp]
             L.stencil_misfit.argtypes = [vp, vp, vp, i64, vp, vp, vp]
-            L.stencil_schedule.argtypes = [i32, i64, i32, ctypes.POINTER(ctypes.c_int32), i64, ctypes.POINTER(i64)]
+            L.stencil_forward_states.argtypes = [vp, vp, vp, ctypes.POINTER(_Coeffs), i64, ctypes.POINTER(vp), vp,
+                                                 vp, i64]
+            L.stencil_axpby.argtypes = [vp, i64, ctypes.c_double, vp, ctypes.c_double, vp, vp, vp]
+            L.stencil_schedule.argtypes = [i32, i32, i64, i32, ctypes.POINTER(ctypes.c_int32), i64,
+                                           ctypes.POINTER(i64)]
             L.stencil_fma_peak.argtypes = [i32, vp, dp, dp]
             L.stencil_strerror.argtypes = [i32]
             L.stencil_strerror.restype = ctypes.c_char_p
             L.stencil_last_cuda_error.argtypes = []
             for fn in ("stencil_plan", "stencil_plan_set", "stencil_plan_get", "stencil_forward",
-                       "stencil_adjoint", "stencil_misfit", "stencil_schedule", "stencil_fma_peak",
-                       "stencil_last_cuda_error"):
+                       "stencil_forward_states", "stencil_adjoint", "stencil_axpby", "stencil_misfit",
+                       "stencil_schedule", "stencil_fma_peak", "stencil_last_cuda_error"):
                 getattr(L, fn).restype = i32
             _lib = L
     return _lib
@@ -98,12 +103,12 @@ def _ptr(t):
     return None if t is None else ctypes.c_void_p(t.data_ptr())
 
 
-def schedule(kind: int, T: int, b: int):
+def schedule(kind: int, T: int, b: int, dtype: int = F32):
     """The pass/copy program stencil_forward runs (host-only query)."""
     n = ctypes.c_int64(0)
-    _check("stencil_schedule", lib().stencil_schedule(kind, T, b, None, 0, ctypes.byref(n)))
+    _check("stencil_schedule", lib().stencil_schedule(kind, dtype, T, b, None, 0, ctypes.byref(n)))
     buf = (ctypes.c_int32 * (6 * max(1, n.value)))()
-    _check("stencil_schedule", lib().stencil_schedule(kind, T, b, buf, n.value, ctypes.byref(n)))
+    _check("stencil_schedule", lib().stencil_schedule(kind, dtype, T, b, buf, n.value, ctypes.byref(n)))
     return [tuple(buf[6 * i:6 * i + 6]) for i in range(n.value)]
 
 
@@ -182,6 +187,29 @@ class Plan:
         _check("stencil_forward", lib().stencil_forward(self._h, _ptr(u_prev), _ptr(u), ctypes.byref(c), int(T),
                                                         _stream_handle(stream), _ptr(trace), int(rcv_z)))
         del keep
+
+    def forward_states(self, u_prev, u, w=None, W=None, states=(), trace=None, rcv_z=0, stream=None):
+        """stencil_forward_states: states[t] <- u^{t+1} for t < len(states); inputs read only."""
+        T = len(states)
+        self._check_tensor(u_prev, self.padded_shape, "u_prev")
+        self._check_tensor(u, self.padded_shape, "u")
+        for s_ in states:
+            self._check_tensor(s_, self.padded_shape, "state")
+        if trace is not None:
+            self._check_tensor(trace, (T, self.n[1], self.n[0]), "trace")
+        arr = (ctypes.c_void_p * max(1, T))(*[s_.data_ptr() for s_ in states])
+        c, keep = self._coeffs(w, W)
+        _check("stencil_forward_states", lib().stencil_forward_states(
+            self._h, _ptr(u_prev), _ptr(u), ctypes.byref(c), int(T), ctypes.cast(arr, ctypes.POINTER(ctypes.c_void_p)),
+            _stream_handle(stream), _ptr(trace), int(rcv_z)))
+        del keep
+
+    def axpby(self, alpha, x, beta, y, out, stream=None):
+        """stencil_axpby: out = alpha x + beta y (same-shape tensors of the plan dtype)."""
+        for name, t in (("x", x), ("y", y), ("out", out)):
+            self._check_tensor(t, tuple(x.shape), name)
+        _check("stencil_axpby", lib().stencil_axpby(self._h, int(x.numel()), float(alpha), _ptr(x), float(beta), _ptr(y),
+                                                    _ptr(out), _stream_handle(stream)))
 
     def adjoint(self, lam_next, lam, w=None, W=None, T=1, fwd_states=None, residual=None, rcv_z=0, grad=None,
                 stream=None):

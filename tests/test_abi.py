@@ -44,8 +44,9 @@ def test_strerror_and_invalid_arguments(st):
     assert L.stencil_plan(ctypes.byref(h), 1, 0, 8, 8, 1, 0) == -1
     assert L.stencil_plan(ctypes.byref(h), 9, 8, 8, 8, 1, 0) == -1
     n = ctypes.c_int64()
-    assert L.stencil_schedule(1, -1, 1, None, 0, ctypes.byref(n)) == -1
-    assert L.stencil_schedule(1, 4, 0, None, 0, ctypes.byref(n)) == -1
+    assert L.stencil_schedule(1, 1, -1, 1, None, 0, ctypes.byref(n)) == -1
+    assert L.stencil_schedule(1, 1, 4, 0, None, 0, ctypes.byref(n)) == -1
+    assert L.stencil_schedule(1, 5, 4, 1, None, 0, ctypes.byref(n)) == -1
 
 
 def simulate(kind, T, ops, wave):
@@ -80,18 +81,19 @@ def simulate(kind, T, ops, wave):
 
 @pytest.mark.parametrize("kind", [1, 2, 3, 4, 5, 6])
 @pytest.mark.parametrize("b", [1, 2, 3, 4, 5, 8])
-def test_schedule_leaves_state_in_caller_buffers(st, kind, b):
+@pytest.mark.parametrize("dtype", [0, 1])
+def test_schedule_leaves_state_in_caller_buffers(st, kind, b, dtype):
     wave = st.SECOND_ORDER[kind]
     for T in range(0, 40):
-        ops = st.schedule(kind, T, b)
+        ops = st.schedule(kind, T, b, dtype)
         buf = simulate(kind, T, ops, wave)
         if T > 0:
             assert buf[1] == T and buf[0] == T - 1, (kind, T, b, ops)
             npass = sum(1 for o in ops if o[0] == 0)
             ncopy = sum(1 for o in ops if o[0] == 1)
-            # at most one extra pass beyond ceil(T / b) and at most 2 copies (T = 1)
-            import math
-            assert npass <= math.ceil(T / b) + 2
+            # passes never exceed T; at most 2 copies (T = 1)
+            assert npass <= T
+            assert all(o[1] == 1 or o[1] <= b for o in ops if o[0] == 0)
             assert ncopy <= (2 if T == 1 else 1)
         else:
             assert ops == []
