@@ -50,6 +50,8 @@ def parse():
     p.add_argument("--dtype", default="f64", choices=["f64", "f32"])
     p.add_argument("--time-block", type=int, default=None, help="levels per pass (default: library choice)")
     p.add_argument("--scheme", type=int, default=None, help="1 overlapped tiles, 2 diamond tiles in y")
+    p.add_argument("--variant", type=int, default=None, help="plain forward tile variant (0 = default)")
+    p.add_argument("--sweep", action="store_true", help="time every tile variant and block depth, one line each")
     p.add_argument("--no-variants", action="store_true")
     p.add_argument("--no-cpu", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
@@ -194,7 +196,7 @@ def max_over_ranks(torch, ws, v):
 
 
 def forward_case(torch, st, wl, kind, n, T, dtype, steps, warmup, ws, stream, time_block=None, e2e=False,
-                 wk=None, scheme=None):
+                 wk=None, scheme=None, variant=None):
     """Time `steps` calls of stencil_forward(T) on the workload; returns dict."""
     tdt = torch.float64 if dtype == st.F64 else torch.float32
     if wk is None:
@@ -204,6 +206,8 @@ def forward_case(torch, st, wl, kind, n, T, dtype, steps, warmup, ws, stream, ti
         plan.set(st.OPT_TIME_BLOCK, time_block)
     if scheme is not None:
         plan.set(st.OPT_SCHEME, scheme)
+    if variant is not None:
+        plan.set(st.OPT_VARIANT, variant)
     b = plan.get(st.OPT_TIME_BLOCK)
     up = torch.from_numpy(wk.u_prev).to("cuda", tdt)
     u = torch.from_numpy(wk.u).to("cuda", tdt)
@@ -219,7 +223,7 @@ def forward_case(torch, st, wl, kind, n, T, dtype, steps, warmup, ws, stream, ti
     lups = float(n) ** 3 * T
     passes = [o for o in st.schedule(kind, T, b, dtype) if o[0] == 0]
     res = {"kind": wl.KIND_NAMES[kind], "n": n, "T": T, "dtype": "f64" if dtype == st.F64 else "f32",
-           "scheme": plan.get(st.OPT_SCHEME),
+           "scheme": plan.get(st.OPT_SCHEME), "variant": plan.get(st.OPT_VARIANT),
            "time_block": b, "ms_per_step": ms / steps, "glups": lups * steps * ws / (ms * 1e-3) / 1e9,
            "launches_per_step": len(passes), "ms_per_launch": ms / steps / len(passes)}
     if e2e:
@@ -279,6 +283,29 @@ def roofline_of(pm, kind, dtype_name, n, res, peak_f64, hbm_peak, fp32_peak):
             "alu_view": {"achieved_tflops": flops_pass / t_pass / 1e12, "peak_tflops": fp32_peak / 1e12}}
 
 
+def run_sweep(args, torch, st, wl, pm, stream, ws, peak_f64, hbm_peak, peak_f32):
+    """Tuning sweep (the auto-tuning of tile parameters): every forward tile
+    variant and block depth of every kind and dtype at the given size; one
+    JSON line per case."""
+    n, T = args.n, args.T
+    for kind in (wl.J7_CONST, wl.J7_VAR, wl.W25_CONST, wl.W25_VAR):
+        wk = wl.make(kind, n, T, seed=0) if kind != wl.J7_VAR else wl.j7_var(n, T, seed=0)
+        for dtype in (st.F64, st.F32):
+            for v in (1, 2, 3, 4, 5):
+                r, _ = forward_case(torch, st, wl, kind, n, T, dtype, args.steps, 1, ws, stream, time_block=1,
+                                    wk=wk, variant=v)
+                r["roofline"] = roofline_of(pm, kind, r["dtype"], n, r, peak_f64, hbm_peak, peak_f32)
+                print(json.dumps({"sweep": r}), flush=True)
+            if dtype == st.F32:
+                for b in ((2, 4) if wl.RADIUS[kind] == 1 else (2,)):
+                    for sch in (1, 2):
+                        r, _ = forward_case(torch, st, wl, kind, n, T, dtype, args.steps, 1, ws, stream,
+                                            time_block=b, wk=wk, scheme=sch)
+                        r["roofline"] = roofline_of(pm, kind, r["dtype"], n, r, peak_f64, hbm_peak, peak_f32)
+                        print(json.dumps({"sweep": r}), flush=True)
+        del wk
+
+
 def run_ours(args):
     import torch
     ws, rank, local = dist_env()
@@ -304,12 +331,16 @@ def run_ours(args):
         os.path.join(ROOT, "MEASURED_PEAKS.json")) else {}
     hbm_peak = peaks.get("hbm_gbs", 6800.0)
 
+    if args.sweep:
+        run_sweep(args, torch, st, wl, pm, stream, ws, peak_f64, hbm_peak, peak_f32)
+        return
     dev_index = torch.cuda.current_device()
     sampler = ClockSampler(dev_index)
     wk = wl.make(kind, n, T, seed=0) if kind != wl.J7_VAR else wl.j7_var(n, T, seed=0)
     with sampler:
         main, _ = forward_case(torch, st, wl, kind, n, T, dtype, args.steps, args.warmup, ws, stream,
-                               time_block=args.time_block, e2e=not args.no_e2e, wk=wk, scheme=args.scheme)
+                               time_block=args.time_block, e2e=not args.no_e2e, wk=wk, scheme=args.scheme,
+                               variant=args.variant)
     clocks = sampler.summary()
     roofline = roofline_of(pm, kind, args.dtype, n, main, peak_f64, hbm_peak, peak_f32)
     roofline["kernel"] = ("plain_sweep_kernel" if main["time_block"] == 1 else "blocked_kernel (phase A + B)") + \

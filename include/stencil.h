@@ -90,7 +90,12 @@ enum stencil_option {
        registers before one read-modify-write of the gradient arrays
        (1..16, default 1).  G > 1 makes the plan hold G + 2 state fields of
        scratch in which stencil_adjoint keeps the adjoint levels of a batch. */
-    STENCIL_OPT_GRAD_BATCH = 4
+    STENCIL_OPT_GRAD_BATCH = 4,
+    /* Tile variant of the plain forward sweep (the tuning parameter of the
+       one-level kernel): 0 = measured default for the kind and dtype,
+       1..4 = asynchronously staged tiles of 32x8, 32x16, 32x16 (4 rows per
+       thread) and 64x8 columns, 5 = register-staged 2.5D kernel. */
+    STENCIL_OPT_VARIANT = 5
 };
 
 typedef struct stencil_plan_s *stencil_plan_t;
@@ -142,7 +147,8 @@ int stencil_forward(stencil_plan_t plan, void *u_prev, void *u, const stencil_co
  * of checkpointed differentiation): states is a host array of T device
  * pointers, states[t] receives u^{t+1}.  u_prev, u hold (u^{-1}, u^0) and
  * are only read.  trace / rcv_z as in stencil_forward.  The state arrays
- * must be distinct from each other and from the inputs. */
+ * must be distinct from each other and from the inputs, and their halos
+ * must be zero (only interiors are written). */
 int stencil_forward_states(stencil_plan_t plan, const void *u_prev, const void *u,
                            const stencil_coeffs_t *coeffs, int64_t T, void *const *states,
                            void *stream, void *trace, int64_t rcv_z);

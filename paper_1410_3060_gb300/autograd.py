@@ -102,7 +102,7 @@ class MisfitRunner:
         lam_next = torch.zeros(shape, device=dev, dtype=self.dtype)
         lam = torch.zeros(shape, device=dev, dtype=self.dtype)
         grad = torch.zeros((st.NUM_ARRAYS[self.kind],) + shape, device=dev, dtype=torch.float64)
-        bufs = [torch.empty(shape, device=dev, dtype=self.dtype) for _ in range(K)]
+        bufs = [torch.zeros(shape, device=dev, dtype=self.dtype) for _ in range(K)]  # zero halo
         top = True
         for c, cp, cu in reversed(state["ckpts"]):
             k = min(K, T - c)

@@ -28,6 +28,17 @@
 
 using namespace stc;
 
+namespace stc {
+// Default forward tile variant per kind and dtype (0 = FP64, 1 = FP32): the
+// variant measured fastest on GB300 at 512^3 (see the tile sweep in the
+// design notes).
+int default_variant(int kind, int dtype) {
+    (void)kind;
+    (void)dtype;
+    return 5;
+}
+}  // namespace stc
+
 namespace {
 
 thread_local int g_last_cuda_error = 0;
@@ -156,6 +167,7 @@ struct stencil_plan_s {
     void *scratch[2];
     void *bands[8];   // diamond edge bands of the blocked passes
     int nbands;
+    int variant;      // forward sweep tile variant (0 = default)
     int grad_batch;   // adjoint steps per FP64 gradient update
     void *gring[GRAD_MAX_STEPS + 2];  // adjoint levels of one gradient batch
     int ngring;
@@ -256,6 +268,7 @@ int run_program(stencil_plan_s *p, void *pair_p, void *pair_c, const stencil_coe
             a.rcv_z = (int)rcv_z;
             a.trace = (!adjoint && trace) ? (T *)trace + t * plane : nullptr;
             a.inject = (adjoint && inject) ? (const T *)inject + (nsteps - j) * plane : nullptr;
+            a.variant = p->variant;
             cudaError_t e = launch_plain<T>(p->kind, adjoint, a, st, p->num_sms);
             if (e != cudaSuccess) return cuda_fail(e);
         } else {
@@ -298,6 +311,7 @@ cudaError_t plain_step(stencil_plan_s *p, bool adjoint, const Scalars &s, const 
     a.rcv_z = (int)rcv_z;
     a.trace = trace;
     a.inject = inject;
+    a.variant = p->variant;
     return launch_plain<T>(p->kind, adjoint, a, st, p->num_sms);
 }
 
@@ -489,6 +503,10 @@ int stencil_plan_set(stencil_plan_t p, int option, int64_t value) {
         if (value < 0 || value > 2) return STENCIL_EINVAL;
         p->scheme = (int)value;
         return STENCIL_OK;
+    case STENCIL_OPT_VARIANT:
+        if (value < 0 || value > 5) return STENCIL_EINVAL;
+        p->variant = (int)value;
+        return STENCIL_OK;
     case STENCIL_OPT_GRAD_BATCH:
         if (value < 1 || value > GRAD_MAX_STEPS) return STENCIL_EINVAL;
         p->grad_batch = (int)value;
@@ -504,6 +522,7 @@ int stencil_plan_get(stencil_plan_t p, int option, int64_t *value) {
     case STENCIL_OPT_TIME_BLOCK: *value = effective_time_block(p); return STENCIL_OK;
     case STENCIL_OPT_SCHEME: *value = p->scheme; return STENCIL_OK;
     case STENCIL_OPT_GRAD_BATCH: *value = p->grad_batch; return STENCIL_OK;
+    case STENCIL_OPT_VARIANT: *value = p->variant ? p->variant : default_variant(p->kind, p->dtype); return STENCIL_OK;
     case STENCIL_OPT_SCRATCH_BYTES:
         *value = (int64_t)((p->scratch[0] ? 2 * p->field_bytes : 0) + (p->nbands + p->ngring) * p->field_bytes +
                            p->npartials * sizeof(double));

@@ -68,6 +68,7 @@ struct SweepArgs {
     Geom g;
     int rcv_z;           // interior z of the receiver plane (trace / inject)
     int zchunk;          // interior planes per CTA along z
+    int variant;         // forward tile variant (0 = default of the kind / dtype)
 };
 
 // ---- cp.async (LDGSTS) helpers: 4- or 8-byte element copies into shared

@@ -4,6 +4,9 @@
 
 namespace stc {
 
+// Default forward tile variant of a kind and dtype (0 = FP64, 1 = FP32).
+int default_variant(int kind, int dtype);
+
 // One plain sweep (one time level), forward or adjoint.
 template <typename T>
 cudaError_t launch_plain(int kind, bool adjoint, const SweepArgs<T> &a, cudaStream_t st, int num_sms);

@@ -1,0 +1,61 @@
+// plain_f64.cu -- double instantiations of the plain sweeps (plain_impl.cuh).
+#include "plain_impl.cuh"
+
+namespace stc {
+
+// Tile variants of the streaming forward kernel (TX threads in x, BY thread
+// rows, NR rows per thread, PD planes of prefetch), selected per plan
+// (STENCIL_OPT_VARIANT): 1 = 32x8x1/2, 2 = 32x8x2/2, 3 = 32x4x4/2,
+// 4 = 64x4x2/2, 5 = the register-staged plain kernel (plain_sweep_kernel).
+// 0 picks the default of the kind and dtype (measured best).
+template <typename T, int KIND>
+static cudaError_t launch_forward(const SweepArgs<T> &a, cudaStream_t st, int num_sms, int variant) {
+    constexpr int R = KindTraits<KIND>::R;
+    if (variant == 0) variant = default_variant(KIND, sizeof(T) == 8 ? 0 : 1);
+    switch (variant) {
+    case 1: return launch_stream<T, KIND, 32, 8, 1, 2>(a, st, num_sms);
+    case 2: return launch_stream<T, KIND, 32, 8, 2, 2>(a, st, num_sms);
+    case 3: return launch_stream<T, KIND, 32, 4, 4, 2>(a, st, num_sms);
+    case 4: return launch_stream<T, KIND, 64, 4, 2, 2>(a, st, num_sms);
+    case 5:
+        if constexpr (sizeof(T) == 4) {
+            if constexpr (R == 1) return launch_cfg<T, KIND, false, 64, 4, 8, 2>(a, st, num_sms);
+            else return launch_cfg<T, KIND, false, 32, 8, 4, 2>(a, st, num_sms);
+        } else {
+            if constexpr (R == 1) return launch_cfg<T, KIND, false, 32, 8, 4, 2>(a, st, num_sms);
+            else return launch_cfg<T, KIND, false, 32, 8, 2, 2>(a, st, num_sms);
+        }
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+template <typename T, int KIND>
+static cudaError_t launch_adjoint_var(const SweepArgs<T> &a, cudaStream_t st, int num_sms) {
+    constexpr int R = KindTraits<KIND>::R;
+    if constexpr (sizeof(T) == 4) {
+        if constexpr (R == 1) return launch_cfg<T, KIND, true, 64, 4, 8, 2>(a, st, num_sms);
+        else return launch_cfg<T, KIND, true, 32, 8, 4, 2>(a, st, num_sms);
+    } else {
+        if constexpr (R == 1) return launch_cfg<T, KIND, true, 32, 8, 4, 2>(a, st, num_sms);
+        else return launch_cfg<T, KIND, true, 32, 8, 2, 2>(a, st, num_sms);
+    }
+}
+
+template <typename T>
+cudaError_t launch_plain(int kind, bool adjoint, const SweepArgs<T> &a, cudaStream_t st, int num_sms) {
+    const int v = a.variant;
+    switch (kind) {
+    // the constant kinds are symmetric: their adjoint is the forward sweep
+    case J7_CONST: return launch_forward<T, J7_CONST>(a, st, num_sms, v);
+    case W25_CONST: return launch_forward<T, W25_CONST>(a, st, num_sms, v);
+    case J7_VAR: return adjoint ? launch_adjoint_var<T, J7_VAR>(a, st, num_sms) : launch_forward<T, J7_VAR>(a, st, num_sms, v);
+    case W25_VAR: return adjoint ? launch_adjoint_var<T, W25_VAR>(a, st, num_sms) : launch_forward<T, W25_VAR>(a, st, num_sms, v);
+    case J25_VAR: return adjoint ? launch_adjoint_var<T, J25_VAR>(a, st, num_sms) : launch_forward<T, J25_VAR>(a, st, num_sms, v);
+    case W25_ALPHA: return adjoint ? launch_adjoint_var<T, W25_ALPHA>(a, st, num_sms) : launch_forward<T, W25_ALPHA>(a, st, num_sms, v);
+    default: return cudaErrorInvalidValue;
+    }
+}
+
+template cudaError_t launch_plain<double>(int, bool, const SweepArgs<double> &, cudaStream_t, int);
+
+}  // namespace stc

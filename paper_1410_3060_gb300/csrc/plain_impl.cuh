@@ -1,4 +1,5 @@
-// plain.cu -- the plain one-step-per-sweep kernels (forward and adjoint).
+// plain_impl.cuh -- the plain one-step-per-sweep kernels (forward and adjoint);
+// instantiated per dtype by plain_f32.cu and plain_f64.cu.
 //
 // One launch applies one time level to the whole lattice: the naive update
 // order of the paper (Sect. 4.1, "naive" approach, Fig. 4a) with the spatial
@@ -22,6 +23,7 @@
 // (A^T y)(q) = sum_k A_k(q - o_k) y(q - o_k) reads each coefficient at the
 // source point of its term (a shifted, coalesced load); the constant kinds
 // are symmetric and reuse the forward update.
+#pragma once
 #include "common.cuh"
 #include "plain.cuh"
 
@@ -224,7 +226,226 @@ plain_sweep_kernel(const SweepArgs<T> a) {
     }
 }
 
-// ---------------------------------------------------------------- launch
+// ---------------------------------------------------------------- streaming forward
+// Forward sweep (also the adjoint of the symmetric constant kinds) with its
+// loads kept off the critical path:
+//  * the field plane q + PD (tile plus halo) is staged by cp.async in
+//    iteration q, into a ring of R + 2 + PD plane slots (a plane is read
+//    until R iterations after it arrives and may not be overwritten while a
+//    slower thread still reads it);
+//  * the per-point inputs of an output plane (u^{t-1} and the coefficients,
+//    no halo) are loaded into registers one iteration before they are used
+//    (double buffer), so their latency overlaps a full iteration.
+template <typename T, int KIND, int TX, int BY, int NR, int PD>
+__global__ void __launch_bounds__(TX * BY)
+plain_stream_kernel(const SweepArgs<T> a) {
+    constexpr int R = KindTraits<KIND>::R;
+    constexpr bool WAVE = KindTraits<KIND>::WAVE;
+    constexpr int NA = KindTraits<KIND>::NARR;
+    constexpr int TY = BY * NR;
+    constexpr int SW = TX + 2 * R;
+    constexpr int SH = TY + 2 * R;
+    constexpr int SPLANE = SW * SH;
+    constexpr int NSU = R + 2 + PD;
+    constexpr int NPO = (WAVE ? 1 : 0) + NA;    // per-point inputs: u_prev (wave), coefficients
+    constexpr int NPB = NPO > 0 ? NPO : 1;
+    constexpr int RING = 2 * R + 1;
+    constexpr int NT = TX * BY;
+
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T *su = reinterpret_cast<T *>(smem_raw);       // [NSU][SPLANE]
+
+    const Geom g = a.g;
+    const int tx = threadIdx.x, ty = threadIdx.y;
+    const int tid = ty * TX + tx;
+    const int x0 = blockIdx.x * TX;
+    const int y0 = blockIdx.y * TY;
+    const int z0 = blockIdx.z * a.zchunk;
+    const int z1 = min(z0 + a.zchunk, g.nz);
+    const int x = x0 + tx;
+    const bool xok = x < g.nx;
+    const int qs = z0 - R, qe = z1 + R;
+
+    auto issue = [&](int q) {
+        const T *src = a.u + (int64_t)(q + R) * g.sz;
+        T *dst = su + cmod(q - qs, NSU) * SPLANE;
+#pragma unroll 4
+        for (int e = tid; e < SPLANE; e += NT) {
+            const int r = e / SW, c = e - r * SW;
+            const int gy = y0 + r, gx = x0 + c;
+            if (gy < g.py && gx < g.px) cp_async<sizeof(T)>(dst + e, src + (int64_t)gy * g.sy + gx);
+        }
+    };
+    // per-point inputs of output plane z for this thread's rows
+    T pin[NPB][NR], pnx[NPB][NR];
+    auto load_point_inputs = [&](int z) {
+        if constexpr (NPO > 0) {
+            if (z < z0 || z >= z1) return;
+            const int64_t base = (int64_t)(z + R) * g.sz + (x + R);
+#pragma unroll
+            for (int jr = 0; jr < NR; ++jr) {
+                const int y = y0 + ty * NR + jr;
+                if (!xok || y >= g.ny) continue;
+                const int64_t off = base + (int64_t)(y + R) * g.sy;
+#pragma unroll
+                for (int t = 0; t < NPO; ++t) {
+                    const T *src = (WAVE && t == 0) ? a.u_prev + off
+                                                    : a.W + (int64_t)(t - (WAVE ? 1 : 0)) * g.nfield + off;
+                    pnx[t][jr] = *src;
+                }
+            }
+        }
+    };
+
+    T ring[RING][NR];
+#pragma unroll
+    for (int i = 0; i < RING; ++i)
+#pragma unroll
+        for (int jr = 0; jr < NR; ++jr) ring[i][jr] = T(0);
+#pragma unroll
+    for (int t = 0; t < NPB; ++t)
+#pragma unroll
+        for (int jr = 0; jr < NR; ++jr) { pin[t][jr] = T(0); pnx[t][jr] = T(0); }
+
+#pragma unroll
+    for (int i = 0; i < PD; ++i) {
+        if (qs + i < qe) issue(qs + i);
+        cp_async_commit();
+    }
+    load_point_inputs(z0);   // used in the first computing iteration (q = z0 + R)
+
+    const T s0 = T(a.s.c[0]), s1 = T(a.s.c[1]), s2 = T(a.s.c[2]);
+    const T s3 = T(a.s.c[3]), s4 = T(a.s.c[4]);
+    (void)s0; (void)s1; (void)s2; (void)s3; (void)s4;
+
+    for (int qb = qs; qb < qe; qb += RING) {
+        static_for<RING>([&](auto jj) {
+            constexpr int j = decltype(jj)::value;
+            const int q = qb + j;
+            if (q >= qe) return;
+            const int z = q - R;
+            if constexpr (NPO > 0) {
+                if (z >= z0) {
+                    // inputs of plane z arrived during the previous iteration; fetch plane z + 1
+#pragma unroll
+                    for (int t = 0; t < NPO; ++t)
+#pragma unroll
+                        for (int jr = 0; jr < NR; ++jr) pin[t][jr] = pnx[t][jr];
+                    load_point_inputs(z + 1);
+                }
+            }
+            if (q + PD < qe) issue(q + PD);
+            cp_async_commit();
+            cp_async_wait<PD>();
+            __syncthreads();
+
+            const T *sq = su + cmod(q - qs, NSU) * SPLANE;
+#pragma unroll
+            for (int jr = 0; jr < NR; ++jr) ring[j][jr] = sq[(ty * NR + jr + R) * SW + tx + R];
+
+            if (z < z0) return;
+            const T *sp = su + cmod(z - qs, NSU) * SPLANE;
+            constexpr int jc = cmod(j - R, RING);
+            const int64_t zrow = (int64_t)(z + R) * g.sz;
+#pragma unroll
+            for (int jr = 0; jr < NR; ++jr) {
+                const int y = y0 + ty * NR + jr;
+                if (!xok || y >= g.ny) continue;
+                const int lr = ty * NR + jr + R;
+                const int64_t idx = zrow + (int64_t)(y + R) * g.sy + (x + R);
+                const T c = ring[jc][jr];
+                T xn[R][2], yn[R][2], zn[R][2];
+#pragma unroll
+                for (int d = 1; d <= R; ++d) {
+                    xn[d - 1][0] = sp[lr * SW + tx + R - d];
+                    xn[d - 1][1] = sp[lr * SW + tx + R + d];
+                    if (jr - d >= 0) yn[d - 1][0] = ring[jc][jr - d];
+                    else yn[d - 1][0] = sp[(lr - d) * SW + tx + R];
+                    if (jr + d < NR) yn[d - 1][1] = ring[jc][jr + d];
+                    else yn[d - 1][1] = sp[(lr + d) * SW + tx + R];
+                    zn[d - 1][0] = ring[cmod(j - R - d, RING)][jr];
+                    zn[d - 1][1] = ring[cmod(j - R + d, RING)][jr];
+                }
+                constexpr int CO = WAVE ? 1 : 0;          // first coefficient slot
+                const T pv = WAVE ? pin[0][jr] : T(0);
+                (void)pv;
+                T v;
+                if constexpr (KIND == J7_CONST) {
+                    v = s0 * c + s1 * (((xn[0][0] + xn[0][1]) + (yn[0][0] + yn[0][1])) + (zn[0][0] + zn[0][1]));
+                } else if constexpr (KIND == J7_VAR) {
+                    v = pin[0][jr] * c;
+                    v = fma(pin[1][jr], xn[0][0], v);
+                    v = fma(pin[2][jr], xn[0][1], v);
+                    v = fma(pin[3][jr], yn[0][0], v);
+                    v = fma(pin[4][jr], yn[0][1], v);
+                    v = fma(pin[5][jr], zn[0][0], v);
+                    v = fma(pin[6][jr], zn[0][1], v);
+                } else if constexpr (KIND == W25_CONST) {
+                    T acc = s0 * c - pv;
+                    const T wr[4] = {s1, s2, s3, s4};
+#pragma unroll
+                    for (int d = 0; d < 4; ++d)
+                        acc = fma(wr[d], ((xn[d][0] + xn[d][1]) + (yn[d][0] + yn[d][1])) + (zn[d][0] + zn[d][1]), acc);
+                    v = acc;
+                } else if constexpr (KIND == W25_ALPHA) {
+                    const T wr[4] = {s1, s2, s3, s4};
+                    T s = s0 * c;
+#pragma unroll
+                    for (int d = 0; d < 4; ++d)
+                        s = fma(wr[d], ((xn[d][0] + xn[d][1]) + (yn[d][0] + yn[d][1])) + (zn[d][0] + zn[d][1]), s);
+                    v = fma(pin[CO][jr], s, T(2) * c - pv);
+                } else {  // W25_VAR, J25_VAR
+                    T acc = pin[CO][jr] * c;
+                    if constexpr (WAVE) acc = fma(T(2), c, acc) - pv;
+#pragma unroll
+                    for (int d = 0; d < 4; ++d) {
+                        acc = fma(pin[CO + 3 * d + 1][jr], xn[d][0] + xn[d][1], acc);
+                        acc = fma(pin[CO + 3 * d + 2][jr], yn[d][0] + yn[d][1], acc);
+                        acc = fma(pin[CO + 3 * d + 3][jr], zn[d][0] + zn[d][1], acc);
+                    }
+                    v = acc;
+                }
+                if (z == a.rcv_z) {
+                    const int64_t pidx = (int64_t)y * g.nx + x;
+                    if (a.inject) v += a.inject[pidx];
+                    if (a.trace) a.trace[pidx] = v;
+                }
+                a.out[idx] = v;
+            }
+        });
+    }
+}
+
+template <typename T, int KIND, int TX, int BY, int NR, int PD>
+constexpr size_t stream_smem() {
+    constexpr int R = KindTraits<KIND>::R;
+    constexpr int TY = BY * NR;
+    return sizeof(T) * (size_t)(R + 2 + PD) * (TX + 2 * R) * (TY + 2 * R);
+}
+
+// Grid: tiles of TX x TY columns times z chunks, chunks sized for about four
+// waves of CTAs and at least 8R planes (each chunk re-reads 2R planes).
+template <typename K>
+static cudaError_t launch_grid(K kern, size_t smem, int TX, int BY, int TY, int R, const SweepArgs<void> *,
+                               int nx, int ny, int nz, int num_sms, int *zchunk, dim3 *grid) {
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    int blocks_per_sm = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks_per_sm, kern, TX * BY, smem);
+    if (blocks_per_sm < 1) blocks_per_sm = 1;
+    const int gx = (nx + TX - 1) / TX, gy = (ny + TY - 1) / TY;
+    const int64_t want = (int64_t)num_sms * blocks_per_sm * 4;
+    const int64_t tiles = (int64_t)gx * gy;
+    int nzc = (int)((want + tiles - 1) / tiles);
+    const int min_chunk = 8 * R;
+    if (nzc < 1) nzc = 1;
+    if ((nz + nzc - 1) / nzc < min_chunk) nzc = (nz + min_chunk - 1) / min_chunk;
+    if (nzc < 1) nzc = 1;
+    *zchunk = (nz + nzc - 1) / nzc;
+    *grid = dim3(gx, gy, (nz + *zchunk - 1) / *zchunk);
+    return cudaSuccess;
+}
+
 template <typename T, int KIND, bool ADJ, int TX, int BY, int NR, int PD>
 static cudaError_t launch_cfg(const SweepArgs<T> &a, cudaStream_t st, int num_sms) {
     constexpr int R = KindTraits<KIND>::R;
@@ -232,58 +453,27 @@ static cudaError_t launch_cfg(const SweepArgs<T> &a, cudaStream_t st, int num_sm
     constexpr int NS = R + 2 + PD;
     constexpr size_t smem = sizeof(T) * (size_t)NS * (TX + 2 * R) * (TY + 2 * R);
     auto kern = plain_sweep_kernel<T, KIND, ADJ, TX, BY, NR, PD>;
-    static bool configured = false;  // per instantiation
-    if (!configured) {
-        cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        if (e != cudaSuccess) return e;
-        configured = true;
-    }
     SweepArgs<T> b = a;
-    const int gx = (a.g.nx + TX - 1) / TX, gy = (a.g.ny + TY - 1) / TY;
-    // z chunks: enough CTAs for several waves, chunks of at least 4R planes
-    int blocks_per_sm = 0;
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks_per_sm, kern, TX * BY, smem);
-    if (blocks_per_sm < 1) blocks_per_sm = 1;
-    const int64_t want = (int64_t)num_sms * blocks_per_sm * 4;
-    int64_t tiles = (int64_t)gx * gy;
-    int nzc = (int)((want + tiles - 1) / tiles);
-    const int min_chunk = 8 * R;
-    nzc = nzc < 1 ? 1 : nzc;
-    if ((a.g.nz + nzc - 1) / nzc < min_chunk) nzc = (a.g.nz + min_chunk - 1) / min_chunk;
-    if (nzc < 1) nzc = 1;
-    b.zchunk = (a.g.nz + nzc - 1) / nzc;
-    const int gz = (a.g.nz + b.zchunk - 1) / b.zchunk;
-    dim3 grid(gx, gy, gz), block(TX, BY, 1);
-    kern<<<grid, block, smem, st>>>(b);
+    dim3 grid;
+    cudaError_t e = launch_grid(kern, smem, TX, BY, TY, R, nullptr, a.g.nx, a.g.ny, a.g.nz, num_sms, &b.zchunk, &grid);
+    if (e != cudaSuccess) return e;
+    kern<<<grid, dim3(TX, BY, 1), smem, st>>>(b);
     return cudaGetLastError();
 }
 
-template <typename T, int KIND, bool ADJ>
-static cudaError_t launch_kind(const SweepArgs<T> &a, cudaStream_t st, int num_sms) {
+template <typename T, int KIND, int TX, int BY, int NR, int PD>
+static cudaError_t launch_stream(const SweepArgs<T> &a, cudaStream_t st, int num_sms) {
     constexpr int R = KindTraits<KIND>::R;
-    if constexpr (sizeof(T) == 4) {
-        if constexpr (R == 1) return launch_cfg<T, KIND, ADJ, 64, 4, 8, 2>(a, st, num_sms);
-        else return launch_cfg<T, KIND, ADJ, 32, 8, 4, 2>(a, st, num_sms);
-    } else {
-        if constexpr (R == 1) return launch_cfg<T, KIND, ADJ, 32, 8, 4, 2>(a, st, num_sms);
-        else return launch_cfg<T, KIND, ADJ, 32, 8, 2, 2>(a, st, num_sms);
-    }
+    constexpr int TY = BY * NR;
+    constexpr size_t smem = stream_smem<T, KIND, TX, BY, NR, PD>();
+    static_assert(smem <= 227 * 1024, "shared memory per CTA");
+    auto kern = plain_stream_kernel<T, KIND, TX, BY, NR, PD>;
+    SweepArgs<T> b = a;
+    dim3 grid;
+    cudaError_t e = launch_grid(kern, smem, TX, BY, TY, R, nullptr, a.g.nx, a.g.ny, a.g.nz, num_sms, &b.zchunk, &grid);
+    if (e != cudaSuccess) return e;
+    kern<<<grid, dim3(TX, BY, 1), smem, st>>>(b);
+    return cudaGetLastError();
 }
-
-template <typename T>
-cudaError_t launch_plain(int kind, bool adjoint, const SweepArgs<T> &a, cudaStream_t st, int num_sms) {
-    switch (kind) {
-    case J7_CONST: return launch_kind<T, J7_CONST, false>(a, st, num_sms);      // symmetric
-    case W25_CONST: return launch_kind<T, W25_CONST, false>(a, st, num_sms);    // symmetric
-    case J7_VAR: return adjoint ? launch_kind<T, J7_VAR, true>(a, st, num_sms) : launch_kind<T, J7_VAR, false>(a, st, num_sms);
-    case W25_VAR: return adjoint ? launch_kind<T, W25_VAR, true>(a, st, num_sms) : launch_kind<T, W25_VAR, false>(a, st, num_sms);
-    case J25_VAR: return adjoint ? launch_kind<T, J25_VAR, true>(a, st, num_sms) : launch_kind<T, J25_VAR, false>(a, st, num_sms);
-    case W25_ALPHA: return adjoint ? launch_kind<T, W25_ALPHA, true>(a, st, num_sms) : launch_kind<T, W25_ALPHA, false>(a, st, num_sms);
-    default: return cudaErrorInvalidValue;
-    }
-}
-
-template cudaError_t launch_plain<float>(int, bool, const SweepArgs<float> &, cudaStream_t, int);
-template cudaError_t launch_plain<double>(int, bool, const SweepArgs<double> &, cudaStream_t, int);
 
 }  // namespace stc

@@ -35,7 +35,7 @@ def test_forward_states(st, kind, dtype):
     n, T = (45, 38, 30), 5
     wk = wl.make(kind, n, T, seed=6)
     plan = st.Plan(kind, *n, dtype)
-    states = [torch.empty(plan.padded_shape, device="cuda", dtype=plan.torch_dtype()) for _ in range(T)]
+    states = [torch.zeros(plan.padded_shape, device="cuda", dtype=plan.torch_dtype()) for _ in range(T)]  # zero halo
     up, u = to_dev(wk.u_prev, dtype), to_dev(wk.u, dtype)
     plan.forward_states(up, u, wk.w, to_dev(wk.W, dtype), states)
     torch.cuda.synchronize()
@@ -152,7 +152,7 @@ def test_autograd_finite_differences_gpu(st, fwi48):
     assert abs(fd - an) <= 1e-6 * abs(an)
     for k in (0, 7):
         dw = torch.zeros_like(W)
-        dw[k] = to_dev(rand_interior(fw.n, R, rng), F64) * float(W[k].abs().max())
+        dw[k] = to_dev(rand_interior(fw.n, R, rng), F64) * float(W[k].detach().abs().max())
         h = 1e-6
         with torch.no_grad():
             fd = (run(u0, W + h * dw, dd).item() - run(u0, W - h * dw, dd).item()) / (2 * h)
