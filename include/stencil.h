@@ -93,8 +93,9 @@ enum stencil_option {
     STENCIL_OPT_GRAD_BATCH = 4,
     /* Tile variant of the plain forward sweep (the tuning parameter of the
        one-level kernel): 0 = measured default for the kind and dtype,
-       1..4 = asynchronously staged tiles of 32x8, 32x16, 32x16 (4 rows per
-       thread) and 64x8 columns, 5 = register-staged 2.5D kernel. */
+       1..4, 6, 7 = asynchronously staged tiles of 32x8, 32x16, 32x16 (4 rows
+       per thread), 64x8, 64x16 and 128x8 columns, 5 = register-staged 2.5D
+       kernel. */
     STENCIL_OPT_VARIANT = 5
 };
 

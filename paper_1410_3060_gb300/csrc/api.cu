@@ -504,7 +504,7 @@ int stencil_plan_set(stencil_plan_t p, int option, int64_t value) {
         p->scheme = (int)value;
         return STENCIL_OK;
     case STENCIL_OPT_VARIANT:
-        if (value < 0 || value > 5) return STENCIL_EINVAL;
+        if (value < 0 || value > 7) return STENCIL_EINVAL;
         p->variant = (int)value;
         return STENCIL_OK;
     case STENCIL_OPT_GRAD_BATCH:

@@ -227,15 +227,21 @@ plain_sweep_kernel(const SweepArgs<T> a) {
 }
 
 // ---------------------------------------------------------------- streaming forward
-// Forward sweep (also the adjoint of the symmetric constant kinds) with its
-// loads kept off the critical path:
+// One forward level (also the adjoint of the symmetric constant kinds).
+// The kernel is written for few instructions per lattice update:
 //  * the field plane q + PD (tile plus halo) is staged by cp.async in
-//    iteration q, into a ring of R + 2 + PD plane slots (a plane is read
-//    until R iterations after it arrives and may not be overwritten while a
-//    slower thread still reads it);
-//  * the per-point inputs of an output plane (u^{t-1} and the coefficients,
-//    no halo) are loaded into registers one iteration before they are used
-//    (double buffer), so their latency overlaps a full iteration.
+//    iteration q into a ring of NSU = M (2R+1) >= R + 2 + PD plane slots
+//    (a plane is read until R iterations after it arrives and must not be
+//    overwritten while a slower thread still reads it).  Each thread copies
+//    fixed rows (ty + i BY) of its column (and of one halo column when
+//    tx < 2R): in-plane offsets and bounds masks are computed once, a
+//    plane costs one 64-bit base per iteration;
+//  * slot numbers are compile-time constants within a block of 2R+1
+//    iterations (the z loop is unrolled by 2R+1, which also makes the z
+//    register ring static), plus the block's parity when M > 1;
+//  * the per-point inputs of an output plane (u^{t-1}, coefficients, no
+//    halo) are loaded into registers one iteration before use;
+//  * receiver trace / residual injection are handled once per plane.
 template <typename T, int KIND, int TX, int BY, int NR, int PD>
 __global__ void __launch_bounds__(TX * BY)
 plain_stream_kernel(const SweepArgs<T> a) {
@@ -246,53 +252,68 @@ plain_stream_kernel(const SweepArgs<T> a) {
     constexpr int SW = TX + 2 * R;
     constexpr int SH = TY + 2 * R;
     constexpr int SPLANE = SW * SH;
-    constexpr int NSU = R + 2 + PD;
-    constexpr int NPO = (WAVE ? 1 : 0) + NA;    // per-point inputs: u_prev (wave), coefficients
-    constexpr int NPB = NPO > 0 ? NPO : 1;
     constexpr int RING = 2 * R + 1;
-    constexpr int NT = TX * BY;
+    constexpr int M = (R + 2 + PD + RING - 1) / RING;
+    constexpr int NSU = M * RING;
+    constexpr int NLR = (SH + BY - 1) / BY;       // rows each thread copies
+    constexpr int NPO = (WAVE ? 1 : 0) + NA;
+    constexpr int NPB = NPO > 0 ? NPO : 1;
+    static_assert(2 * R <= TX, "halo columns are copied by the first 2R threads");
+    static_assert(NLR <= 32 && NR <= 32, "bit masks");
 
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    T *su = reinterpret_cast<T *>(smem_raw);       // [NSU][SPLANE]
+    T *su = reinterpret_cast<T *>(smem_raw);       // [NSU][SH][SW]
 
     const Geom g = a.g;
     const int tx = threadIdx.x, ty = threadIdx.y;
-    const int tid = ty * TX + tx;
     const int x0 = blockIdx.x * TX;
     const int y0 = blockIdx.y * TY;
     const int z0 = blockIdx.z * a.zchunk;
     const int z1 = min(z0 + a.zchunk, g.nz);
     const int x = x0 + tx;
-    const bool xok = x < g.nx;
     const int qs = z0 - R, qe = z1 + R;
+    const int sy = (int)g.sy;
 
-    auto issue = [&](int q) {
-        const T *src = a.u + (int64_t)(q + R) * g.sz;
-        T *dst = su + cmod(q - qs, NSU) * SPLANE;
-#pragma unroll 4
-        for (int e = tid; e < SPLANE; e += NT) {
-            const int r = e / SW, c = e - r * SW;
-            const int gy = y0 + r, gx = x0 + c;
-            if (gy < g.py && gx < g.px) cp_async<sizeof(T)>(dst + e, src + (int64_t)gy * g.sy + gx);
+    // ---- copy plan of this thread (padded coordinates, in-plane offsets)
+    const int goff0 = (y0 + ty) * sy + x0 + tx;
+    uint32_t mmain = 0, mhalo = 0;
+#pragma unroll
+    for (int i = 0; i < NLR; ++i) {
+        const int r = ty + i * BY, gy = y0 + r;
+        if (r < SH && gy < g.py) {
+            if (x0 + tx < g.px) mmain |= 1u << i;
+            if (tx < 2 * R && x0 + TX + tx < g.px) mhalo |= 1u << i;
+        }
+    }
+    auto issue = [&](int q, T *dst) {
+        const T *pb = a.u + (int64_t)(q + R) * g.sz + goff0;
+        T *d = dst + ty * SW + tx;
+#pragma unroll
+        for (int i = 0; i < NLR; ++i) {
+            if (mmain & (1u << i)) cp_async<sizeof(T)>(d + i * BY * SW, pb + i * BY * sy);
+            if (mhalo & (1u << i)) cp_async<sizeof(T)>(d + i * BY * SW + TX, pb + i * BY * sy + TX);
         }
     };
-    // per-point inputs of output plane z for this thread's rows
+
+    // ---- this thread's output rows
+    const int pofs0 = (y0 + ty * NR + R) * sy + x + R;     // in-plane offset of row 0
+    uint32_t rowok = 0;
+#pragma unroll
+    for (int jr = 0; jr < NR; ++jr)
+        if (x < g.nx && y0 + ty * NR + jr < g.ny) rowok |= 1u << jr;
+
     T pin[NPB][NR], pnx[NPB][NR];
     auto load_point_inputs = [&](int z) {
         if constexpr (NPO > 0) {
-            if (z < z0 || z >= z1) return;
-            const int64_t base = (int64_t)(z + R) * g.sz + (x + R);
+            if (z >= z1) return;
+            const int64_t base = (int64_t)(z + R) * g.sz + pofs0;
 #pragma unroll
             for (int jr = 0; jr < NR; ++jr) {
-                const int y = y0 + ty * NR + jr;
-                if (!xok || y >= g.ny) continue;
-                const int64_t off = base + (int64_t)(y + R) * g.sy;
+                if (!(rowok & (1u << jr))) continue;
+                const int64_t off = base + jr * sy;
+                if constexpr (WAVE) pnx[0][jr] = a.u_prev[off];
 #pragma unroll
-                for (int t = 0; t < NPO; ++t) {
-                    const T *src = (WAVE && t == 0) ? a.u_prev + off
-                                                    : a.W + (int64_t)(t - (WAVE ? 1 : 0)) * g.nfield + off;
-                    pnx[t][jr] = *src;
-                }
+                for (int t = 0; t < NA; ++t) pnx[(WAVE ? 1 : 0) + t][jr] = a.W[off + t * g.nfield];
             }
         }
     };
@@ -307,18 +328,21 @@ plain_stream_kernel(const SweepArgs<T> a) {
 #pragma unroll
         for (int jr = 0; jr < NR; ++jr) { pin[t][jr] = T(0); pnx[t][jr] = T(0); }
 
+    // prologue: planes qs .. qs+PD-1 into slots 0 .. PD-1
 #pragma unroll
     for (int i = 0; i < PD; ++i) {
-        if (qs + i < qe) issue(qs + i);
+        if (qs + i < qe) issue(qs + i, su + i * SPLANE);
         cp_async_commit();
     }
-    load_point_inputs(z0);   // used in the first computing iteration (q = z0 + R)
+    load_point_inputs(z0);
 
     const T s0 = T(a.s.c[0]), s1 = T(a.s.c[1]), s2 = T(a.s.c[2]);
     const T s3 = T(a.s.c[3]), s4 = T(a.s.c[4]);
     (void)s0; (void)s1; (void)s2; (void)s3; (void)s4;
 
+    int blk = 0;   // (qb - qs) / RING modulo M
     for (int qb = qs; qb < qe; qb += RING) {
+        T *const slots = su + blk * RING * SPLANE;          // slot of the block's first plane
         static_for<RING>([&](auto jj) {
             constexpr int j = decltype(jj)::value;
             const int q = qb + j;
@@ -326,7 +350,6 @@ plain_stream_kernel(const SweepArgs<T> a) {
             const int z = q - R;
             if constexpr (NPO > 0) {
                 if (z >= z0) {
-                    // inputs of plane z arrived during the previous iteration; fetch plane z + 1
 #pragma unroll
                     for (int t = 0; t < NPO; ++t)
 #pragma unroll
@@ -334,39 +357,44 @@ plain_stream_kernel(const SweepArgs<T> a) {
                     load_point_inputs(z + 1);
                 }
             }
-            if (q + PD < qe) issue(q + PD);
+            // slot of plane q + PD
+            {
+                T *dst = slots + (j + PD) * SPLANE;
+                if (j + PD >= NSU - blk * RING) dst -= NSU * SPLANE;
+                if (q + PD < qe) issue(q + PD, dst);
+            }
             cp_async_commit();
             cp_async_wait<PD>();
             __syncthreads();
 
-            const T *sq = su + cmod(q - qs, NSU) * SPLANE;
+            const T *sq = slots + j * SPLANE;
 #pragma unroll
             for (int jr = 0; jr < NR; ++jr) ring[j][jr] = sq[(ty * NR + jr + R) * SW + tx + R];
-
             if (z < z0) return;
-            const T *sp = su + cmod(z - qs, NSU) * SPLANE;
+
+            const T *sp = slots + (j - R) * SPLANE;               // plane z = q - R
+            if (j - R < -blk * RING) sp += NSU * SPLANE;
             constexpr int jc = cmod(j - R, RING);
-            const int64_t zrow = (int64_t)(z + R) * g.sz;
+            T *outp = a.out + (int64_t)(z + R) * g.sz + pofs0;
+            const T *rowp = sp + (ty * NR + R) * SW + tx + R;   // this thread's first row, centre column
+            T res[NR];
 #pragma unroll
             for (int jr = 0; jr < NR; ++jr) {
-                const int y = y0 + ty * NR + jr;
-                if (!xok || y >= g.ny) continue;
-                const int lr = ty * NR + jr + R;
-                const int64_t idx = zrow + (int64_t)(y + R) * g.sy + (x + R);
+                const T *cp = rowp + jr * SW;
                 const T c = ring[jc][jr];
                 T xn[R][2], yn[R][2], zn[R][2];
 #pragma unroll
                 for (int d = 1; d <= R; ++d) {
-                    xn[d - 1][0] = sp[lr * SW + tx + R - d];
-                    xn[d - 1][1] = sp[lr * SW + tx + R + d];
+                    xn[d - 1][0] = cp[-d];
+                    xn[d - 1][1] = cp[d];
                     if (jr - d >= 0) yn[d - 1][0] = ring[jc][jr - d];
-                    else yn[d - 1][0] = sp[(lr - d) * SW + tx + R];
+                    else yn[d - 1][0] = cp[-d * SW];
                     if (jr + d < NR) yn[d - 1][1] = ring[jc][jr + d];
-                    else yn[d - 1][1] = sp[(lr + d) * SW + tx + R];
+                    else yn[d - 1][1] = cp[d * SW];
                     zn[d - 1][0] = ring[cmod(j - R - d, RING)][jr];
                     zn[d - 1][1] = ring[cmod(j - R + d, RING)][jr];
                 }
-                constexpr int CO = WAVE ? 1 : 0;          // first coefficient slot
+                constexpr int CO = WAVE ? 1 : 0;
                 const T pv = WAVE ? pin[0][jr] : T(0);
                 (void)pv;
                 T v;
@@ -405,14 +433,22 @@ plain_stream_kernel(const SweepArgs<T> a) {
                     }
                     v = acc;
                 }
-                if (z == a.rcv_z) {
-                    const int64_t pidx = (int64_t)y * g.nx + x;
-                    if (a.inject) v += a.inject[pidx];
-                    if (a.trace) a.trace[pidx] = v;
-                }
-                a.out[idx] = v;
+                res[jr] = v;
             }
+            if (z == a.rcv_z) {
+                const int64_t pl = (int64_t)(y0 + ty * NR) * g.nx + x;
+#pragma unroll
+                for (int jr = 0; jr < NR; ++jr) {
+                    if (!(rowok & (1u << jr))) continue;
+                    if (a.inject) res[jr] += a.inject[pl + jr * g.nx];
+                    if (a.trace) a.trace[pl + jr * g.nx] = res[jr];
+                }
+            }
+#pragma unroll
+            for (int jr = 0; jr < NR; ++jr)
+                if (rowok & (1u << jr)) outp[jr * sy] = res[jr];
         });
+        blk = (blk + 1 == M) ? 0 : blk + 1;
     }
 }
 
@@ -420,7 +456,9 @@ template <typename T, int KIND, int TX, int BY, int NR, int PD>
 constexpr size_t stream_smem() {
     constexpr int R = KindTraits<KIND>::R;
     constexpr int TY = BY * NR;
-    return sizeof(T) * (size_t)(R + 2 + PD) * (TX + 2 * R) * (TY + 2 * R);
+    constexpr int RING = 2 * R + 1;
+    constexpr int M = (R + 2 + PD + RING - 1) / RING;
+    return sizeof(T) * (size_t)(M * RING) * (TX + 2 * R) * (TY + 2 * R);
 }
 
 // Grid: tiles of TX x TY columns times z chunks, chunks sized for about four

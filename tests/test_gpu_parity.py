@@ -157,3 +157,29 @@ def test_fma_peak_probe(st):
     f64, clk = st.fma_peak(0)
     f32, _ = st.fma_peak(1)
     assert f64 > 1e11 and f32 > 1e13 and clk > 5e8
+
+
+@pytest.mark.parametrize("kind", KINDS)
+@pytest.mark.parametrize("dtype", [F64, F32])
+@pytest.mark.parametrize("variant", [1, 2, 3, 4, 5, 6, 7])
+def test_forward_tile_variants(st, kind, dtype, variant):
+    """Every forward tile variant against the oracle (ragged tiles in x, y, z)."""
+    shape, T = (150, 45, 40), 3
+    wk = wl.make(kind, shape, T, seed=8)
+    rz = 11
+    op, ou, otr = oracle_forward(wk, T, rcv_z=rz)
+    import gpu_util
+    torch = gpu_util.torch_mod()
+    nx, ny, nz = shape
+    plan = st.Plan(kind, nx, ny, nz, dtype)
+    plan.set(st.OPT_VARIANT, variant)
+    assert plan.get(st.OPT_VARIANT) == variant
+    up, u = to_dev(wk.u_prev, dtype), to_dev(wk.u, dtype)
+    tr = torch.zeros((T, ny, nx), device="cuda", dtype=up.dtype)
+    plan.forward(up, u, wk.w, to_dev(wk.W, dtype) if wk.W is not None else None, T, trace=tr, rcv_z=rz)
+    torch.cuda.synchronize()
+    tol = 1e-12 if dtype == F64 else fp32_bound(kind, T, wk.R)
+    assert normwise_err(to_np(u), ou) <= tol
+    assert normwise_err(to_np(up), op) <= tol
+    assert normwise_err(to_np(tr), otr) <= tol
+    plan.close()
