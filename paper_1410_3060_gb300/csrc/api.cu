@@ -33,9 +33,18 @@ namespace stc {
 // variant measured fastest on GB300 at 512^3 (see the tile sweep in the
 // design notes).
 int default_variant(int kind, int dtype) {
-    (void)kind;
-    (void)dtype;
-    return 5;
+    if (dtype == 1) {  // FP32 (sweep at 512^3, T = 8)
+        switch (kind) {
+        case J7_CONST: return 7;               // 128 x 8 tiles
+        case J7_VAR: return 3;                 // 32 x 16, 4 rows per thread
+        case W25_CONST: case W25_ALPHA: return 3;
+        default: return 4;                     // W25_VAR, J25_VAR: 64 x 8
+        }
+    }
+    switch (kind) {    // FP64 (bound by the FP64 pipe)
+    case J7_CONST: return 3;
+    default: return 1;                         // 32 x 8, one row per thread
+    }
 }
 }  // namespace stc
 
