@@ -189,6 +189,31 @@ int stencil_axpby(stencil_plan_t plan, int64_t n, double alpha, const void *x, d
 int stencil_misfit(stencil_plan_t plan, const void *trace, const void *d, int64_t T, void *residual,
                    double *loss, void *stream);
 
+/* Receiver misfit that allocates nothing: the same result as
+ * stencil_misfit (residual = trace - d, *loss = 0.5 * sum (trace - d)^2 in
+ * FP64, fixed summation order), without a plan.  The paper has no
+ * counterpart; this entry exists for callers that cannot allocate device
+ * memory themselves -- code embedded in an application whose device memory
+ * is owned by its own allocator (raw cudaMalloc/cudaFree are not allowed or
+ * would fragment its pool), or latency-critical loops where a device
+ * allocation, which may synchronise the device, is not acceptable.
+ *  dtype: STENCIL_F64 or STENCIL_F32; trace, d, residual: device arrays of
+ *         n elements of that type (caller-owned); loss: device FP64.
+ *  n must be <= STENCIL_MISFIT_STATIC_MAX_ELEMS, else STENCIL_EINVAL (no
+ *  work is enqueued).
+ * Scratch: the FP64 partial sums live in a static device array of the
+ * library (64 KiB, one partial per 2048 elements, at most 8192), which every
+ * GPU that loads the library holds until the process exits.  The first call
+ * on a device looks up that array's device address (cudaGetSymbolAddress,
+ * with the device current); make that first call before any stream capture.
+ * All calls share the array: calls that may overlap on the GPU (different
+ * streams, or other threads) race and must be serialised by the caller.
+ * Every entry a call reads is written by the same call, so nothing carries
+ * over between calls.  Calls no cudaMalloc / cudaFree. */
+#define STENCIL_MISFIT_STATIC_MAX_ELEMS ((int64_t)8192 * 2048)
+int stencil_misfit_static(int dtype, const void *trace, const void *d, int64_t n, void *residual,
+                          double *loss, void *stream);
+
 /* Host-only: the program of passes and copies that stencil_forward (and,
  * with the same rules, stencil_adjoint) runs for T steps of `kind` in
  * `dtype` with temporal block depth b (b >= 1; 1 = plain sweeps; a depth

@@ -654,6 +654,16 @@ int stencil_misfit(stencil_plan_t p, const void *trace, const void *d, int64_t T
     return e == cudaSuccess ? STENCIL_OK : cuda_fail(e);
 }
 
+int stencil_misfit_static(int dtype, const void *trace, const void *d, int64_t n, void *residual, double *loss,
+                          void *stream) {
+    if ((dtype != STENCIL_F64 && dtype != STENCIL_F32) || !trace || !d || !residual || !loss || n < 0)
+        return STENCIL_EINVAL;
+    if (n > STENCIL_MISFIT_STATIC_MAX_ELEMS) return STENCIL_EINVAL;  // needs more than the static partial sums
+    static_assert(STENCIL_MISFIT_STATIC_MAX_ELEMS == MISFIT_STATIC_MAX_ELEMS, "header limit matches the array");
+    cudaError_t e = misfit_static(dtype, trace, d, n, residual, loss, (cudaStream_t)stream);
+    return e == cudaSuccess ? STENCIL_OK : cuda_fail(e);
+}
+
 int stencil_schedule(int kind, int dtype, int64_t T, int b, int32_t *ops, int64_t max_ops, int64_t *n_ops) {
     if (kind_radius(kind) < 0 || (dtype != STENCIL_F64 && dtype != STENCIL_F32) || T < 0 || b < 1 || !n_ops ||
         (max_ops > 0 && !ops))

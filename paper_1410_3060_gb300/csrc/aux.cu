@@ -11,6 +11,7 @@
 // The batch sum is kept in FP64 registers and added to the FP64 gradient
 // arrays once per batch.
 #include <algorithm>
+#include <mutex>
 
 #include "plain.cuh"
 
@@ -138,6 +139,46 @@ template cudaError_t launch_axpby<float>(double, const float *, double, const fl
                                          cudaStream_t);
 template cudaError_t launch_axpby<double>(double, const double *, double, const double *, double *, int64_t, int,
                                           cudaStream_t);
+// ---- allocation-free misfit: the partial sums live in a library-owned
+// static device array instead of plan scratch.  The array's name is only a
+// host-side stand-in; its device address is looked up once per device
+// (with that device current) and cached.
+static __device__ __align__(256) double g_misfit_partials[MISFIT_STATIC_MAX_PARTIALS];
+
+namespace {
+std::mutex g_static_mtx;
+constexpr int kMaxDevices = 64;
+double *g_static_addr[kMaxDevices] = {};
+}  // namespace
+
+cudaError_t misfit_static(int dtype, const void *trace, const void *d, int64_t n, void *residual, double *loss,
+                          cudaStream_t st) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+    double *partials = nullptr;
+    {
+        std::lock_guard<std::mutex> lock(g_static_mtx);
+        if (!g_static_addr[dev]) {
+            void *ptr = nullptr;
+            e = cudaGetSymbolAddress(&ptr, g_misfit_partials);
+            if (e != cudaSuccess) return e;
+            g_static_addr[dev] = static_cast<double *>(ptr);
+        }
+        partials = g_static_addr[dev];
+    }
+    // one partial sum per MISFIT_STATIC_ELEMS_PER_PARTIAL elements; every
+    // partial the final sum reads is written by this call, so nothing has
+    // to be cleared between calls
+    const int np = (int)std::max<int64_t>(1, (n + MISFIT_STATIC_ELEMS_PER_PARTIAL - 1) / MISFIT_STATIC_ELEMS_PER_PARTIAL);
+    if (dtype == 0)
+        return launch_misfit<double>((const double *)trace, (const double *)d, (double *)residual, n, partials, np,
+                                     loss, st);
+    return launch_misfit<float>((const float *)trace, (const float *)d, (float *)residual, n, partials, np, loss,
+                                st);
+}
+
 template cudaError_t launch_grad<float>(int, const GradArgs<float> &, cudaStream_t);
 template cudaError_t launch_grad<double>(int, const GradArgs<double> &, cudaStream_t);
 template cudaError_t launch_misfit<float>(const float *, const float *, float *, int64_t, double *, int, double *,

@@ -31,6 +31,13 @@ template <typename T>
 cudaError_t launch_misfit(const T *trace, const T *d, T *residual, int64_t n, double *partials,
                           int npartials, double *loss, cudaStream_t st);
 
+// Misfit with its partial sums in a static device array (no allocation).
+constexpr int MISFIT_STATIC_MAX_PARTIALS = 8192;          // 64 KiB of FP64
+constexpr int64_t MISFIT_STATIC_ELEMS_PER_PARTIAL = 2048;
+constexpr int64_t MISFIT_STATIC_MAX_ELEMS = (int64_t)MISFIT_STATIC_MAX_PARTIALS * MISFIT_STATIC_ELEMS_PER_PARTIAL;
+cudaError_t misfit_static(int dtype, const void *trace, const void *d, int64_t n, void *residual, double *loss,
+                          cudaStream_t st);
+
 // out = alpha x + beta y over n elements
 template <typename T>
 cudaError_t launch_axpby(double alpha, const T *x, double beta, const T *y, T *out, int64_t n, int num_sms,

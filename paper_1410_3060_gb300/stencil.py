@@ -26,8 +26,9 @@ SECOND_ORDER = {J7_CONST: False, J7_VAR: False, W25_CONST: True, W25_VAR: True, 
 # every symbol include/stencil.h declares
 EXPORTED = ("stencil_plan", "stencil_plan_set", "stencil_plan_get", "stencil_plan_destroy",
             "stencil_forward", "stencil_forward_states", "stencil_adjoint", "stencil_axpby",
-            "stencil_misfit", "stencil_schedule", "stencil_fma_peak", "stencil_strerror",
-            "stencil_last_cuda_error")
+            "stencil_misfit", "stencil_misfit_static", "stencil_schedule", "stencil_fma_peak",
+            "stencil_strerror", "stencil_last_cuda_error")
+MISFIT_STATIC_MAX_ELEMS = 8192 * 2048
 
 _lock = threading.Lock()
 _lib = None
@@ -72,6 +73,7 @@ def lib():
             L.stencil_misfit.argtypes = [vp, vp, vp, i64, vp, vp, vp]
             L.stencil_forward_states.argtypes = [vp, vp, vp, ctypes.POINTER(_Coeffs), i64, ctypes.POINTER(vp), vp,
                                                  vp, i64]
+            L.stencil_misfit_static.argtypes = [i32, vp, vp, i64, vp, vp, vp]
             L.stencil_axpby.argtypes = [vp, i64, ctypes.c_double, vp, ctypes.c_double, vp, vp, vp]
             L.stencil_schedule.argtypes = [i32, i32, i64, i32, ctypes.POINTER(ctypes.c_int32), i64,
                                            ctypes.POINTER(i64)]
@@ -81,6 +83,7 @@ def lib():
             L.stencil_last_cuda_error.argtypes = []
             for fn in ("stencil_plan", "stencil_plan_set", "stencil_plan_get", "stencil_forward",
                        "stencil_forward_states", "stencil_adjoint", "stencil_axpby", "stencil_misfit",
+                       "stencil_misfit_static",
                        "stencil_schedule", "stencil_fma_peak", "stencil_last_cuda_error"):
                 getattr(L, fn).restype = i32
             _lib = L
@@ -110,6 +113,20 @@ def schedule(kind: int, T: int, b: int, dtype: int = F32):
     buf = (ctypes.c_int32 * (6 * max(1, n.value)))()
     _check("stencil_schedule", lib().stencil_schedule(kind, dtype, T, b, buf, n.value, ctypes.byref(n)))
     return [tuple(buf[6 * i:6 * i + 6]) for i in range(n.value)]
+
+
+def misfit_static(trace, d, residual, loss, stream=None):
+    """stencil_misfit_static: the receiver misfit without a plan or any device
+    allocation (partial sums in the library's static device array)."""
+    import torch
+    dtype = F64 if trace.dtype == torch.float64 else F32
+    for name, t in (("d", d), ("residual", residual)):
+        if t.dtype != trace.dtype or t.shape != trace.shape or not t.is_contiguous() or not t.is_cuda:
+            raise ValueError(f"{name}: expected a contiguous CUDA tensor like trace")
+    if not trace.is_contiguous() or not trace.is_cuda or loss.dtype != torch.float64 or not loss.is_cuda:
+        raise ValueError("trace: contiguous CUDA tensor; loss: CUDA float64")
+    _check("stencil_misfit_static", lib().stencil_misfit_static(dtype, _ptr(trace), _ptr(d), int(trace.numel()),
+                                                                _ptr(residual), _ptr(loss), _stream_handle(stream)))
 
 
 def fma_peak(dtype: int, stream=None):
