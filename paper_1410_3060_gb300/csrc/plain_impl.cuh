@@ -3,7 +3,7 @@
 //
 // One launch applies one time level to the whole lattice: the naive update
 // order of the paper (Sect. 4.1, "naive" approach, Fig. 4a) with the spatial
-// blocking of Sect. 3 mapped to a GPU 2.5D scheme:
+// blocking of Sect. 3.3 mapped to a GPU 2.5D scheme:
 //
 //  * a CTA owns a TX x TY tile of (x, y) columns and marches along z through
 //    a chunk of planes;

@@ -3,12 +3,11 @@ CPU code-balance and cache-block-size models, and roofline arithmetic.
 
 Paper models (arXiv 1410.3060):
 
-* code balance B_C of the naive sweep in bytes/LUP (Sect. 3, "Roofline
-  model"), with the CPU write-allocate transfer counted unless non-temporal
+* code balance B_C of the naive sweep in bytes/LUP (Sect. 3.3), with the CPU write-allocate transfer counted unless non-temporal
   stores are used;
-* roofline P = b_S / B_C (Sect. 3);
-* cache block size of one wavefront-diamond tile (Sect. 4.3, Eqs. for R = 1
-  and general R), with W_w the wavefront width.
+* roofline P = b_S / B_C (Sect. 3.3);
+* cache block size of one wavefront-diamond tile (Sect. 5.3, the equations
+  for R = 1 and general R), with W_w the wavefront width.
 
 GPU model: a GPU store does not allocate, so the plain one-step sweep moves
 exactly one read of every input stream and one write of the output per
@@ -31,7 +30,7 @@ FP_INSTR_PER_LUP = {J7_CONST: 7, J7_VAR: 7, W25_CONST: 25, W25_VAR: 26, J25_VAR:
 
 
 def cpu_code_balance(kind: int, word: int = 8, write_allocate: bool = True) -> float:
-    """Minimum bytes/LUP of the naive sweep on a CPU (paper Sect. 3).
+    """Minimum bytes/LUP of the naive sweep on a CPU (paper Sect. 3.3).
 
     First-order kinds read u and the coefficient streams and write u'; the
     write to a separate array costs a write-allocate read unless streaming
@@ -56,17 +55,17 @@ def gpu_bytes_per_pass(kind: int, word: int, n_points: int, trace_plane: int = 0
 
 
 def roofline(bandwidth: float, code_balance: float) -> float:
-    """P = b_S / B_C (updates/s for bandwidth in bytes/s)."""
+    """P = b_S / B_C (updates/s for bandwidth in bytes/s), Sect. 3.3."""
     return bandwidth / code_balance
 
 
 def wavefront_width(Dw: int, NF: int, R: int = 1) -> int:
-    """W_w = D_w - 2R + N_F + 1 (for R = 1: D_w + N_F - 1), paper Sect. 4.3."""
+    """W_w = D_w - 2R + N_F + 1 (for R = 1: D_w + N_F - 1), paper Sect. 5.3."""
     return Dw - 2 * R + NF + 1
 
 
 def cache_block_bytes(Dw: int, NF: int, Nxb: float, ND: int = 1, R: int = 1) -> float:
-    """Cache block size of one extruded diamond, paper Sect. 4.3:
+    """Cache block size of one extruded diamond, paper Sect. 5.3:
     N_xb [N_D D_w (D_w/2 - R + N_F + 1) + 2R (D_w + W_w)]; for R = 1 this is
     N_xb [N_D (D_w^2/2 + D_w N_F) + 2 (D_w + W_w)]."""
     Ww = wavefront_width(Dw, NF, R)
