@@ -14,7 +14,7 @@
 //    registers).  The x/y neighbours of level k's centre plane are exchanged
 //    through one shared-memory plane per level (double buffered: one
 //    __syncthreads per step).  The "thread group sharing a cache" of the
-//    multi-thread wavefront (Sect. 4.4, MWD) is the CTA sharing its SM's
+//    multi-thread wavefront (Sect. 5.1, MWD) is the CTA sharing its SM's
 //    registers and shared memory; all its warps advance the frontline
 //    together, synchronised once per plane.
 //  * x is tiled with an overlapped halo of B*R columns (the paper leaves x
@@ -65,22 +65,31 @@ struct Rows {
     }
 };
 
-template <typename T, int KIND, int PHASE, int B, int TX, int BY, int NR>
+template <typename T, int KIND, int PHASE, int B, int TX, int BY, int NR, int PD>
 __global__ void __launch_bounds__(TX * BY)
 blocked_kernel(const BlockedArgs<T> a) {
     constexpr int R = KindTraits<KIND>::R;
     constexpr bool WAVE = KindTraits<KIND>::WAVE;
+    constexpr int NA = KindTraits<KIND>::NARR;
+    constexpr int NAB = NA > 0 ? NA : 1;
     constexpr int RY = BY * NR;
     constexpr int RING = 2 * R + 1;
     constexpr int PX = TX + 2 * R;      // shared plane pitch (R pad on each side)
     constexpr int PY = RY + 2 * R;
     constexpr int PLANE = PX * PY;
+    constexpr int M0 = (R + 2 + PD + RING - 1) / RING;
+    constexpr int NS0 = M0 * RING;      // level-0 plane slots
     static_assert(PHASE != PH_B || RY == 2 * (B + 1) * R, "phase B region is 2(B+1)R rows");
     static_assert(PHASE == PH_B || RY >= 2 * B * R, "tile must hold the trapezoid");
+    static_assert(NR <= 32, "row masks");
+    // coefficient loads are issued one level ahead when the double buffer
+    // fits in registers; otherwise at the start of each level
+    constexpr bool PREF = NA * NR <= 28;
     using Rw = Rows<PHASE, B, R, RY>;
 
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    T *sm = reinterpret_cast<T *>(smem_raw);  // [B][2][PLANE]
+    T *s0buf = reinterpret_cast<T *>(smem_raw);        // [NS0][PLANE] level 0
+    T *sbuf = s0buf + NS0 * PLANE;                      // [B-1][2][PLANE] levels 1..B-1
 
     const Geom g = a.g;
     const int tx = threadIdx.x, ty = threadIdx.y;
@@ -95,10 +104,38 @@ blocked_kernel(const BlockedArgs<T> a) {
     const int x = X0 + tx;
     const bool xin = x >= 0 && x < g.nx;
     const bool xown = xin && tx >= B * R && tx < TX - B * R;
-    const bool xmem = x >= -R && x < g.nx + R;   // inside the padded array
-
+    const int sy = (int)g.sy;
     const int qs = z0 - B * R, qe = z1 + B * R;
     const int64_t plane_elems = (int64_t)g.nx * g.ny;
+
+    // ---- per-thread constants: copy plan of level 0 (rows ty + i BY of
+    // column tx, zero outside the padded array) and masks of own rows
+    const bool xmem = x >= -R && x < g.nx + R;
+    uint32_t cmask = 0;      // copy rows inside the padded array
+#pragma unroll
+    for (int i = 0; i < NR; ++i) {
+        const int y = Y0 + ty + i * BY;
+        if (xmem && y >= -R && y < g.ny + R) cmask |= 1u << i;
+    }
+    const int coff0 = (Y0 + ty + R) * sy + (x + R);     // padded in-plane offset of copy row 0
+    uint32_t ymask = 0;      // own rows inside the interior (and the column inside)
+#pragma unroll
+    for (int jr = 0; jr < NR; ++jr) {
+        const int y = Y0 + ty * NR + jr;
+        if (xin && y >= 0 && y < g.ny) ymask |= 1u << jr;
+    }
+    const int pofs0 = (Y0 + ty * NR + R) * sy + (x + R);  // padded in-plane offset of own row 0
+
+    auto issue0 = [&](int q, T *slot) {
+        const bool qmem = q >= -R && q < g.nz + R;
+        const T *pb = a.u + (qmem ? (int64_t)(q + R) * g.sz : 0) + coff0;
+        T *d = slot + (ty + R) * PX + tx + R;
+#pragma unroll
+        for (int i = 0; i < NR; ++i) {
+            const bool ok = qmem && (cmask & (1u << i));
+            cp_async_zfill<sizeof(T)>(d + i * BY * PX, ok ? (const void *)(pb + i * BY * sy) : (const void *)a.u, ok);
+        }
+    };
 
     T ring[B][RING][NR];
 #pragma unroll
@@ -106,112 +143,150 @@ blocked_kernel(const BlockedArgs<T> a) {
 #pragma unroll
         for (int i = 0; i < RING; ++i)
 #pragma unroll
-            for (int j = 0; j < NR; ++j) ring[k][i][j] = T(0);
+            for (int jr = 0; jr < NR; ++jr) ring[k][i][jr] = T(0);
 
-    // level-0 input of the next step and (second order) u^{t-1} of level 1
-    T pre[NR], preP[NR];
-    auto load_level0 = [&](int q) {
-#pragma unroll
-        for (int j = 0; j < NR; ++j) {
-            const int y = Y0 + ty * NR + j;
-            const bool ok = xmem && y >= -R && y < g.ny + R && q >= -R && q < g.nz + R;
-            pre[j] = ok ? a.u[(int64_t)(q + R) * g.sz + (int64_t)(y + R) * g.sy + (x + R)] : T(0);
-        }
-    };
+    // u^{t-1} of level 1 (second order), one step ahead
+    T preP[NR];
     auto load_prev = [&](int z) {
+        const bool zin = z >= 0 && z < g.nz;
+        const int64_t zo = (int64_t)(z + R) * g.sz + pofs0;
 #pragma unroll
-        for (int j = 0; j < NR; ++j) {
-            const int y = Y0 + ty * NR + j;
-            const bool ok = xin && y >= 0 && y < g.ny && z >= 0 && z < g.nz;
-            preP[j] = ok ? a.u_prev[(int64_t)(z + R) * g.sz + (int64_t)(y + R) * g.sy + (x + R)] : T(0);
+        for (int jr = 0; jr < NR; ++jr)
+            preP[jr] = (zin && (ymask & (1u << jr))) ? a.u_prev[zo + jr * sy] : T(0);
+    };
+    // coefficients of level k at plane z for own rows
+    T cf[NAB][NR], cfn[NAB][NR];
+#pragma unroll
+    for (int t = 0; t < NAB; ++t)
+#pragma unroll
+        for (int jr = 0; jr < NR; ++jr) { cf[t][jr] = T(0); cfn[t][jr] = T(0); }
+    auto load_cf = [&](int z) {
+        if constexpr (NA > 0) {
+            if (z < 0 || z >= g.nz) return;
+            const int64_t zo = (int64_t)(z + R) * g.sz + pofs0;
+#pragma unroll
+            for (int jr = 0; jr < NR; ++jr) {
+                if (!(ymask & (1u << jr))) continue;
+#pragma unroll
+                for (int t = 0; t < NA; ++t) cfn[t][jr] = a.W[zo + jr * sy + t * g.nfield];
+            }
         }
     };
-    load_level0(qs);
+
+#pragma unroll
+    for (int i = 0; i < PD; ++i) {
+        if (qs + i < qe) issue0(qs + i, s0buf + i * PLANE);
+        cp_async_commit();
+    }
     if constexpr (WAVE) load_prev(qs - R);
 
     const T s0 = T(a.s.c[0]), s1 = T(a.s.c[1]), s2 = T(a.s.c[2]);
     const T s3 = T(a.s.c[3]), s4 = T(a.s.c[4]);
     (void)s0; (void)s1; (void)s2; (void)s3; (void)s4;
 
-    int par = 0;
+    int par = 0, blk = 0;
     for (int qb = qs; qb < qe; qb += RING) {
+        T *const slots0 = s0buf + blk * RING * PLANE;
         static_for<RING>([&](auto jj) {
             constexpr int j = decltype(jj)::value;
             const int q = qb + j;
             if (q >= qe) return;
-            // (a) level-0 front (plane q) into level 1's ring
             T curP[NR];
 #pragma unroll
-            for (int r = 0; r < NR; ++r) { ring[0][j][r] = pre[r]; curP[r] = preP[r]; }
-            // (b) prefetch the next step's inputs
-            if (q + 1 < qe) {
-                load_level0(q + 1);
-                if constexpr (WAVE) load_prev(q + 1 - R);
+            for (int jr = 0; jr < NR; ++jr) curP[jr] = preP[jr];
+            if constexpr (WAVE) {
+                if (q + 1 < qe) load_prev(q + 1 - R);
             }
-            // (c) centre planes of every level into shared memory
-            static_for<B>([&](auto kk) {
-                constexpr int k = decltype(kk)::value + 1;
-                if (q < qs + 2 * k * R) return;
-                T *buf = sm + ((k - 1) * 2 + par) * PLANE;
-                constexpr int jc = cmod(j - k * R, RING);
+            if constexpr (NA > 0 && PREF) load_cf(q - R);   // level 1 of this step
+            {
+                T *dst = slots0 + (j + PD) * PLANE;
+                if (j + PD >= NS0 - blk * RING) dst -= NS0 * PLANE;
+                if (q + PD < qe) issue0(q + PD, dst);
+            }
+            cp_async_commit();
+            // centre planes of levels 1..B-1 (inputs of levels 2..B)
+            static_for<B - 1>([&](auto kk) {
+                constexpr int k = decltype(kk)::value + 1;       // level whose plane is written
+                if (q < qs + 2 * (k + 1) * R) return;
+                T *buf = sbuf + ((k - 1) * 2 + par) * PLANE + (ty * NR + R) * PX + tx + R;
+                constexpr int jc = cmod(j - (k + 1) * R, RING);
 #pragma unroll
-                for (int r = 0; r < NR; ++r) buf[(ty * NR + r + R) * PX + tx + R] = ring[k - 1][jc][r];
+                for (int jr = 0; jr < NR; ++jr) buf[jr * PX] = ring[k][jc][jr];
             });
+            cp_async_wait<PD>();
             __syncthreads();
-            // (d) levels 1..B
+            // level-0 front
+            {
+                const T *sq = slots0 + j * PLANE + (ty * NR + R) * PX + tx + R;
+#pragma unroll
+                for (int jr = 0; jr < NR; ++jr) ring[0][j][jr] = sq[jr * PX];
+            }
+            // levels 1..B
             static_for<B>([&](auto kk) {
                 constexpr int k = decltype(kk)::value + 1;
                 if (q < qs + 2 * k * R) return;
                 const int z = q - k * R;
                 const bool zin = z >= 0 && z < g.nz;
                 const bool zown = z >= z0 && z < z1;
-                const T *sp = sm + ((k - 1) * 2 + par) * PLANE;
-                // ring slot of plane z (all rings index planes alike); ring[k-1]
-                // holds level k-1 around z, level k's result enters ring[k] there
-                constexpr int jc = cmod(j - k * R, RING);
-                const int64_t zoff = (int64_t)(z + R) * g.sz;
+                // coefficients: this level's arrived, prefetch the next level's
+                if constexpr (NA > 0) {
+                    if constexpr (!PREF) load_cf(z);
 #pragma unroll
-                for (int r = 0; r < NR; ++r) {
-                    const int ry = ty * NR + r;
-                    const int y = Y0 + ry;
-                    const bool in = xin && zin && y >= 0 && y < g.ny;
-                    const int64_t idx = zoff + (int64_t)(y + R) * g.sy + (x + R);
+                    for (int t = 0; t < NA; ++t)
+#pragma unroll
+                        for (int jr = 0; jr < NR; ++jr) cf[t][jr] = cfn[t][jr];
+                    if constexpr (PREF && k < B) load_cf(z - R);
+                }
+                const T *sp;
+                if constexpr (k == 1) {
+                    T *p0 = slots0 + (j - R) * PLANE;
+                    if (j - R < -blk * RING) p0 += NS0 * PLANE;
+                    sp = p0;
+                } else {
+                    sp = sbuf + ((k - 2) * 2 + par) * PLANE;
+                }
+                const T *rowp = sp + (ty * NR + R) * PX + tx + R;
+                constexpr int jc = cmod(j - k * R, RING);
+                const int64_t zoff = (int64_t)(z + R) * g.sz + pofs0;
+#pragma unroll
+                for (int jr = 0; jr < NR; ++jr) {
+                    const int ry = ty * NR + jr;
+                    const bool in = zin && (ymask & (1u << jr));
                     T v = T(0);
                     if (Rw::computed(k, ry)) {
                         if (in) {
-                            const int lr = ry + R;
-                            const T c = ring[k - 1][jc][r];
+                            const T *cp = rowp + jr * PX;
+                            const T c = ring[k - 1][jc][jr];
                             T xn[R][2], yn[R][2], zn[R][2];
 #pragma unroll
                             for (int d = 1; d <= R; ++d) {
-                                xn[d - 1][0] = sp[lr * PX + tx + R - d];
-                                xn[d - 1][1] = sp[lr * PX + tx + R + d];
-                                if (r - d >= 0) yn[d - 1][0] = ring[k - 1][jc][r - d];
-                                else yn[d - 1][0] = sp[(lr - d) * PX + tx + R];
-                                if (r + d < NR) yn[d - 1][1] = ring[k - 1][jc][r + d];
-                                else yn[d - 1][1] = sp[(lr + d) * PX + tx + R];
-                                zn[d - 1][0] = ring[k - 1][cmod(j - k * R - d, RING)][r];
-                                zn[d - 1][1] = ring[k - 1][cmod(j - k * R + d, RING)][r];
+                                xn[d - 1][0] = cp[-d];
+                                xn[d - 1][1] = cp[d];
+                                if (jr - d >= 0) yn[d - 1][0] = ring[k - 1][jc][jr - d];
+                                else yn[d - 1][0] = cp[-d * PX];
+                                if (jr + d < NR) yn[d - 1][1] = ring[k - 1][jc][jr + d];
+                                else yn[d - 1][1] = cp[d * PX];
+                                zn[d - 1][0] = ring[k - 1][cmod(j - k * R - d, RING)][jr];
+                                zn[d - 1][1] = ring[k - 1][cmod(j - k * R + d, RING)][jr];
                             }
-                            // u^{t-1} of this level: level k-2 at plane z
                             T pv = T(0);
                             if constexpr (WAVE) {
-                                if constexpr (k == 1) pv = curP[r];
-                                else pv = ring[k - 2][cmod(j - k * R, RING)][r];
+                                if constexpr (k == 1) pv = curP[jr];
+                                else pv = ring[k - 2][jc][jr];
                             }
                             (void)pv;
+                            constexpr int CO = (KIND == W25_ALPHA) ? 0 : 0;
+                            (void)CO;
                             if constexpr (KIND == J7_CONST) {
                                 v = s0 * c + s1 * (((xn[0][0] + xn[0][1]) + (yn[0][0] + yn[0][1])) + (zn[0][0] + zn[0][1]));
                             } else if constexpr (KIND == J7_VAR) {
-                                const T *Wp = a.W + idx;
-                                const int64_t n = g.nfield;
-                                v = Wp[0] * c;
-                                v = fma(Wp[1 * n], xn[0][0], v);
-                                v = fma(Wp[2 * n], xn[0][1], v);
-                                v = fma(Wp[3 * n], yn[0][0], v);
-                                v = fma(Wp[4 * n], yn[0][1], v);
-                                v = fma(Wp[5 * n], zn[0][0], v);
-                                v = fma(Wp[6 * n], zn[0][1], v);
+                                v = cf[0][jr] * c;
+                                v = fma(cf[1][jr], xn[0][0], v);
+                                v = fma(cf[2][jr], xn[0][1], v);
+                                v = fma(cf[3][jr], yn[0][0], v);
+                                v = fma(cf[4][jr], yn[0][1], v);
+                                v = fma(cf[5][jr], zn[0][0], v);
+                                v = fma(cf[6][jr], zn[0][1], v);
                             } else if constexpr (KIND == W25_CONST) {
                                 T acc = s0 * c - pv;
                                 const T wr[4] = {s1, s2, s3, s4};
@@ -225,46 +300,54 @@ blocked_kernel(const BlockedArgs<T> a) {
 #pragma unroll
                                 for (int d = 0; d < 4; ++d)
                                     s = fma(wr[d], ((xn[d][0] + xn[d][1]) + (yn[d][0] + yn[d][1])) + (zn[d][0] + zn[d][1]), s);
-                                v = fma(a.W[idx], s, T(2) * c - pv);
+                                v = fma(cf[0][jr], s, T(2) * c - pv);
                             } else {  // W25_VAR, J25_VAR
-                                const T *Wp = a.W + idx;
-                                const int64_t n = g.nfield;
-                                T acc = Wp[0] * c;
+                                T acc = cf[0][jr] * c;
                                 if constexpr (WAVE) acc = fma(T(2), c, acc) - pv;
 #pragma unroll
                                 for (int d = 0; d < 4; ++d) {
-                                    acc = fma(Wp[(3 * d + 1) * n], xn[d][0] + xn[d][1], acc);
-                                    acc = fma(Wp[(3 * d + 2) * n], yn[d][0] + yn[d][1], acc);
-                                    acc = fma(Wp[(3 * d + 3) * n], zn[d][0] + zn[d][1], acc);
+                                    acc = fma(cf[3 * d + 1][jr], xn[d][0] + xn[d][1], acc);
+                                    acc = fma(cf[3 * d + 2][jr], yn[d][0] + yn[d][1], acc);
+                                    acc = fma(cf[3 * d + 3][jr], zn[d][0] + zn[d][1], acc);
                                 }
                                 v = acc;
                             }
-                            if (zown && xown && Rw::owned(k, ry)) {
-                                if (a.trace && z == a.rcv_z) a.trace[(k - 1) * plane_elems + (int64_t)y * g.nx + x] = v;
-                                if constexpr (k == B) {
-                                    a.out[idx] = v;
+                            if (zown && xown) {
+                                if (Rw::owned(k, ry)) {
+                                    if (z == a.rcv_z && a.trace)
+                                        a.trace[(k - 1) * plane_elems + (int64_t)(Y0 + ry) * g.nx + x] = v;
+                                    if constexpr (k == B) a.out[zoff + jr * sy] = v;
                                 }
-                            }
-                            if constexpr (PHASE == PH_A && k < B) {
-                                if (zown && xown && Rw::band_store(k, ry)) a.bands[k][idx] = v;
+                                if constexpr (PHASE == PH_A && k < B) {
+                                    if (Rw::band_store(k, ry)) a.bands[k][zoff + jr * sy] = v;
+                                }
                             }
                         }
                     } else if constexpr (PHASE == PH_B && k < B) {
-                        if (Rw::band_load(k, ry) && in) v = a.bands[k][idx];
+                        if (Rw::band_load(k, ry) && in) v = a.bands[k][zoff + jr * sy];
                     }
                     if constexpr (k == B) {
                         // level B-1 at plane z: the next pass's u^{t-1}
                         if (a.out_prev && in && zown && xown && Rw::owned(B - 1, ry) &&
                             (PHASE != PH_OVL || Rw::owned(B, ry)))
-                            a.out_prev[idx] = ring[B - 1][jc][r];
+                            a.out_prev[zoff + jr * sy] = ring[B - 1][jc][jr];
                     } else {
-                        ring[k][jc][r] = v;
+                        ring[k][jc][jr] = v;
                     }
                 }
             });
             par ^= 1;
         });
+        blk = (blk + 1 == M0) ? 0 : blk + 1;
     }
+}
+
+template <typename T, int KIND, int B, int TX, int BY, int NR, int PD>
+constexpr size_t blocked_smem() {
+    constexpr int R = KindTraits<KIND>::R;
+    constexpr int RING = 2 * R + 1;
+    constexpr int M0 = (R + 2 + PD + RING - 1) / RING;
+    return sizeof(T) * (size_t)(M0 * RING + 2 * (B - 1)) * (TX + 2 * R) * (BY * NR + 2 * R);
 }
 
 // ---------------------------------------------------------------- configs
@@ -282,9 +365,11 @@ template <int B> struct Cfg<4, B> {
 
 template <typename T, int KIND, int PHASE, int B, int TX, int BY, int NR>
 static cudaError_t launch_one(const BlockedArgs<T> &a, cudaStream_t st, int num_sms, int gy) {
-    auto kern = blocked_kernel<T, KIND, PHASE, B, TX, BY, NR>;
+    constexpr int PD = 2;
+    auto kern = blocked_kernel<T, KIND, PHASE, B, TX, BY, NR, PD>;
     constexpr int R = KindTraits<KIND>::R;
-    constexpr size_t smem = sizeof(T) * (size_t)B * 2 * (TX + 2 * R) * (BY * NR + 2 * R);
+    constexpr size_t smem = blocked_smem<T, KIND, B, TX, BY, NR, PD>();
+    static_assert(smem <= 227 * 1024, "shared memory per CTA");
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     int per_sm = 0;

@@ -83,6 +83,17 @@ __device__ __forceinline__ void cp_async(void *smem, const void *gmem) {
     else
         asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem) : "memory");
 }
+// cp.async that writes zeros instead of reading when `valid` is false (the
+// source operand size is then 0 and nothing is read).
+template <int BYTES>
+__device__ __forceinline__ void cp_async_zfill(void *smem, const void *gmem, bool valid) {
+    const unsigned s = static_cast<unsigned>(__cvta_generic_to_shared(smem));
+    const int src = valid ? BYTES : 0;
+    if constexpr (BYTES == 4)
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(s), "l"(gmem), "r"(src) : "memory");
+    else
+        asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;\n" ::"r"(s), "l"(gmem), "r"(src) : "memory");
+}
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 template <int N>
 __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
