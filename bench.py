@@ -291,13 +291,15 @@ def run_sweep(args, torch, st, wl, pm, stream, ws, peak_f64, hbm_peak, peak_f32)
     for kind in (wl.J7_CONST, wl.J7_VAR, wl.W25_CONST, wl.W25_VAR):
         wk = wl.make(kind, n, T, seed=0) if kind != wl.J7_VAR else wl.j7_var(n, T, seed=0)
         for dtype in (st.F64, st.F32):
-            for v in (1, 2, 3, 4, 5, 6, 7):
+            for v in (1, 2, 3, 4, 5, 6, 7, 8, 9):
                 r, _ = forward_case(torch, st, wl, kind, n, T, dtype, args.steps, 1, ws, stream, time_block=1,
                                     wk=wk, variant=v)
                 r["roofline"] = roofline_of(pm, kind, r["dtype"], n, r, peak_f64, hbm_peak, peak_f32)
                 print(json.dumps({"sweep": r}), flush=True)
-            if dtype == st.F32:
-                for b in ((2, 4) if wl.RADIUS[kind] == 1 else (2,)):
+            blocked = ((2, 4) if wl.RADIUS[kind] == 1 else (2,)) if dtype == st.F32 else \
+                ((2,) if wl.RADIUS[kind] == 1 else ())
+            if blocked:
+                for b in blocked:
                     for sch in (1, 2):
                         r, _ = forward_case(torch, st, wl, kind, n, T, dtype, args.steps, 1, ws, stream,
                                             time_block=b, wk=wk, scheme=sch)

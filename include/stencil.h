@@ -95,7 +95,8 @@ enum stencil_option {
        one-level kernel): 0 = measured default for the kind and dtype,
        1..4, 6, 7 = asynchronously staged tiles of 32x8, 32x16, 32x16 (4 rows
        per thread), 64x8, 64x16 and 128x8 columns, 5 = register-staged 2.5D
-       kernel. */
+       kernel, 8 and 9 = 32x8 and 32x16 tiles with the per-point inputs
+       (coefficients, u^{t-1}) staged asynchronously as well. */
     STENCIL_OPT_VARIANT = 5
 };
 

@@ -187,7 +187,6 @@ struct stencil_plan_s {
 namespace {
 
 int default_time_block(const stencil_plan_s *p) {
-    if (p->dtype == STENCIL_F64) return 1;  // FP64 sweeps are bound by the FP64 pipe
     return blocked_default_levels(p->kind, p->dtype);
 }
 
@@ -513,7 +512,7 @@ int stencil_plan_set(stencil_plan_t p, int option, int64_t value) {
         p->scheme = (int)value;
         return STENCIL_OK;
     case STENCIL_OPT_VARIANT:
-        if (value < 0 || value > 7) return STENCIL_EINVAL;
+        if (value < 0 || value > 9) return STENCIL_EINVAL;
         p->variant = (int)value;
         return STENCIL_OK;
     case STENCIL_OPT_GRAD_BATCH:

@@ -351,16 +351,20 @@ constexpr size_t blocked_smem() {
 }
 
 // ---------------------------------------------------------------- configs
-// Per radius: tile of the overlapped / phase-A launch (TX x BY threads, NR
-// rows each) and of the phase-B launch (2(B+1)R rows).
-template <int R, int B> struct Cfg;
-template <int B> struct Cfg<1, B> {
+// Per element size and radius: tile of the overlapped / phase-A launch (TX x
+// BY threads, NR rows each) and of the phase-B launch (2(B+1)R rows).
+template <int WORD, int R, int B> struct Cfg;
+template <int B> struct Cfg<4, 1, B> {
     static constexpr int TX = 64, BY = 8, NR = 4;                 // 64 x 32 region
     static constexpr int BTX = 64, BNR = 2, BBY = (B + 1);        // 64 x 2(B+1)
 };
-template <int B> struct Cfg<4, B> {
+template <int B> struct Cfg<4, 4, B> {
     static constexpr int TX = 64, BY = 8, NR = 3;                 // 64 x 24 region
     static constexpr int BTX = 64, BNR = 3, BBY = 8 * (B + 1) / 3;  // 64 x 2(B+1)R
+};
+template <int B> struct Cfg<8, 1, B> {                            // FP64: 256-thread tiles
+    static constexpr int TX = 32, BY = 8, NR = 2;                 // 32 x 16 region
+    static constexpr int BTX = 32, BNR = 2, BBY = (B + 1);
 };
 
 template <typename T, int KIND, int PHASE, int B, int TX, int BY, int NR>
@@ -377,11 +381,12 @@ static cudaError_t launch_one(const BlockedArgs<T> &a, cudaStream_t st, int num_
     if (per_sm < 1) per_sm = 1;
     constexpr int TXO = TX - 2 * B * R;
     const int gx = (a.g.nx + TXO - 1) / TXO;
-    // z chunks: about 3 waves of CTAs, each chunk at least 8*B*R planes
-    const int64_t want = (int64_t)num_sms * per_sm * 3;
+    // z chunks: enough CTAs for one to two waves; every chunk recomputes a
+    // ramp of 2BR planes, so chunks are at least 16BR (and 32) planes long
+    const int64_t want = (int64_t)num_sms * per_sm;
     const int64_t tiles = (int64_t)gx * gy;
     int nzc = (int)((want + tiles - 1) / tiles);
-    const int min_chunk = 8 * B * R;
+    const int min_chunk = 16 * B * R > 32 ? 16 * B * R : 32;
     if (nzc < 1) nzc = 1;
     if ((a.g.nz + nzc - 1) / nzc < min_chunk) nzc = (a.g.nz + min_chunk - 1) / min_chunk;
     if (nzc < 1) nzc = 1;
@@ -396,7 +401,7 @@ static cudaError_t launch_one(const BlockedArgs<T> &a, cudaStream_t st, int num_
 template <typename T, int KIND, int B>
 static cudaError_t launch_levels(const BlockedArgs<T> &a, cudaStream_t st, int num_sms, int scheme) {
     constexpr int R = KindTraits<KIND>::R;
-    using C = Cfg<R, B>;
+    using C = Cfg<(int)sizeof(T), R, B>;
     constexpr int RY = C::BY * C::NR;
     if (scheme == 1) {
         constexpr int WO = RY - 2 * B * R;
@@ -435,16 +440,19 @@ static cudaError_t launch_kind(const BlockedArgs<T> &a, cudaStream_t st, int num
 }
 
 bool blocked_supported(int kind, int dtype, int levels) {
-    if (dtype != 1) return false;  // FP32 only: FP64 sweeps are bound by the FP64 pipe
     const int R = kind_radius(kind);
+    if (dtype != 1) return R == 1 && levels == 2;  // FP64: 7-point kinds, two levels per pass
     if (R == 1) return levels == 2 || levels == 4;
     if (R == 4) return levels == 2;
     return false;
 }
 
+// Default block depth per kind and dtype (measured, 512^3): 1 where the
+// plain streaming sweep is faster.
 int blocked_default_levels(int kind, int dtype) {
-    if (dtype != 1) return 1;
-    return kind_radius(kind) == 1 ? 4 : 2;
+    (void)kind;
+    (void)dtype;
+    return 1;
 }
 
 int blocked_scratch_levels(int levels) { return levels > 1 ? levels - 1 : 0; }
@@ -463,7 +471,13 @@ cudaError_t launch_blocked(int kind, const BlockedArgs<T> &a, cudaStream_t st, i
         default: return cudaErrorInvalidValue;
         }
     } else {
-        return cudaErrorNotSupported;
+        switch (kind) {
+        case J7_CONST:
+            return a.levels == 2 ? launch_levels<T, J7_CONST, 2>(a, st, num_sms, scheme) : cudaErrorNotSupported;
+        case J7_VAR:
+            return a.levels == 2 ? launch_levels<T, J7_VAR, 2>(a, st, num_sms, scheme) : cudaErrorNotSupported;
+        default: return cudaErrorNotSupported;
+        }
     }
 }
 

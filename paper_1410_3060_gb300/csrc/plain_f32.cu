@@ -7,7 +7,8 @@ namespace stc {
 // rows, NR rows per thread, PD planes of prefetch), selected per plan
 // (STENCIL_OPT_VARIANT): 1 = 32x8x1/2, 2 = 32x8x2/2, 3 = 32x4x4/2,
 // 4 = 64x4x2/2, 5 = the register-staged plain kernel (plain_sweep_kernel),
-// 6 = 64x4x4/2, 7 = 128x2x4/2.
+// 6 = 64x4x4/2, 7 = 128x2x4/2; 8 = 32x8x1/3 and 9 = 32x8x2/2 with the
+// per-point inputs (coefficients, u^{t-1}) also staged by cp.async.
 // 0 picks the default of the kind and dtype (measured best).
 template <typename T, int KIND>
 static cudaError_t launch_forward(const SweepArgs<T> &a, cudaStream_t st, int num_sms, int variant) {
@@ -20,6 +21,12 @@ static cudaError_t launch_forward(const SweepArgs<T> &a, cudaStream_t st, int nu
     case 4: return launch_stream<T, KIND, 64, 4, 2, 2>(a, st, num_sms);
     case 6: return launch_stream<T, KIND, 64, 4, 4, 2>(a, st, num_sms);
     case 7: return launch_stream<T, KIND, 128, 2, 4, 2>(a, st, num_sms);
+    case 8: return launch_stream<T, KIND, 32, 8, 1, 3, true>(a, st, num_sms);
+    case 9:  // falls back to 8 where its staged tiles exceed shared memory
+        if constexpr (stream_smem<T, KIND, 32, 8, 2, 2, true>() <= 227 * 1024)
+            return launch_stream<T, KIND, 32, 8, 2, 2, true>(a, st, num_sms);
+        else
+            return launch_stream<T, KIND, 32, 8, 1, 3, true>(a, st, num_sms);
     case 5:
         if constexpr (sizeof(T) == 4) {
             if constexpr (R == 1) return launch_cfg<T, KIND, false, 64, 4, 8, 2>(a, st, num_sms);

@@ -242,7 +242,7 @@ plain_sweep_kernel(const SweepArgs<T> a) {
 //  * the per-point inputs of an output plane (u^{t-1}, coefficients, no
 //    halo) are loaded into registers one iteration before use;
 //  * receiver trace / residual injection are handled once per plane.
-template <typename T, int KIND, int TX, int BY, int NR, int PD>
+template <typename T, int KIND, int TX, int BY, int NR, int PD, bool STAGE = false>
 __global__ void __launch_bounds__(TX * BY)
 plain_stream_kernel(const SweepArgs<T> a) {
     constexpr int R = KindTraits<KIND>::R;
@@ -261,8 +261,15 @@ plain_stream_kernel(const SweepArgs<T> a) {
     static_assert(2 * R <= TX, "halo columns are copied by the first 2R threads");
     static_assert(NLR <= 32 && NR <= 32, "bit masks");
 
+    // STAGE: per-point inputs also travel through the cp.async pipeline, in
+    // a ring of NSO = PD + 2 output-plane slots ([NPO][TY][TX] each)
+    constexpr int OT = TX * TY;
+    constexpr int NSO = PD + 2;
+
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T *su = reinterpret_cast<T *>(smem_raw);       // [NSU][SH][SW]
+    T *so = su + NSU * SPLANE;                     // STAGE: [NSO][NPO][TY][TX]
+    (void)so;
 
     const Geom g = a.g;
     const int tx = threadIdx.x, ty = threadIdx.y;
@@ -318,6 +325,24 @@ plain_stream_kernel(const SweepArgs<T> a) {
         }
     };
 
+    // STAGE: copies of the per-point inputs of output plane z into slot `o`
+    auto issue_points = [&](int z, int o) {
+        if constexpr (STAGE && NPO > 0) {
+            if (z < z0 || z >= z1) return;
+            const int64_t base = (int64_t)(z + R) * g.sz + pofs0;
+            T *d = so + o * (NPO * OT) + (ty * NR) * TX + tx;
+#pragma unroll
+            for (int jr = 0; jr < NR; ++jr) {
+                if (!(rowok & (1u << jr))) continue;
+                const int64_t off = base + jr * sy;
+                if constexpr (WAVE) cp_async<sizeof(T)>(d + jr * TX, a.u_prev + off);
+#pragma unroll
+                for (int t = 0; t < NA; ++t)
+                    cp_async<sizeof(T)>(d + ((WAVE ? 1 : 0) + t) * OT + jr * TX, a.W + off + t * g.nfield);
+            }
+        }
+    };
+
     T ring[RING][NR];
 #pragma unroll
     for (int i = 0; i < RING; ++i)
@@ -328,13 +353,17 @@ plain_stream_kernel(const SweepArgs<T> a) {
 #pragma unroll
         for (int jr = 0; jr < NR; ++jr) { pin[t][jr] = T(0); pnx[t][jr] = T(0); }
 
-    // prologue: planes qs .. qs+PD-1 into slots 0 .. PD-1
+    // prologue: planes qs .. qs+PD-1 into slots 0 .. PD-1 (and, staged, the
+    // per-point inputs of their output planes)
 #pragma unroll
     for (int i = 0; i < PD; ++i) {
-        if (qs + i < qe) issue(qs + i, su + i * SPLANE);
+        if (qs + i < qe) {
+            issue(qs + i, su + i * SPLANE);
+            issue_points(qs + i - R, i % NSO);
+        }
         cp_async_commit();
     }
-    load_point_inputs(z0);
+    if constexpr (!STAGE) load_point_inputs(z0);
 
     const T s0 = T(a.s.c[0]), s1 = T(a.s.c[1]), s2 = T(a.s.c[2]);
     const T s3 = T(a.s.c[3]), s4 = T(a.s.c[4]);
@@ -348,7 +377,7 @@ plain_stream_kernel(const SweepArgs<T> a) {
             const int q = qb + j;
             if (q >= qe) return;
             const int z = q - R;
-            if constexpr (NPO > 0) {
+            if constexpr (NPO > 0 && !STAGE) {
                 if (z >= z0) {
 #pragma unroll
                     for (int t = 0; t < NPO; ++t)
@@ -361,11 +390,23 @@ plain_stream_kernel(const SweepArgs<T> a) {
             {
                 T *dst = slots + (j + PD) * SPLANE;
                 if (j + PD >= NSU - blk * RING) dst -= NSU * SPLANE;
-                if (q + PD < qe) issue(q + PD, dst);
+                if (q + PD < qe) {
+                    issue(q + PD, dst);
+                    issue_points(q + PD - R, (q + PD - qs) % NSO);
+                }
             }
             cp_async_commit();
             cp_async_wait<PD>();
             __syncthreads();
+            if constexpr (STAGE && NPO > 0) {
+                if (z >= z0) {
+                    const T *sop = so + ((q - qs) % NSO) * (NPO * OT) + (ty * NR) * TX + tx;
+#pragma unroll
+                    for (int t = 0; t < NPO; ++t)
+#pragma unroll
+                        for (int jr = 0; jr < NR; ++jr) pin[t][jr] = sop[t * OT + jr * TX];
+                }
+            }
 
             const T *sq = slots + j * SPLANE;
 #pragma unroll
@@ -452,13 +493,15 @@ plain_stream_kernel(const SweepArgs<T> a) {
     }
 }
 
-template <typename T, int KIND, int TX, int BY, int NR, int PD>
+template <typename T, int KIND, int TX, int BY, int NR, int PD, bool STAGE = false>
 constexpr size_t stream_smem() {
     constexpr int R = KindTraits<KIND>::R;
     constexpr int TY = BY * NR;
     constexpr int RING = 2 * R + 1;
     constexpr int M = (R + 2 + PD + RING - 1) / RING;
-    return sizeof(T) * (size_t)(M * RING) * (TX + 2 * R) * (TY + 2 * R);
+    constexpr int NPO = (KindTraits<KIND>::WAVE ? 1 : 0) + KindTraits<KIND>::NARR;
+    return sizeof(T) * ((size_t)(M * RING) * (TX + 2 * R) * (TY + 2 * R) +
+                        (STAGE ? (size_t)(PD + 2) * NPO * TX * TY : 0));
 }
 
 // Grid: tiles of TX x TY columns times z chunks, chunks sized for about four
@@ -499,13 +542,13 @@ static cudaError_t launch_cfg(const SweepArgs<T> &a, cudaStream_t st, int num_sm
     return cudaGetLastError();
 }
 
-template <typename T, int KIND, int TX, int BY, int NR, int PD>
+template <typename T, int KIND, int TX, int BY, int NR, int PD, bool STAGE = false>
 static cudaError_t launch_stream(const SweepArgs<T> &a, cudaStream_t st, int num_sms) {
     constexpr int R = KindTraits<KIND>::R;
     constexpr int TY = BY * NR;
-    constexpr size_t smem = stream_smem<T, KIND, TX, BY, NR, PD>();
+    constexpr size_t smem = stream_smem<T, KIND, TX, BY, NR, PD, STAGE>();
     static_assert(smem <= 227 * 1024, "shared memory per CTA");
-    auto kern = plain_stream_kernel<T, KIND, TX, BY, NR, PD>;
+    auto kern = plain_stream_kernel<T, KIND, TX, BY, NR, PD, STAGE>;
     SweepArgs<T> b = a;
     dim3 grid;
     cudaError_t e = launch_grid(kern, smem, TX, BY, TY, R, nullptr, a.g.nx, a.g.ny, a.g.nz, num_sms, &b.zchunk, &grid);

@@ -66,6 +66,22 @@ def test_blocked_matches_plain_gpu(st, kind, b, scheme):
     assert normwise_err(gu_b, gu_p) <= 8 * T * 2.0 ** -24 * (T if kind in (3, 4, 6) else 1)
 
 
+@pytest.mark.parametrize("kind", R1)
+@pytest.mark.parametrize("scheme", [1, 2])
+@pytest.mark.parametrize("shape", [(70, 45, 40), (33, 19, 11)])
+def test_blocked_forward_fp64(st, kind, scheme, shape):
+    """FP64 two-level passes match the oracle to 1e-12."""
+    from gpu_util import F64
+    T = 7
+    wk = wl.make(kind, shape, T, seed=9)
+    rz = 3
+    op, ou, otr = oracle.forward(kind, wk.u_prev, wk.u, wk.w, wk.W, T, rcv_z=rz, threads=8)
+    gp, gu, gtr = gpu_forward(st.Plan, wk, F64, rcv_z=rz, time_block=2, scheme=scheme)
+    assert normwise_err(gu, ou) <= 1e-12
+    assert normwise_err(gp, op) <= 1e-12
+    assert normwise_err(gtr, otr) <= 1e-12
+
+
 def test_time_block_option_roundtrip(st):
     p = st.Plan(1, 32, 32, 32, F32)
     p.set(1, 4)
