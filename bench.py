@@ -296,7 +296,7 @@ def run_sweep(args, torch, st, wl, pm, stream, ws, peak_f64, hbm_peak, peak_f32)
                                     wk=wk, variant=v)
                 r["roofline"] = roofline_of(pm, kind, r["dtype"], n, r, peak_f64, hbm_peak, peak_f32)
                 print(json.dumps({"sweep": r}), flush=True)
-            blocked = ((2, 4) if wl.RADIUS[kind] == 1 else (2,)) if dtype == st.F32 else \
+            blocked = ((2, 3, 4) if wl.RADIUS[kind] == 1 else (2,)) if dtype == st.F32 else \
                 ((2,) if wl.RADIUS[kind] == 1 else ())
             if blocked:
                 for b in blocked:

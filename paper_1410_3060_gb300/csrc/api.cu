@@ -37,12 +37,13 @@ int default_variant(int kind, int dtype) {
         switch (kind) {
         case J7_CONST: return 7;               // 128 x 8 tiles
         case J7_VAR: return 3;                 // 32 x 16, 4 rows per thread
-        case W25_CONST: case W25_ALPHA: return 3;
+        case W25_CONST: case W25_ALPHA: return 9;  // 32 x 16, staged u^{t-1}
         default: return 4;                     // W25_VAR, J25_VAR: 64 x 8
         }
     }
     switch (kind) {    // FP64 (bound by the FP64 pipe)
     case J7_CONST: return 3;
+    case J7_VAR: case W25_CONST: case W25_ALPHA: return 8;  // staged per-point inputs
     default: return 1;                         // 32 x 8, one row per thread
     }
 }

@@ -65,7 +65,11 @@ struct Rows {
     }
 };
 
-template <typename T, int KIND, int PHASE, int B, int TX, int BY, int NR, int PD>
+// CS: coefficient planes are staged once per pass in a shared-memory ring of
+// NCS = (B-1)R + PD + 2 plane slots and reused by all B levels (a plane is
+// issued PD steps before level 1 needs it and read last by level B, (B-1)R
+// steps later); otherwise each level loads them from global memory / L2.
+template <typename T, int KIND, int PHASE, int B, int TX, int BY, int NR, int PD, bool CS = false>
 __global__ void __launch_bounds__(TX * BY)
 blocked_kernel(const BlockedArgs<T> a) {
     constexpr int R = KindTraits<KIND>::R;
@@ -84,12 +88,17 @@ blocked_kernel(const BlockedArgs<T> a) {
     static_assert(NR <= 32, "row masks");
     // coefficient loads are issued one level ahead when the double buffer
     // fits in registers; otherwise at the start of each level
-    constexpr bool PREF = NA * NR <= 28;
+    constexpr bool CST = CS && NA > 0;
+    constexpr bool PREF = !CST && NA * NR <= 28;
+    constexpr int NCS = (B - 1) * R + PD + 2;
+    constexpr int CPL = NAB * RY * TX;    // one staged coefficient plane
     using Rw = Rows<PHASE, B, R, RY>;
 
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T *s0buf = reinterpret_cast<T *>(smem_raw);        // [NS0][PLANE] level 0
     T *sbuf = s0buf + NS0 * PLANE;                      // [B-1][2][PLANE] levels 1..B-1
+    T *cbuf = sbuf + 2 * (B - 1) * PLANE;               // CST: [NCS][NA][RY][TX]
+    (void)cbuf;
 
     const Geom g = a.g;
     const int tx = threadIdx.x, ty = threadIdx.y;
@@ -126,6 +135,26 @@ blocked_kernel(const BlockedArgs<T> a) {
     }
     const int pofs0 = (Y0 + ty * NR + R) * sy + (x + R);  // padded in-plane offset of own row 0
 
+    uint32_t imask = 0;      // copy rows inside the interior (coefficient staging)
+#pragma unroll
+    for (int i = 0; i < NR; ++i) {
+        const int y = Y0 + ty + i * BY;
+        if (xin && y >= 0 && y < g.ny) imask |= 1u << i;
+    }
+    // coefficient plane p into ring slot (p mod NCS)
+    auto issue_coef = [&](int p) {
+        if constexpr (CST) {
+            if (p < 0 || p >= g.nz) return;
+            T *d = cbuf + cmod(p, NCS) * CPL + ty * TX + tx;
+            const T *src = a.W + (int64_t)(p + R) * g.sz + coff0;
+#pragma unroll
+            for (int t = 0; t < NA; ++t)
+#pragma unroll
+                for (int i = 0; i < NR; ++i)
+                    if (imask & (1u << i))
+                        cp_async<sizeof(T)>(d + t * RY * TX + i * BY * TX, src + t * g.nfield + i * BY * sy);
+        }
+    };
     auto issue0 = [&](int q, T *slot) {
         const bool qmem = q >= -R && q < g.nz + R;
         const T *pb = a.u + (qmem ? (int64_t)(q + R) * g.sz : 0) + coff0;
@@ -175,7 +204,10 @@ blocked_kernel(const BlockedArgs<T> a) {
 
 #pragma unroll
     for (int i = 0; i < PD; ++i) {
-        if (qs + i < qe) issue0(qs + i, s0buf + i * PLANE);
+        if (qs + i < qe) {
+            issue0(qs + i, s0buf + i * PLANE);
+            issue_coef(qs + i - R);
+        }
         cp_async_commit();
     }
     if constexpr (WAVE) load_prev(qs - R);
@@ -201,7 +233,10 @@ blocked_kernel(const BlockedArgs<T> a) {
             {
                 T *dst = slots0 + (j + PD) * PLANE;
                 if (j + PD >= NS0 - blk * RING) dst -= NS0 * PLANE;
-                if (q + PD < qe) issue0(q + PD, dst);
+                if (q + PD < qe) {
+                    issue0(q + PD, dst);
+                    issue_coef(q + PD - R);
+                }
             }
             cp_async_commit();
             // centre planes of levels 1..B-1 (inputs of levels 2..B)
@@ -229,7 +264,15 @@ blocked_kernel(const BlockedArgs<T> a) {
                 const bool zin = z >= 0 && z < g.nz;
                 const bool zown = z >= z0 && z < z1;
                 // coefficients: this level's arrived, prefetch the next level's
-                if constexpr (NA > 0) {
+                if constexpr (CST) {
+                    if (z >= 0 && z < g.nz) {
+                        const T *cs = cbuf + cmod(z, NCS) * CPL + (ty * NR) * TX + tx;
+#pragma unroll
+                        for (int t = 0; t < NA; ++t)
+#pragma unroll
+                            for (int jr = 0; jr < NR; ++jr) cf[t][jr] = cs[t * RY * TX + jr * TX];
+                    }
+                } else if constexpr (NA > 0) {
                     if constexpr (!PREF) load_cf(z);
 #pragma unroll
                     for (int t = 0; t < NA; ++t)
@@ -342,37 +385,46 @@ blocked_kernel(const BlockedArgs<T> a) {
     }
 }
 
-template <typename T, int KIND, int B, int TX, int BY, int NR, int PD>
+template <typename T, int KIND, int B, int TX, int BY, int NR, int PD, bool CS = false>
 constexpr size_t blocked_smem() {
     constexpr int R = KindTraits<KIND>::R;
     constexpr int RING = 2 * R + 1;
     constexpr int M0 = (R + 2 + PD + RING - 1) / RING;
-    return sizeof(T) * (size_t)(M0 * RING + 2 * (B - 1)) * (TX + 2 * R) * (BY * NR + 2 * R);
+    constexpr int NA = KindTraits<KIND>::NARR;
+    constexpr size_t cs = (CS && NA > 0) ? (size_t)((B - 1) * R + PD + 2) * NA * BY * NR * TX : 0;
+    return sizeof(T) * ((size_t)(M0 * RING + 2 * (B - 1)) * (TX + 2 * R) * (BY * NR + 2 * R) + cs);
 }
 
 // ---------------------------------------------------------------- configs
-// Per element size and radius: tile of the overlapped / phase-A launch (TX x
-// BY threads, NR rows each) and of the phase-B launch (2(B+1)R rows).
-template <int WORD, int R, int B> struct Cfg;
-template <int B> struct Cfg<4, 1, B> {
+// Per element size, radius, block depth and coefficient staging: tile of the
+// overlapped / phase-A launch (TX x BY threads, NR rows each) and of the
+// phase-B launch (2(B+1)R rows).  With staged coefficients (CS) the region is
+// kept small enough for the coefficient ring to fit shared memory.
+template <int WORD, int R, int B, bool CS> struct Cfg;
+template <int B> struct Cfg<4, 1, B, false> {
     static constexpr int TX = 64, BY = 8, NR = 4;                 // 64 x 32 region
     static constexpr int BTX = 64, BNR = 2, BBY = (B + 1);        // 64 x 2(B+1)
 };
-template <int B> struct Cfg<4, 4, B> {
+template <int B> struct Cfg<4, 1, B, true> {
+    static constexpr int TX = (B <= 3 ? 64 : 32), BY = 4, NR = 4; // 64 x 16 (32 x 16 for B = 4)
+    static constexpr int BTX = TX, BNR = 2, BBY = (B + 1);
+};
+template <int B> struct Cfg<4, 4, B, false> {
     static constexpr int TX = 64, BY = 8, NR = 3;                 // 64 x 24 region
     static constexpr int BTX = 64, BNR = 3, BBY = 8 * (B + 1) / 3;  // 64 x 2(B+1)R
 };
-template <int B> struct Cfg<8, 1, B> {                            // FP64: 256-thread tiles
+template <int B> struct Cfg<4, 4, B, true> : Cfg<4, 4, B, false> {};
+template <int B, bool CS> struct Cfg<8, 1, B, CS> {               // FP64: 256-thread tiles
     static constexpr int TX = 32, BY = 8, NR = 2;                 // 32 x 16 region
     static constexpr int BTX = 32, BNR = 2, BBY = (B + 1);
 };
 
-template <typename T, int KIND, int PHASE, int B, int TX, int BY, int NR>
+template <typename T, int KIND, int PHASE, int B, int TX, int BY, int NR, bool CS>
 static cudaError_t launch_one(const BlockedArgs<T> &a, cudaStream_t st, int num_sms, int gy) {
     constexpr int PD = 2;
-    auto kern = blocked_kernel<T, KIND, PHASE, B, TX, BY, NR, PD>;
+    auto kern = blocked_kernel<T, KIND, PHASE, B, TX, BY, NR, PD, CS>;
     constexpr int R = KindTraits<KIND>::R;
-    constexpr size_t smem = blocked_smem<T, KIND, B, TX, BY, NR, PD>();
+    constexpr size_t smem = blocked_smem<T, KIND, B, TX, BY, NR, PD, CS>();
     static_assert(smem <= 227 * 1024, "shared memory per CTA");
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
@@ -401,13 +453,14 @@ static cudaError_t launch_one(const BlockedArgs<T> &a, cudaStream_t st, int num_
 template <typename T, int KIND, int B>
 static cudaError_t launch_levels(const BlockedArgs<T> &a, cudaStream_t st, int num_sms, int scheme) {
     constexpr int R = KindTraits<KIND>::R;
-    using C = Cfg<(int)sizeof(T), R, B>;
+    constexpr bool CS = KindTraits<KIND>::NARR > 0 && R == 1;   // stage the 7 coefficient planes
+    using C = Cfg<(int)sizeof(T), R, B, CS>;
     constexpr int RY = C::BY * C::NR;
     if (scheme == 1) {
         constexpr int WO = RY - 2 * B * R;
         if constexpr (WO > 0) {
             const int gy = (a.g.ny + WO - 1) / WO;
-            return launch_one<T, KIND, PH_OVL, B, C::TX, C::BY, C::NR>(a, st, num_sms, gy);
+            return launch_one<T, KIND, PH_OVL, B, C::TX, C::BY, C::NR, CS>(a, st, num_sms, gy);
         } else {
             return cudaErrorNotSupported;
         }
@@ -416,10 +469,10 @@ static cudaError_t launch_levels(const BlockedArgs<T> &a, cudaStream_t st, int n
     BlockedArgs<T> b = a;
     b.wA = RY;
     const int nA = (a.g.ny + RY - 1) / RY;
-    cudaError_t e = launch_one<T, KIND, PH_A, B, C::TX, C::BY, C::NR>(b, st, num_sms, nA);
+    cudaError_t e = launch_one<T, KIND, PH_A, B, C::TX, C::BY, C::NR, CS>(b, st, num_sms, nA);
     if (e != cudaSuccess) return e;
     static_assert(C::BBY * C::BNR == 2 * (B + 1) * R, "phase B rows");
-    return launch_one<T, KIND, PH_B, B, C::BTX, C::BBY, C::BNR>(b, st, num_sms, nA + 1);
+    return launch_one<T, KIND, PH_B, B, C::BTX, C::BBY, C::BNR, CS>(b, st, num_sms, nA + 1);
 }
 
 template <typename T, int KIND>
@@ -428,6 +481,7 @@ static cudaError_t launch_kind(const BlockedArgs<T> &a, cudaStream_t st, int num
     if constexpr (R == 1) {
         switch (a.levels) {
         case 2: return launch_levels<T, KIND, 2>(a, st, num_sms, scheme);
+        case 3: return launch_levels<T, KIND, 3>(a, st, num_sms, scheme);
         case 4: return launch_levels<T, KIND, 4>(a, st, num_sms, scheme);
         default: return cudaErrorNotSupported;
         }
@@ -442,7 +496,7 @@ static cudaError_t launch_kind(const BlockedArgs<T> &a, cudaStream_t st, int num
 bool blocked_supported(int kind, int dtype, int levels) {
     const int R = kind_radius(kind);
     if (dtype != 1) return R == 1 && levels == 2;  // FP64: 7-point kinds, two levels per pass
-    if (R == 1) return levels == 2 || levels == 4;
+    if (R == 1) return levels >= 2 && levels <= 4;
     if (R == 4) return levels == 2;
     return false;
 }

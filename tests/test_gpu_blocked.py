@@ -27,7 +27,7 @@ def st():
 def cases():
     out = []
     for kind in R1:
-        for b in (2, 4):
+        for b in (2, 3, 4):
             for scheme in (1, 2):
                 out.append((kind, b, scheme))
     for kind in R4:
