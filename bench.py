@@ -283,6 +283,58 @@ def roofline_of(pm, kind, dtype_name, n, res, peak_f64, hbm_peak, fp32_peak):
             "alu_view": {"achieved_tflops": flops_pass / t_pass / 1e12, "peak_tflops": fp32_peak / 1e12}}
 
 
+def fwd_adj_case(torch, st, wl, n, T, K, dtype, steps, warmup, ws, stream, fw=None):
+    """Differentiable 25-point variable wave workload: one step = the
+    checkpointed forward (T steps, state pair kept every K steps, receiver
+    trace, FP64 misfit) plus the backward (recompute of every segment and the
+    adjoint sweep with FP64 coefficient gradients) through MisfitRunner.
+    GLUP/s = n^3 T / (forward + backward time).  The observed data come from a
+    forward run of the same library with the perturbed model."""
+    from paper_1410_3060_gb300.autograd import MisfitRunner
+    tdt = torch.float64 if dtype == st.F64 else torch.float32
+    if fw is None:
+        fw = wl.fwi(n, T=T, K=K, seed=0)
+    nx, ny, nz = fw.n
+    run = MisfitRunner(wl.W25_VAR, fw.n, T, K, fw.rcv_z, dtype=dtype)
+    u0 = torch.from_numpy(fw.u0).to("cuda", tdt)
+    W = torch.from_numpy(fw.W).to("cuda", tdt)
+    Wt = torch.from_numpy(fw.W_true).to("cuda", tdt)
+    d = torch.zeros((T, ny, nx), device="cuda", dtype=tdt)
+    up, uc = u0.clone(), u0.clone()
+    run.plan.forward(up, uc, None, Wt, T, trace=d, rcv_z=fw.rcv_z)
+    del up, uc, Wt
+
+    def one():
+        loss, state = run.forward_pass(u0, W, d)
+        du0, dW = run.backward_pass(state, W, torch.ones((), dtype=torch.float64))
+        return loss, du0, dW
+
+    for _ in range(warmup):
+        one()
+    barrier(torch, ws)
+    t_f = t_b = 0.0
+    for _ in range(steps):
+        with Timer(torch, stream) as tf:
+            loss, state = run.forward_pass(u0, W, d)
+        with Timer(torch, stream) as tb:
+            run.backward_pass(state, W, torch.ones((), dtype=torch.float64))
+        t_f += tf.ms
+        t_b += tb.ms
+        del state
+    barrier(torch, ws)
+    ms = max_over_ranks(torch, ws, (t_f + t_b) / steps)
+    lups = float(nx) * ny * nz * T
+    res = {"kind": "w25_var_fwd_adj", "n": n, "T": T, "K": K, "dtype": "f64" if dtype == st.F64 else "f32",
+           "ms_per_step": ms, "glups": lups * ws / (ms * 1e-3) / 1e9,
+           "forward_ms": t_f / steps, "backward_ms": t_b / steps,
+           "forward_glups": lups / (t_f / steps * 1e-3) / 1e9, "loss": float(loss.item()),
+           "time_block": run.plan.get(st.OPT_TIME_BLOCK), "variant": run.plan.get(st.OPT_VARIANT)}
+    run.close()
+    del u0, W, d
+    torch.cuda.empty_cache()
+    return res, fw
+
+
 def run_sweep(args, torch, st, wl, pm, stream, ws, peak_f64, hbm_peak, peak_f32):
     """Tuning sweep (the auto-tuning of tile parameters): every forward tile
     variant and block depth of every kind and dtype at the given size; one
@@ -367,6 +419,11 @@ def run_ours(args):
             r["roofline"] = roofline_of(pm, vk, r["dtype"], n, r, peak_f64, hbm_peak, peak_f32)
             variants.append(r)
         cache.clear()
+        # forward + adjoint of the differentiable wave workload (256^3, T = 200, K = 20)
+        fw = None
+        for vd in (st.F32, st.F64):
+            r, fw = fwd_adj_case(torch, st, wl, 256, 200, 20, vd, 1, 1, ws, stream, fw=fw)
+            variants.append(r)
 
     cpu = None
     if rank == 0 and not args.no_cpu:
