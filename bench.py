@@ -252,6 +252,12 @@ def forward_case(torch, st, wl, kind, n, T, dtype, steps, warmup, ws, stream, ti
     return res, wk
 
 
+# DRAM bytes per update measured by ncu (dram__bytes_read.sum +
+# dram__bytes_write.sum of one launch / updates of that launch) for the kernel
+# configurations summarised under profiles/; the roofline record reports them
+# scaled to one launch of the benchmarked size, null for any other kernel.
+MEASURED_TRAFFIC = {("j7_var", "f64", 1, 8): (72.5, "profiles/plain_stream_j7_var_256_fp64.md")}
+
 KIND_BY_NAME = {"j7_const": 1, "j7_var": 2, "w25_const": 3, "w25_var": 4, "j25_var": 5, "w25_alpha": 6}
 KIND_TEXT = {1: "7-point constant coefficients (Fig. 1b)", 2: "7-point variable coefficients (Fig. 1c)",
              3: "25-point constant-coefficient wave (Fig. 1e, scalar alpha)",
@@ -397,6 +403,10 @@ def run_ours(args):
                                variant=args.variant)
     clocks = sampler.summary()
     roofline = roofline_of(pm, kind, args.dtype, n, main, peak_f64, hbm_peak, peak_f32)
+    tr = MEASURED_TRAFFIC.get((args.kind, args.dtype, main["time_block"], main["variant"]))
+    if tr is not None:
+        roofline["traffic"] = tr[0] * float(n) ** 3
+        roofline["traffic_source"] = tr[1] + " (bytes per update x updates per launch)"
     roofline["kernel"] = ("plain_sweep_kernel" if main["time_block"] == 1 else "blocked_kernel (phase A + B)") + \
         f"<{'double' if dtype == st.F64 else 'float'}, {args.kind}>"
     roofline["peak_source"] = ("2 FP64 FMA/clk/SM x %d SMs x %.0f MHz (measured clock); FMA-chain probe %.3f TFLOP/s"
