@@ -52,6 +52,8 @@ def parse():
     p.add_argument("--scheme", type=int, default=None, help="1 overlapped tiles, 2 diamond tiles in y")
     p.add_argument("--variant", type=int, default=None, help="plain forward tile variant (0 = default)")
     p.add_argument("--sweep", action="store_true", help="time every tile variant and block depth, one line each")
+    p.add_argument("--fwd-adj", action="store_true",
+                   help="time only the forward+adjoint of the differentiable wave workload (size --n, T --T)")
     p.add_argument("--no-variants", action="store_true")
     p.add_argument("--no-cpu", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
@@ -393,6 +395,10 @@ def run_ours(args):
 
     if args.sweep:
         run_sweep(args, torch, st, wl, pm, stream, ws, peak_f64, hbm_peak, peak_f32)
+        return
+    if args.fwd_adj:
+        r, _ = fwd_adj_case(torch, st, wl, n, T, 20, dtype, args.steps, args.warmup, ws, stream)
+        print(json.dumps({"fwd_adj": r}), flush=True)
         return
     dev_index = torch.cuda.current_device()
     sampler = ClockSampler(dev_index)
