@@ -8,8 +8,8 @@
 //   W25_VAR / J25_VAR (Fig. 1d structure): u^n(x) for k = 0, the pair
 //           u^n(x + r e_a) + u^n(x - r e_a) for k = 3(r-1)+a+1
 //   W25_ALPHA (Fig. 1e): w0 u^n(x) + sum_r w_r (pairs along x, y, z)
-// The batch sum is kept in FP64 registers and added to the FP64 gradient
-// arrays once per batch.
+// The batch sum is added to the FP64 gradient arrays once per batch (see
+// grad_kernel for how FP32 plans form it).
 #include <algorithm>
 #include <mutex>
 
@@ -17,6 +17,42 @@
 
 namespace stc {
 
+// Per-step gradient terms d_k of one point (FP64 plans: in FP64; FP32
+// plans: products of the FP32 fields formed in FP32).
+template <typename T, int KIND>
+__device__ __forceinline__ void grad_terms(const T *u, const T l, const Geom &g, const Scalars &s, T *d) {
+    if constexpr (KIND == J7_VAR) {
+        const int64_t o[7] = {0, -1, 1, -g.sy, g.sy, -g.sz, g.sz};
+#pragma unroll
+        for (int k = 0; k < 7; ++k) d[k] = l * u[o[k]];
+    } else if constexpr (KIND == W25_VAR || KIND == J25_VAR) {
+        d[0] = l * u[0];
+        const int64_t st[3] = {1, g.sy, g.sz};
+#pragma unroll
+        for (int r = 1; r <= 4; ++r)
+#pragma unroll
+            for (int ax = 0; ax < 3; ++ax) {
+                const int64_t off = r * st[ax];
+                d[3 * (r - 1) + ax + 1] = l * (u[-off] + u[off]);
+            }
+    } else {  // W25_ALPHA: d(alpha L u)/d alpha = L u
+        T sum = T(s.c[0]) * u[0];
+#pragma unroll
+        for (int r = 1; r <= 4; ++r) {
+            const int64_t sy = g.sy, sz = g.sz;
+            const T pr = ((u[-r] + u[r]) + (u[-r * sy] + u[r * sy])) + (u[-r * sz] + u[r * sz]);
+            sum = fma(T(s.c[r]), pr, sum);
+        }
+        d[0] = l * sum;
+    }
+}
+
+// One thread per interior point; loops over the batch of steps.  FP64
+// plans accumulate the terms in FP64.  FP32 plans form each term in FP32
+// (the fields are FP32) and sum the terms of the batch with compensated
+// (Kahan) FP32 summation -- error of a few FP32 roundings of the batch sum,
+// the order of the rounding of the FP32 terms themselves -- then add the
+// batch sum to the FP64 gradient: the sum over time is carried in FP64.
 template <typename T, int KIND>
 __global__ void __launch_bounds__(256) grad_kernel(const GradArgs<T> a) {
     constexpr int R = KindTraits<KIND>::R;
@@ -27,41 +63,39 @@ __global__ void __launch_bounds__(256) grad_kernel(const GradArgs<T> a) {
     const int z = blockIdx.z;
     if (x >= g.nx || y >= g.ny) return;
     const int64_t idx = (int64_t)(z + R) * g.sz + (int64_t)(y + R) * g.sy + (x + R);
-    double acc[NA];
+    if constexpr (sizeof(T) == 8) {
+        double acc[NA];
 #pragma unroll
-    for (int k = 0; k < NA; ++k) acc[k] = 0.0;
-    for (int s = 0; s < a.nsteps; ++s) {
-        const T *u = a.u[s] + idx;
-        const double l = (double)a.lam[s][idx];
-        if constexpr (KIND == J7_VAR) {
-            const int64_t o[7] = {0, -1, 1, -g.sy, g.sy, -g.sz, g.sz};
+        for (int k = 0; k < NA; ++k) acc[k] = 0.0;
+        for (int s = 0; s < a.nsteps; ++s) {
+            T d[NA];
+            grad_terms<T, KIND>(a.u[s] + idx, a.lam[s][idx], g, a.s, d);
 #pragma unroll
-            for (int k = 0; k < 7; ++k) acc[k] = fma(l, (double)u[o[k]], acc[k]);
-        } else if constexpr (KIND == W25_VAR || KIND == J25_VAR) {
-            acc[0] = fma(l, (double)u[0], acc[0]);
-#pragma unroll
-            for (int r = 1; r <= 4; ++r) {
-                const int64_t st[3] = {1, g.sy, g.sz};
-#pragma unroll
-                for (int ax = 0; ax < 3; ++ax) {
-                    const int64_t d = r * st[ax];
-                    acc[3 * (r - 1) + ax + 1] = fma(l, (double)u[-d] + (double)u[d], acc[3 * (r - 1) + ax + 1]);
-                }
-            }
-        } else {  // W25_ALPHA
-            double sum = a.s.c[0] * (double)u[0];
-#pragma unroll
-            for (int r = 1; r <= 4; ++r) {
-                const int64_t sy = g.sy, sz = g.sz;
-                const double pr = ((double)u[-r] + (double)u[r]) + ((double)u[-r * sy] + (double)u[r * sy]) +
-                                  ((double)u[-r * sz] + (double)u[r * sz]);
-                sum = fma(a.s.c[r], pr, sum);
-            }
-            acc[0] = fma(l, sum, acc[0]);
+            for (int k = 0; k < NA; ++k) acc[k] += d[k];
         }
-    }
 #pragma unroll
-    for (int k = 0; k < NA; ++k) a.grad[(int64_t)k * g.nfield + idx] += acc[k];
+        for (int k = 0; k < NA; ++k) a.grad[(int64_t)k * g.nfield + idx] += acc[k];
+    } else {
+        float sum[NA], cmp[NA];
+#pragma unroll
+        for (int k = 0; k < NA; ++k) { sum[k] = 0.f; cmp[k] = 0.f; }
+        for (int s = 0; s < a.nsteps; ++s) {
+            T d[NA];
+            grad_terms<T, KIND>(a.u[s] + idx, a.lam[s][idx], g, a.s, d);
+#pragma unroll
+            for (int k = 0; k < NA; ++k) {
+                // compensated summation; __fadd_rn / __fsub_rn keep the
+                // compensation from being reassociated away
+                const float yk = __fsub_rn(d[k], cmp[k]);
+                const float tk = __fadd_rn(sum[k], yk);
+                cmp[k] = __fsub_rn(__fsub_rn(tk, sum[k]), yk);
+                sum[k] = tk;
+            }
+        }
+#pragma unroll
+        for (int k = 0; k < NA; ++k)
+            a.grad[(int64_t)k * g.nfield + idx] += (double)sum[k] - (double)cmp[k];
+    }
 }
 
 template <typename T>

@@ -39,16 +39,23 @@ static cudaError_t launch_forward(const SweepArgs<T> &a, cudaStream_t st, int nu
     }
 }
 
+// Adjoint sweep of the variable-coefficient kinds: the streaming kernel with
+// the transposed operator (source-point coefficients prefetched in
+// registers).  Variant 5 selects the register-staged plain kernel instead.
 template <typename T, int KIND>
 static cudaError_t launch_adjoint_var(const SweepArgs<T> &a, cudaStream_t st, int num_sms) {
     constexpr int R = KindTraits<KIND>::R;
-    if constexpr (sizeof(T) == 4) {
-        if constexpr (R == 1) return launch_cfg<T, KIND, true, 64, 4, 8, 2>(a, st, num_sms);
-        else return launch_cfg<T, KIND, true, 32, 8, 4, 2>(a, st, num_sms);
-    } else {
-        if constexpr (R == 1) return launch_cfg<T, KIND, true, 32, 8, 4, 2>(a, st, num_sms);
-        else return launch_cfg<T, KIND, true, 32, 8, 2, 2>(a, st, num_sms);
+    if (a.variant == 5) {
+        if constexpr (sizeof(T) == 4) {
+            if constexpr (R == 1) return launch_cfg<T, KIND, true, 64, 4, 8, 2>(a, st, num_sms);
+            else return launch_cfg<T, KIND, true, 32, 8, 4, 2>(a, st, num_sms);
+        } else {
+            if constexpr (R == 1) return launch_cfg<T, KIND, true, 32, 8, 4, 2>(a, st, num_sms);
+            else return launch_cfg<T, KIND, true, 32, 8, 2, 2>(a, st, num_sms);
+        }
     }
+    if constexpr (R == 1) return launch_stream<T, KIND, 32, 8, 2, 2, false, true>(a, st, num_sms);
+    else return launch_stream<T, KIND, 32, 8, 1, 2, false, true>(a, st, num_sms);
 }
 
 template <typename T>

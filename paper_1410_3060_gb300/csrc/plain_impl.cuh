@@ -242,12 +242,23 @@ plain_sweep_kernel(const SweepArgs<T> a) {
 //  * the per-point inputs of an output plane (u^{t-1}, coefficients, no
 //    halo) are loaded into registers one iteration before use;
 //  * receiver trace / residual injection are handled once per plane.
-template <typename T, int KIND, int TX, int BY, int NR, int PD, bool STAGE = false>
+// ADJ: the adjoint sweep of a variable-coefficient kind.  The transpose
+// gathers each term's coefficient at its source point,
+// (A^T y)(q) = sum_k A_k(q - o_k) y(q - o_k); those NC coefficient values per
+// point (7 for Fig. 1c, 25 for the 25-point kinds) are the per-point inputs
+// that travel one iteration ahead in registers.
+template <int KIND, bool ADJ> struct PointCoeffs { static constexpr int value = KindTraits<KIND>::NARR; };
+template <int KIND> struct PointCoeffs<KIND, true> {
+    static constexpr int value = KindTraits<KIND>::NARR == 0 ? 0 : (KindTraits<KIND>::R == 1 ? 7 : 25);
+};
+
+template <typename T, int KIND, int TX, int BY, int NR, int PD, bool STAGE = false, bool ADJ = false>
 __global__ void __launch_bounds__(TX * BY)
 plain_stream_kernel(const SweepArgs<T> a) {
     constexpr int R = KindTraits<KIND>::R;
     constexpr bool WAVE = KindTraits<KIND>::WAVE;
-    constexpr int NA = KindTraits<KIND>::NARR;
+    constexpr int NA = PointCoeffs<KIND, ADJ>::value;
+    static_assert(!(ADJ && STAGE), "the adjoint sweep keeps its per-point inputs in registers");
     constexpr int TY = BY * NR;
     constexpr int SW = TX + 2 * R;
     constexpr int SH = TY + 2 * R;
@@ -319,8 +330,36 @@ plain_stream_kernel(const SweepArgs<T> a) {
                 if (!(rowok & (1u << jr))) continue;
                 const int64_t off = base + jr * sy;
                 if constexpr (WAVE) pnx[0][jr] = a.u_prev[off];
+                constexpr int CO = WAVE ? 1 : 0;
+                if constexpr (!ADJ) {
 #pragma unroll
-                for (int t = 0; t < NA; ++t) pnx[(WAVE ? 1 : 0) + t][jr] = a.W[off + t * g.nfield];
+                    for (int t = 0; t < NA; ++t) pnx[CO + t][jr] = a.W[off + t * g.nfield];
+                } else if constexpr (R == 1) {
+                    // source points of Fig. 1c's terms: q, q+x, q-x, q+y, q-y, q+z, q-z
+                    const int64_t n = g.nfield, sz = g.sz;
+                    pnx[CO + 0][jr] = a.W[off];
+                    pnx[CO + 1][jr] = a.W[off + n + 1];
+                    pnx[CO + 2][jr] = a.W[off + 2 * n - 1];
+                    pnx[CO + 3][jr] = a.W[off + 3 * n + sy];
+                    pnx[CO + 4][jr] = a.W[off + 4 * n - sy];
+                    pnx[CO + 5][jr] = a.W[off + 5 * n + sz];
+                    pnx[CO + 6][jr] = a.W[off + 6 * n - sz];
+                } else {
+                    // 25-point kinds: centre, then per (r, axis) the coefficient at
+                    // q - r e_a and at q + r e_a (alpha for the alpha-array kind)
+                    const int64_t n = g.nfield;
+                    const int64_t st3[3] = {1, (int64_t)sy, g.sz};
+                    pnx[CO][jr] = a.W[off];
+#pragma unroll
+                    for (int r = 1; r <= 4; ++r)
+#pragma unroll
+                        for (int ax = 0; ax < 3; ++ax) {
+                            const int64_t arr = (KIND == W25_ALPHA) ? 0 : (int64_t)(3 * (r - 1) + ax + 1) * n;
+                            const int64_t d = r * st3[ax];
+                            pnx[CO + 1 + 2 * (3 * (r - 1) + ax)][jr] = a.W[off + arr - d];
+                            pnx[CO + 2 + 2 * (3 * (r - 1) + ax)][jr] = a.W[off + arr + d];
+                        }
+                }
             }
         }
     };
@@ -439,7 +478,46 @@ plain_stream_kernel(const SweepArgs<T> a) {
                 const T pv = WAVE ? pin[0][jr] : T(0);
                 (void)pv;
                 T v;
-                if constexpr (KIND == J7_CONST) {
+                if constexpr (ADJ && KIND == J7_VAR) {
+                    const T *q = &pin[CO][0];
+                    (void)q;
+                    v = pin[CO + 0][jr] * c;
+                    v = fma(pin[CO + 1][jr], xn[0][1], v);
+                    v = fma(pin[CO + 2][jr], xn[0][0], v);
+                    v = fma(pin[CO + 3][jr], yn[0][1], v);
+                    v = fma(pin[CO + 4][jr], yn[0][0], v);
+                    v = fma(pin[CO + 5][jr], zn[0][1], v);
+                    v = fma(pin[CO + 6][jr], zn[0][0], v);
+                } else if constexpr (ADJ && KIND == W25_ALPHA) {
+                    const T wr[4] = {s1, s2, s3, s4};
+                    T sacc = s0 * (pin[CO][jr] * c);
+#pragma unroll
+                    for (int d = 0; d < 4; ++d) {
+                        const int b = CO + 1 + 6 * d;
+                        T pr = pin[b][jr] * xn[d][0];
+                        pr = fma(pin[b + 1][jr], xn[d][1], pr);
+                        pr = fma(pin[b + 2][jr], yn[d][0], pr);
+                        pr = fma(pin[b + 3][jr], yn[d][1], pr);
+                        pr = fma(pin[b + 4][jr], zn[d][0], pr);
+                        pr = fma(pin[b + 5][jr], zn[d][1], pr);
+                        sacc = fma(wr[d], pr, sacc);
+                    }
+                    v = sacc + (T(2) * c - pv);
+                } else if constexpr (ADJ) {  // W25_VAR, J25_VAR
+                    T acc = pin[CO][jr] * c;
+                    if constexpr (WAVE) acc = fma(T(2), c, acc) - pv;
+#pragma unroll
+                    for (int d = 0; d < 4; ++d) {
+                        const int b = CO + 1 + 6 * d;
+                        acc = fma(pin[b][jr], xn[d][0], acc);
+                        acc = fma(pin[b + 1][jr], xn[d][1], acc);
+                        acc = fma(pin[b + 2][jr], yn[d][0], acc);
+                        acc = fma(pin[b + 3][jr], yn[d][1], acc);
+                        acc = fma(pin[b + 4][jr], zn[d][0], acc);
+                        acc = fma(pin[b + 5][jr], zn[d][1], acc);
+                    }
+                    v = acc;
+                } else if constexpr (KIND == J7_CONST) {
                     v = s0 * c + s1 * (((xn[0][0] + xn[0][1]) + (yn[0][0] + yn[0][1])) + (zn[0][0] + zn[0][1]));
                 } else if constexpr (KIND == J7_VAR) {
                     v = pin[0][jr] * c;
@@ -542,13 +620,13 @@ static cudaError_t launch_cfg(const SweepArgs<T> &a, cudaStream_t st, int num_sm
     return cudaGetLastError();
 }
 
-template <typename T, int KIND, int TX, int BY, int NR, int PD, bool STAGE = false>
+template <typename T, int KIND, int TX, int BY, int NR, int PD, bool STAGE = false, bool ADJ = false>
 static cudaError_t launch_stream(const SweepArgs<T> &a, cudaStream_t st, int num_sms) {
     constexpr int R = KindTraits<KIND>::R;
     constexpr int TY = BY * NR;
     constexpr size_t smem = stream_smem<T, KIND, TX, BY, NR, PD, STAGE>();
     static_assert(smem <= 227 * 1024, "shared memory per CTA");
-    auto kern = plain_stream_kernel<T, KIND, TX, BY, NR, PD, STAGE>;
+    auto kern = plain_stream_kernel<T, KIND, TX, BY, NR, PD, STAGE, ADJ>;
     SweepArgs<T> b = a;
     dim3 grid;
     cudaError_t e = launch_grid(kern, smem, TX, BY, TY, R, nullptr, a.g.nx, a.g.ny, a.g.nz, num_sms, &b.zchunk, &grid);

@@ -82,7 +82,8 @@ def rand_interior(n, R, rng):
 
 @pytest.mark.parametrize("kind", KINDS)
 @pytest.mark.parametrize("dtype", [F64, F32])
-def test_adjoint_with_residual_and_gradient(st, kind, dtype):
+@pytest.mark.parametrize("variant", [0, 5])
+def test_adjoint_with_residual_and_gradient(st, kind, dtype, variant):
     import torch
     rng = np.random.default_rng(10 + kind)
     n = (37, 29, 21)
@@ -102,6 +103,7 @@ def test_adjoint_with_residual_and_gradient(st, kind, dtype):
     ol2, ol1 = oracle.adjoint(kind, cast(l2), cast(l1), wk.w, W, T, states=cast(states), residual=cast(res),
                               rcv_z=rz, grad=og, threads=8)
     plan = st.Plan(kind, *n, dtype)
+    plan.set(st.OPT_VARIANT, variant)
     gl2, gl1 = to_dev(l2, dtype), to_dev(l1, dtype)
     gst = [to_dev(s, dtype) for s in states]
     gg = torch.zeros((k,) + l1.shape, device="cuda", dtype=torch.float64) if k else None
