@@ -183,6 +183,11 @@ int stencil_adjoint(stencil_plan_t plan, void *lam_next, void *lam, const stenci
 int stencil_axpby(stencil_plan_t plan, int64_t n, double alpha, const void *x, double beta,
                   const void *y, void *out, void *stream);
 
+/* Set `bytes` bytes of device memory to zero on `stream` (asynchronous
+ * cudaMemsetAsync): clears the caller's state, adjoint and gradient arrays
+ * (whose halos must be zero) without leaving the library. */
+int stencil_fill_zero(void *ptr, int64_t bytes, void *stream);
+
 /* Receiver misfit of T traces: residual = trace - d (plan dtype, may alias
  * neither input unless equal to trace), and *loss (device FP64) =
  * 0.5 * sum (trace - d)^2 accumulated in FP64 in a fixed order

@@ -42,7 +42,7 @@ class _MisfitFn(torch.autograd.Function):
         (W,) = ctx.saved_tensors
         du0, dW = ctx.runner.backward_pass(ctx.state, W, gloss)
         ctx.state = None
-        return du0, dW.to(W.dtype), None, None
+        return du0.clone(), dW.to(W.dtype), None, None
 
 
 class MisfitRunner:
@@ -54,13 +54,31 @@ class MisfitRunner:
     kind (W25_ALPHA) or None.
     """
 
-    def __init__(self, kind, n, T, K, rcv_z, dtype=st.F32, w=None, grad_batch=8, time_block=None):
+    def __init__(self, kind, n, T, K, rcv_z, dtype=st.F32, w=None, grad_batch=8, time_block=None,
+                 device="cuda"):
         self.kind, self.n, self.T, self.K, self.rcv_z, self.w = kind, tuple(n), int(T), int(K), int(rcv_z), w
         self.plan = st.Plan(kind, *n, dtype)
         if time_block is not None:
             self.plan.set(st.OPT_TIME_BLOCK, time_block)
         self.plan.set(st.OPT_GRAD_BATCH, max(1, min(grad_batch, 16)))
         self.dtype = self.plan.torch_dtype()
+        # every buffer of a forward/backward pair is allocated once here (torch
+        # owns the memory); the passes only clear them through the library
+        nx, ny, nz = self.n
+        shape = self.plan.padded_shape
+        new = lambda *s_, dt=None: torch.empty(s_, device=device, dtype=dt or self.dtype)  # noqa: E731
+        nck = (self.T + self.K - 1) // self.K
+        self._ckpt = [(new(*shape), new(*shape)) for _ in range(nck)]
+        self._state = (new(*shape), new(*shape))
+        self._trace = new(self.T, ny, nx)
+        self._res = new(self.T + 1, ny, nx)
+        self._loss = new(1, dt=torch.float64)
+        self._lam = (new(*shape), new(*shape))
+        self._grad = new(st.NUM_ARRAYS[kind], *shape, dt=torch.float64)
+        self._bufs = [new(*shape) for _ in range(self.K)]
+        self._du0 = new(*shape)
+        for b in self._bufs:
+            st.fill_zero(b)   # zero halos (only interiors are ever written)
 
     def close(self):
         self.plan.close()
@@ -71,21 +89,26 @@ class MisfitRunner:
 
     # -- forward: checkpoints, trace, loss
     def forward_pass(self, u0, W, d):
-        T, K, (nx, ny, nz) = self.T, self.K, self.n
-        dev = u0.device
-        up, u = u0.detach().clone(), u0.detach().clone()
-        trace = torch.empty((T, ny, nx), device=dev, dtype=self.dtype)
+        T, K = self.T, self.K
+        up, u = self._state
+        u0d = u0.detach()
+        up.copy_(u0d)
+        u.copy_(u0d)
+        trace = self._trace
         ckpts = []
         t = 0
-        while t < T:
-            ckpts.append((t, up.clone(), u.clone()))
+        for i in range(len(self._ckpt)):
+            cp, cu = self._ckpt[i]
+            cp.copy_(up)
+            cu.copy_(u)
+            ckpts.append((t, cp, cu))
             k = min(K, T - t)
             self.plan.forward(up, u, self.w, W, k, trace=trace[t:t + k], rcv_z=self.rcv_z)
             t += k
-        res = torch.zeros((T + 1, ny, nx), device=dev, dtype=self.dtype)  # res[i] = r^i, r^0 = 0
-        loss = torch.zeros(1, device=dev, dtype=torch.float64)
-        self.plan.misfit(trace, d, res[1:], loss)
-        return loss[0], {"ckpts": ckpts, "res": res, "last": u}
+        res = self._res                      # res[i] = r^i, r^0 = 0
+        st.fill_zero(res[0])
+        self.plan.misfit(trace, d, res[1:], self._loss)
+        return self._loss[0].clone(), {"ckpts": ckpts, "res": res, "last": u}
 
     # -- backward: recompute + adjoint per segment
     def backward_pass(self, state, W, gloss):
@@ -98,11 +121,11 @@ class MisfitRunner:
         g = float(gloss.item())
         if g != 1.0:
             plan.axpby(g, res, 0.0, res, res)
-        shape = plan.padded_shape
-        lam_next = torch.zeros(shape, device=dev, dtype=self.dtype)
-        lam = torch.zeros(shape, device=dev, dtype=self.dtype)
-        grad = torch.zeros((st.NUM_ARRAYS[self.kind],) + shape, device=dev, dtype=torch.float64)
-        bufs = [torch.zeros(shape, device=dev, dtype=self.dtype) for _ in range(K)]  # zero halo
+        lam_next, lam = self._lam
+        grad = self._grad
+        for t_ in (lam_next, lam, grad):
+            st.fill_zero(t_)
+        bufs = self._bufs
         top = True
         for c, cp, cu in reversed(state["ckpts"]):
             k = min(K, T - c)
@@ -118,7 +141,7 @@ class MisfitRunner:
             else:
                 plan.adjoint(lam_next, lam, self.w, W, k, fwd_states=states, residual=res[c:c + k],
                              rcv_z=self.rcv_z, grad=grad)
-        du0 = torch.empty(shape, device=dev, dtype=self.dtype)
+        du0 = self._du0
         if st.SECOND_ORDER[self.kind]:
             plan.axpby(1.0, lam, -1.0, lam_next, du0)
         else:

@@ -640,6 +640,13 @@ int stencil_axpby(stencil_plan_t p, int64_t n, double alpha, const void *x, doub
     return e == cudaSuccess ? STENCIL_OK : cuda_fail(e);
 }
 
+int stencil_fill_zero(void *ptr, int64_t bytes, void *stream) {
+    if (!ptr || bytes < 0) return STENCIL_EINVAL;
+    if (bytes == 0) return STENCIL_OK;
+    cudaError_t e = cudaMemsetAsync(ptr, 0, (size_t)bytes, (cudaStream_t)stream);
+    return e == cudaSuccess ? STENCIL_OK : cuda_fail(e);
+}
+
 int stencil_misfit(stencil_plan_t p, const void *trace, const void *d, int64_t T, void *residual, double *loss,
                    void *stream) {
     if (!p || !trace || !d || !residual || !loss || T < 0) return STENCIL_EINVAL;

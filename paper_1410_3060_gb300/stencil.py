@@ -26,7 +26,7 @@ SECOND_ORDER = {J7_CONST: False, J7_VAR: False, W25_CONST: True, W25_VAR: True, 
 # every symbol include/stencil.h declares
 EXPORTED = ("stencil_plan", "stencil_plan_set", "stencil_plan_get", "stencil_plan_destroy",
             "stencil_forward", "stencil_forward_states", "stencil_adjoint", "stencil_axpby",
-            "stencil_misfit", "stencil_misfit_static", "stencil_schedule", "stencil_fma_peak",
+            "stencil_misfit", "stencil_misfit_static", "stencil_fill_zero", "stencil_schedule", "stencil_fma_peak",
             "stencil_strerror", "stencil_last_cuda_error")
 MISFIT_STATIC_MAX_ELEMS = 8192 * 2048
 
@@ -74,6 +74,7 @@ def lib():
             L.stencil_forward_states.argtypes = [vp, vp, vp, ctypes.POINTER(_Coeffs), i64, ctypes.POINTER(vp), vp,
                                                  vp, i64]
             L.stencil_misfit_static.argtypes = [i32, vp, vp, i64, vp, vp, vp]
+            L.stencil_fill_zero.argtypes = [vp, i64, vp]
             L.stencil_axpby.argtypes = [vp, i64, ctypes.c_double, vp, ctypes.c_double, vp, vp, vp]
             L.stencil_schedule.argtypes = [i32, i32, i64, i32, ctypes.POINTER(ctypes.c_int32), i64,
                                            ctypes.POINTER(i64)]
@@ -83,7 +84,7 @@ def lib():
             L.stencil_last_cuda_error.argtypes = []
             for fn in ("stencil_plan", "stencil_plan_set", "stencil_plan_get", "stencil_forward",
                        "stencil_forward_states", "stencil_adjoint", "stencil_axpby", "stencil_misfit",
-                       "stencil_misfit_static",
+                       "stencil_misfit_static", "stencil_fill_zero",
                        "stencil_schedule", "stencil_fma_peak", "stencil_last_cuda_error"):
                 getattr(L, fn).restype = i32
             _lib = L
@@ -127,6 +128,14 @@ def misfit_static(trace, d, residual, loss, stream=None):
         raise ValueError("trace: contiguous CUDA tensor; loss: CUDA float64")
     _check("stencil_misfit_static", lib().stencil_misfit_static(dtype, _ptr(trace), _ptr(d), int(trace.numel()),
                                                                 _ptr(residual), _ptr(loss), _stream_handle(stream)))
+
+
+def fill_zero(t, stream=None):
+    """stencil_fill_zero: zero a contiguous CUDA tensor (asynchronous memset)."""
+    if not t.is_cuda or not t.is_contiguous():
+        raise ValueError("fill_zero: contiguous CUDA tensor expected")
+    _check("stencil_fill_zero", lib().stencil_fill_zero(_ptr(t), int(t.numel() * t.element_size()),
+                                                        _stream_handle(stream)))
 
 
 def fma_peak(dtype: int, stream=None):
