@@ -78,6 +78,9 @@ def cpu_oracle_rate(kind, wk, T_sample, threads):
 
 
 def run_reference(args):
+    """The reference arm: the FP64 CPU oracle (plain C loops of the naive
+    sweep, all host cores) on a bounded sample of the same workload -- one
+    time step of the full grid per step."""
     ws, rank, _ = dist_env()
     if rank != 0:
         return
@@ -85,21 +88,23 @@ def run_reference(args):
     from paper_1410_3060_gb300 import workloads as wl
     oracle.build()
     threads = oracle.oracle.default_threads()
-    wk = wl.j7_var(args.n, args.T, seed=0)
+    kind = KIND_BY_NAME[args.kind]
+    wk = wl.make(kind, args.n, args.T, seed=0) if kind != wl.J7_VAR else wl.j7_var(args.n, args.T, seed=0)
     T_sample = 1
     for _ in range(args.warmup):
-        cpu_oracle_rate(wl.J7_VAR, wk, T_sample, threads)
-    rates = [cpu_oracle_rate(wl.J7_VAR, wk, T_sample, threads)[0] for _ in range(args.steps)]
+        cpu_oracle_rate(kind, wk, T_sample, threads)
+    rates = [cpu_oracle_rate(kind, wk, T_sample, threads)[0] for _ in range(args.steps)]
     v = statistics.median(rates)
     n3 = args.n ** 3
+    sample = f"{T_sample} time step of the {args.n}^3 {args.kind} sweep per step (FP64 plain C loops, {threads} threads)"
     line = {
         "impl": "reference", "metric": METRIC, "value": v, "unit": METRIC, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": n3 * T_sample / (v * 1e9) * 1e3,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic",
-        "config": {"workload": f"j7_var_{args.n}^3_fp64", "sample": f"{T_sample} time step of the {args.n}^3 grid per step"},
-        "cpu_baseline": {"value": v, "unit": METRIC, "cores": threads, "kind": "oracle",
-                         "sample": f"{T_sample} step of the {args.n}^3 7-point variable-coefficient sweep, FP64, plain C loops"},
+        "config": {"workload": f"{args.kind}_{args.n}^3_T{args.T}_{args.dtype}", "kind": KIND_TEXT[kind],
+                   "n": args.n, "T": args.T, "sample": sample},
+        "cpu_baseline": {"value": v, "unit": METRIC, "cores": threads, "kind": "oracle", "sample": sample},
         "e2e": {"value": v, "unit": METRIC, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
