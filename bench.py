@@ -163,9 +163,11 @@ class ClockSampler:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"]}
         # samples under load: top half of the clock samples by power
         ranked = sorted(zip(power, sm), reverse=True)
-        load = [s for _, s in ranked[:max(1, len(ranked) // 2)]]
+        top = ranked[:max(1, len(ranked) // 2)]
+        load = [s for _, s in top]
         return {"sm_mhz": statistics.median(load), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
-                "samples": len(sm), "power_w_max": max(power)}
+                "samples": len(sm), "power_w_max": max(power),
+                "power_w_under_load": statistics.mean(p for p, _ in top)}
 
 
 # --------------------------------------------------------------- ours
@@ -194,12 +196,20 @@ def barrier(torch, ws):
 
 
 def max_over_ranks(torch, ws, v):
+    """Maximum of a per-rank value over all ranks (the slowest replica sets
+    the job time)."""
     if ws == 1:
         return v
     import torch.distributed as dist
-    t = torch.tensor([v], device="cuda", dtype=torch.float64)
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([v], device=dev, dtype=torch.float64)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
+
+
+def job_rate(units_per_rank, ws, ms_max):
+    """Whole-job throughput: units processed by all ranks / slowest rank's time."""
+    return units_per_rank * ws / (ms_max * 1e-3)
 
 
 def forward_case(torch, st, wl, kind, n, T, dtype, steps, warmup, ws, stream, time_block=None, e2e=False,
@@ -465,6 +475,11 @@ def run_ours(args):
                        "l2": "inputs larger than L2 (no flush needed)" if n >= 256 else "small case"},
             "e2e": main.get("e2e"), "gpu_launches": main["launches_per_step"] * args.steps,
             "roofline": roofline, "clocks": clocks, "cpu_baseline": cpu,
+            "energy": ({"joules_per_step": clocks["power_w_under_load"] * main["ms_per_step"] * 1e-3,
+                        "nJ_per_lup": clocks["power_w_under_load"] * main["ms_per_step"] * 1e-3
+                        / (float(n) ** 3 * T) * 1e9,
+                        "method": "mean nvidia-smi board power of the loaded half of the samples x time per step"}
+                       if clocks.get("power_w_under_load") else None),
             "peaks_measured": {"fp64_fma_probe_tflops": probe_f64 / 1e12, "fp32_fma_probe_tflops": probe_f32 / 1e12,
                                "fp64_peak_tflops": peak_f64 / 1e12, "fp32_peak_tflops": peak_f32 / 1e12,
                                "sm_clock_mhz": clk / 1e6, "hbm_gbs": hbm_peak},
