@@ -54,7 +54,7 @@ class MisfitRunner:
     kind (W25_ALPHA) or None.
     """
 
-    def __init__(self, kind, n, T, K, rcv_z, dtype=st.F32, w=None, grad_batch=8, time_block=None,
+    def __init__(self, kind, n, T, K, rcv_z, dtype=st.F32, w=None, grad_batch=16, time_block=None,
                  device="cuda"):
         self.kind, self.n, self.T, self.K, self.rcv_z, self.w = kind, tuple(n), int(T), int(K), int(rcv_z), w
         self.plan = st.Plan(kind, *n, dtype)

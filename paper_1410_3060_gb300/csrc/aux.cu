@@ -63,15 +63,20 @@ __global__ void __launch_bounds__(256) grad_kernel(const GradArgs<T> a) {
     const int z = blockIdx.z;
     if (x >= g.nx || y >= g.ny) return;
     const int64_t idx = (int64_t)(z + R) * g.sz + (int64_t)(y + R) * g.sy + (x + R);
+    // software pipeline: the terms of step s + 1 are loaded and formed before
+    // the terms of step s are summed, so the loads of two steps are in flight
+    T d[NA], dn[NA];
+    if (a.nsteps > 0) grad_terms<T, KIND>(a.u[0] + idx, a.lam[0][idx], g, a.s, d);
     if constexpr (sizeof(T) == 8) {
         double acc[NA];
 #pragma unroll
         for (int k = 0; k < NA; ++k) acc[k] = 0.0;
         for (int s = 0; s < a.nsteps; ++s) {
-            T d[NA];
-            grad_terms<T, KIND>(a.u[s] + idx, a.lam[s][idx], g, a.s, d);
+            if (s + 1 < a.nsteps) grad_terms<T, KIND>(a.u[s + 1] + idx, a.lam[s + 1][idx], g, a.s, dn);
 #pragma unroll
             for (int k = 0; k < NA; ++k) acc[k] += d[k];
+#pragma unroll
+            for (int k = 0; k < NA; ++k) d[k] = dn[k];
         }
 #pragma unroll
         for (int k = 0; k < NA; ++k) a.grad[(int64_t)k * g.nfield + idx] += acc[k];
@@ -80,8 +85,7 @@ __global__ void __launch_bounds__(256) grad_kernel(const GradArgs<T> a) {
 #pragma unroll
         for (int k = 0; k < NA; ++k) { sum[k] = 0.f; cmp[k] = 0.f; }
         for (int s = 0; s < a.nsteps; ++s) {
-            T d[NA];
-            grad_terms<T, KIND>(a.u[s] + idx, a.lam[s][idx], g, a.s, d);
+            if (s + 1 < a.nsteps) grad_terms<T, KIND>(a.u[s + 1] + idx, a.lam[s + 1][idx], g, a.s, dn);
 #pragma unroll
             for (int k = 0; k < NA; ++k) {
                 // compensated summation; __fadd_rn / __fsub_rn keep the
@@ -91,6 +95,8 @@ __global__ void __launch_bounds__(256) grad_kernel(const GradArgs<T> a) {
                 cmp[k] = __fsub_rn(__fsub_rn(tk, sum[k]), yk);
                 sum[k] = tk;
             }
+#pragma unroll
+            for (int k = 0; k < NA; ++k) d[k] = dn[k];
         }
 #pragma unroll
         for (int k = 0; k < NA; ++k)
