@@ -296,8 +296,14 @@ blocked_kernel(const BlockedArgs<T> a) {
                     const int ry = ty * NR + jr;
                     const bool in = zin && (ymask & (1u << jr));
                     T v = T(0);
-                    if (Rw::computed(k, ry)) {
-                        if (in) {
+                    // Overlapped / phase-A tiles compute every row at every level
+                    // without a branch: rows outside the level's valid band hold
+                    // values that only feed rows that are never stored (the valid
+                    // band shrinks by R per level); points outside the interior
+                    // take the zero Dirichlet value by a select.  Phase-B tiles
+                    // compute their growing band and load the rest from the bands.
+                    if (PHASE != PH_B || Rw::computed(k, ry)) {
+                        if (PHASE != PH_B || in) {
                             const T *cp = rowp + jr * PX;
                             const T c = ring[k - 1][jc][jr];
                             T xn[R][2], yn[R][2], zn[R][2];
@@ -355,7 +361,8 @@ blocked_kernel(const BlockedArgs<T> a) {
                                 }
                                 v = acc;
                             }
-                            if (zown && xown) {
+                            if constexpr (PHASE != PH_B) v = in ? v : T(0);
+                            if (in && zown && xown && Rw::computed(k, ry)) {
                                 if (Rw::owned(k, ry)) {
                                     if (z == a.rcv_z && a.trace)
                                         a.trace[(k - 1) * plane_elems + (int64_t)(Y0 + ry) * g.nx + x] = v;
