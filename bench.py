@@ -49,9 +49,13 @@ def parse():
                                                           "j25_var", "w25_alpha"])
     p.add_argument("--dtype", default="f64", choices=["f64", "f32"])
     p.add_argument("--time-block", type=int, default=None, help="levels per pass (default: library choice)")
-    p.add_argument("--scheme", type=int, default=None, help="1 overlapped tiles, 2 diamond tiles in y")
+    p.add_argument("--scheme", type=int, default=None,
+                   help="1 overlapped tiles, 2 diamond tiles in y, 3 register wavefront")
     p.add_argument("--variant", type=int, default=None, help="plain forward tile variant (0 = default)")
     p.add_argument("--sweep", action="store_true", help="time every tile variant and block depth, one line each")
+    p.add_argument("--sweep-kinds", default="j7_const,j7_var,w25_const,w25_var",
+                   help="comma-separated kinds of the tuning sweep")
+    p.add_argument("--sweep-dtypes", default="f64,f32", help="comma-separated dtypes of the tuning sweep")
     p.add_argument("--fwd-adj", action="store_true",
                    help="time only the forward+adjoint of the differentiable wave workload (size --n, T --T)")
     p.add_argument("--no-variants", action="store_true")
@@ -363,23 +367,25 @@ def run_sweep(args, torch, st, wl, pm, stream, ws, peak_f64, hbm_peak, peak_f32)
     variant and block depth of every kind and dtype at the given size; one
     JSON line per case."""
     n, T = args.n, args.T
-    for kind in (wl.J7_CONST, wl.J7_VAR, wl.W25_CONST, wl.W25_VAR):
+    kinds = [KIND_BY_NAME[k] for k in args.sweep_kinds.split(",") if k]
+    dtypes = [st.F64 if d == "f64" else st.F32 for d in args.sweep_dtypes.split(",") if d]
+    for kind in kinds:
         wk = wl.make(kind, n, T, seed=0) if kind != wl.J7_VAR else wl.j7_var(n, T, seed=0)
-        for dtype in (st.F64, st.F32):
-            for v in (1, 2, 3, 4, 5, 6, 7, 8, 9):
+        r1 = wl.RADIUS[kind] == 1
+        for dtype in dtypes:
+            for v in (1, 2, 3, 4, 5, 6, 7, 8, 9) + ((10, 11) if r1 else ()):
                 r, _ = forward_case(torch, st, wl, kind, n, T, dtype, args.steps, 1, ws, stream, time_block=1,
                                     wk=wk, variant=v)
                 r["roofline"] = roofline_of(pm, kind, r["dtype"], n, r, peak_f64, hbm_peak, peak_f32)
                 print(json.dumps({"sweep": r}), flush=True)
-            blocked = ((2, 3, 4) if wl.RADIUS[kind] == 1 else (2,)) if dtype == st.F32 else \
-                ((2,) if wl.RADIUS[kind] == 1 else ())
-            if blocked:
-                for b in blocked:
-                    for sch in (1, 2):
-                        r, _ = forward_case(torch, st, wl, kind, n, T, dtype, args.steps, 1, ws, stream,
-                                            time_block=b, wk=wk, scheme=sch)
-                        r["roofline"] = roofline_of(pm, kind, r["dtype"], n, r, peak_f64, hbm_peak, peak_f32)
-                        print(json.dumps({"sweep": r}), flush=True)
+            blocked = ((2, 3, 4) if r1 else (2,)) if dtype == st.F32 else ((2,) if r1 else ())
+            for b in blocked:
+                cases = [(1, None), (2, None)] + ([(3, 10), (3, 11)] if r1 else [])
+                for sch, v in cases:
+                    r, _ = forward_case(torch, st, wl, kind, n, T, dtype, args.steps, 1, ws, stream,
+                                        time_block=b, wk=wk, scheme=sch, variant=v)
+                    r["roofline"] = roofline_of(pm, kind, r["dtype"], n, r, peak_f64, hbm_peak, peak_f32)
+                    print(json.dumps({"sweep": r}), flush=True)
         del wk
 
 

@@ -25,6 +25,7 @@
 #include "../../include/stencil.h"
 #include "plain.cuh"
 #include "blocked.cuh"
+#include "wavefront.cuh"
 
 using namespace stc;
 
@@ -191,9 +192,17 @@ int default_time_block(const stencil_plan_s *p) {
     return blocked_default_levels(p->kind, p->dtype);
 }
 
+// The register wavefront serves a blocked pass of scheme 3 (and a plain
+// pass of tile variant >= 10) when it supports the kind, dtype, depth and
+// geometry; the shared-memory blocked kernels serve schemes 1 and 2.
+bool pass_supported(const stencil_plan_s *p, int levels) {
+    if (p->scheme == 3) return wavefront_supported(p->kind, p->dtype, levels, p->g);
+    return blocked_supported(p->kind, p->dtype, levels);
+}
+
 int effective_time_block(const stencil_plan_s *p) {
     int b = p->time_block > 0 ? p->time_block : default_time_block(p);
-    if (b > 1 && !blocked_supported(p->kind, p->dtype, b)) b = 1;
+    if (b > 1 && !pass_supported(p, b)) b = 1;
     return b;
 }
 
@@ -225,14 +234,50 @@ bool overlap(const void *a, const void *b, size_t n) {
     return x < y + n && y < x + n;
 }
 
+// One plain (one-level) sweep: the register wavefront at depth 1 for tile
+// variants >= 10 where it serves the kind and geometry (forward only), else
+// the plain kernels.
+template <typename T>
+cudaError_t plain_step(stencil_plan_s *p, bool adjoint, const Scalars &s, const stencil_coeffs_t *coeffs,
+                       const void *in_p, const void *in_c, void *out, T *trace, const T *inject, int64_t rcv_z,
+                       cudaStream_t st) {
+    if (!adjoint && p->variant >= 10 && wavefront_supported(p->kind, p->dtype, 1, p->g)) {
+        BlockedArgs<T> w;
+        memset(&w, 0, sizeof(w));
+        w.u = (const T *)in_c;
+        w.out = (T *)out;
+        w.W = coeffs ? (const T *)coeffs->arrays : nullptr;
+        w.s = s;
+        w.g = p->g;
+        w.rcv_z = (int)rcv_z;
+        w.trace = trace;
+        w.levels = 1;
+        return launch_wavefront<T>(p->kind, w, p->variant - 9, st, p->num_sms);
+    }
+    SweepArgs<T> a;
+    memset(&a, 0, sizeof(a));
+    a.u_prev = (const T *)in_p;
+    a.u = (const T *)in_c;
+    a.out = (T *)out;
+    a.W = coeffs ? (const T *)coeffs->arrays : nullptr;
+    a.s = s;
+    a.g = p->g;
+    a.rcv_z = (int)rcv_z;
+    a.trace = trace;
+    a.inject = inject;
+    a.variant = p->variant < 10 ? p->variant : 0;  // 10+: register wavefront tiles
+    return launch_plain<T>(p->kind, adjoint, a, st, p->num_sms);
+}
+
 template <typename T>
 int run_program(stencil_plan_s *p, void *pair_p, void *pair_c, const stencil_coeffs_t *coeffs, int64_t nsteps,
                  cudaStream_t st, bool adjoint, void *trace, const void *inject, int64_t rcv_z,
                  const void *const *fwd_states, double *grad) {
     const int b = effective_time_block(p);
     const int kind = p->kind, dtype = p->dtype;
-    const std::vector<Op> ops =
-        build_program(p->kind, nsteps, b, [&](int L) { return blocked_supported(kind, dtype, L); });
+    (void)kind;
+    (void)dtype;
+    const std::vector<Op> ops = build_program(p->kind, nsteps, b, [&](int L) { return pass_supported(p, L); });
     void *buf[4] = {pair_p, pair_c, p->scratch[0], p->scratch[1]};
     const Scalars s = fold_scalars(p->kind, coeffs);
     const int64_t plane = (int64_t)p->g.nx * p->g.ny;
@@ -266,19 +311,10 @@ int run_program(stencil_plan_s *p, void *pair_p, void *pair_c, const stencil_coe
                 cudaError_t e = cudaMemcpyAsync(buf[o.out_p], buf[o.in_c], p->field_bytes, cudaMemcpyDeviceToDevice, st);
                 if (e != cudaSuccess) return cuda_fail(e);
             }
-            SweepArgs<T> a;
-            memset(&a, 0, sizeof(a));
-            a.u_prev = (const T *)buf[o.in_p];
-            a.u = (const T *)buf[o.in_c];
-            a.out = (T *)buf[o.out_c];
-            a.W = coeffs ? (const T *)coeffs->arrays : nullptr;
-            a.s = s;
-            a.g = p->g;
-            a.rcv_z = (int)rcv_z;
-            a.trace = (!adjoint && trace) ? (T *)trace + t * plane : nullptr;
-            a.inject = (adjoint && inject) ? (const T *)inject + (nsteps - j) * plane : nullptr;
-            a.variant = p->variant;
-            cudaError_t e = launch_plain<T>(p->kind, adjoint, a, st, p->num_sms);
+            cudaError_t e = plain_step<T>(p, adjoint, s, coeffs, buf[o.in_p], buf[o.in_c], buf[o.out_c],
+                                          (!adjoint && trace) ? (T *)trace + t * plane : nullptr,
+                                          (adjoint && inject) ? (const T *)inject + (nsteps - j) * plane : nullptr,
+                                          rcv_z, st);
             if (e != cudaSuccess) return cuda_fail(e);
         } else {
             if (adjoint) return STENCIL_EUNSUPPORTED;
@@ -294,9 +330,14 @@ int run_program(stencil_plan_s *p, void *pair_p, void *pair_c, const stencil_coe
             a.rcv_z = (int)rcv_z;
             a.trace = trace ? (T *)trace + t * plane : nullptr;
             a.levels = o.levels;
-            if (blocked_scratch_levels(o.levels) > p->nbands) return STENCIL_EUNSUPPORTED;
-            for (int k = 1; k < o.levels; ++k) a.bands[k] = (T *)p->bands[k - 1];
-            cudaError_t e = launch_blocked<T>(p->kind, a, st, p->num_sms, p->scheme);
+            cudaError_t e;
+            if (p->scheme == 3) {
+                e = launch_wavefront<T>(p->kind, a, p->variant >= 10 ? p->variant - 9 : 0, st, p->num_sms);
+            } else {
+                if (blocked_scratch_levels(o.levels) > p->nbands) return STENCIL_EUNSUPPORTED;
+                for (int k = 1; k < o.levels; ++k) a.bands[k] = (T *)p->bands[k - 1];
+                e = launch_blocked<T>(p->kind, a, st, p->num_sms, p->scheme);
+            }
             if (e != cudaSuccess) return cuda_fail(e);
         }
         t += o.levels;
@@ -304,25 +345,6 @@ int run_program(stencil_plan_s *p, void *pair_p, void *pair_c, const stencil_coe
     return STENCIL_OK;
 }
 
-// Plain sweep launch helper shared by the runners below.
-template <typename T>
-cudaError_t plain_step(stencil_plan_s *p, bool adjoint, const Scalars &s, const stencil_coeffs_t *coeffs,
-                       const void *in_p, const void *in_c, void *out, T *trace, const T *inject, int64_t rcv_z,
-                       cudaStream_t st) {
-    SweepArgs<T> a;
-    memset(&a, 0, sizeof(a));
-    a.u_prev = (const T *)in_p;
-    a.u = (const T *)in_c;
-    a.out = (T *)out;
-    a.W = coeffs ? (const T *)coeffs->arrays : nullptr;
-    a.s = s;
-    a.g = p->g;
-    a.rcv_z = (int)rcv_z;
-    a.trace = trace;
-    a.inject = inject;
-    a.variant = p->variant;
-    return launch_plain<T>(p->kind, adjoint, a, st, p->num_sms);
-}
 
 // Forward T plain steps storing every state: step t reads
 // (u^{t-1}, u^t) and writes u^{t+1} into states[t].
@@ -400,7 +422,7 @@ void free_bands(stencil_plan_s *p) {
 // Allocate the band buffers of the effective block depth (plan time only).
 int ensure_bands(stencil_plan_s *p) {
     const int b = effective_time_block(p);
-    const int need = b > 1 ? blocked_scratch_levels(b) : 0;
+    const int need = (b > 1 && p->scheme != 3) ? blocked_scratch_levels(b) : 0;
     if (need <= p->nbands) return STENCIL_OK;
     free_bands(p);
     for (int i = 0; i < need; ++i) {
@@ -505,15 +527,17 @@ int stencil_plan_set(stencil_plan_t p, int option, int64_t value) {
     switch (option) {
     case STENCIL_OPT_TIME_BLOCK:
         if (value < 0 || value > 64) return STENCIL_EINVAL;
-        if (value > 1 && !blocked_supported(p->kind, p->dtype, (int)value)) return STENCIL_EUNSUPPORTED;
+        if (value > 1 && !blocked_supported(p->kind, p->dtype, (int)value) &&
+            !wavefront_supported(p->kind, p->dtype, (int)value, p->g))
+            return STENCIL_EUNSUPPORTED;
         p->time_block = (int)value;
         return ensure_bands(p);
     case STENCIL_OPT_SCHEME:
-        if (value < 0 || value > 2) return STENCIL_EINVAL;
+        if (value < 0 || value > 3) return STENCIL_EINVAL;
         p->scheme = (int)value;
-        return STENCIL_OK;
+        return ensure_bands(p);
     case STENCIL_OPT_VARIANT:
-        if (value < 0 || value > 9) return STENCIL_EINVAL;
+        if (value < 0 || value > 12) return STENCIL_EINVAL;
         p->variant = (int)value;
         return STENCIL_OK;
     case STENCIL_OPT_GRAD_BATCH:

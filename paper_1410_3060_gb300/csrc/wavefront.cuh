@@ -1,0 +1,16 @@
+// wavefront.cuh -- register wavefront passes (B time levels per sweep, B >= 1)
+// with warp-shuffle x neighbours and overlapped tiles.
+#pragma once
+#include "blocked.cuh"
+
+namespace stc {
+
+// Whether the register wavefront serves this kind / dtype / depth and the
+// plan's geometry (vector width: the padded row length must be a multiple of
+// the elements per thread).
+bool wavefront_supported(int kind, int dtype, int levels, const Geom &g);
+// Tile variant of the register wavefront (0 = default of the kind / dtype).
+template <typename T>
+cudaError_t launch_wavefront(int kind, const BlockedArgs<T> &a, int tile, cudaStream_t st, int num_sms);
+
+}  // namespace stc

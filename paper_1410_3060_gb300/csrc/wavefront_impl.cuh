@@ -1,0 +1,426 @@
+// wavefront_impl.cuh -- register wavefront passes: B time levels per sweep over
+// HBM (B = 1 is the plain one-level sweep), written for few instructions
+// per lattice update.
+//
+// Wavefront temporal blocking (paper Sect. 4.1) with the frontline marching
+// in z: at step q a CTA receives level-0 plane q, and level k (1..B) updates
+// plane q - kR from the 2R+1 planes of level k-1 around it, so the
+// frontline has slope -1/R.  The thread group that shares a cache in the
+// paper's multicore wavefront (Sect. 5.1) is here a CTA sharing registers
+// and one small shared buffer; it synchronises once per plane.
+//
+// Data placement (per thread: V consecutive x columns, NR consecutive y rows):
+//  * every level's 2R+1 planes of the thread's points live in a register
+//    ring (level 0: 2R+1 + PD slots, loaded PD planes ahead with vector
+//    loads); the step loop is unrolled by the ring length so every slot is a
+//    register;
+//  * x neighbours across lanes come from warp shuffles; the tile's outer
+//    columns (lanes 0 and 31) get no neighbour and become invalid, R columns
+//    per level: x is tiled with an overlapped halo of B*R columns;
+//  * y neighbours inside the thread's rows are registers; across warps the
+//    first and last R rows of every level's plane are exchanged through a
+//    double-buffered shared buffer (one __syncthreads per step); the tile's
+//    outer warps get no neighbour: y is tiled with an overlapped halo of B*R
+//    rows;
+//  * z is split into chunks; each chunk recomputes a ramp of (B-k)R planes
+//    of level k at both ends.
+// Points outside the interior hold the zero Dirichlet value at every level:
+// for the constant kind the two weights of such a point are zero, for the
+// variable kind the result is selected to zero.  Only level B (and, when
+// asked, level B-1: the next pass's u^{t-1}) is written to HBM, plus the
+// receiver trace of every level.
+//
+// The update of a point is the plain sweep's expression, so results agree
+// with the one-level kernels to rounding.
+#pragma once
+#include "wavefront.cuh"
+
+namespace stc {
+
+namespace {
+
+template <typename T, int V> struct Vec;
+template <> struct Vec<float, 1> { using type = float; };
+template <> struct Vec<float, 2> { using type = float2; };
+template <> struct Vec<float, 4> { using type = float4; };
+template <> struct Vec<double, 1> { using type = double; };
+template <> struct Vec<double, 2> { using type = double2; };
+
+// read-only global vector load
+template <typename T, int V>
+__device__ __forceinline__ void vld_g(T (&d)[V], const T *p) {
+    using VT = typename Vec<T, V>::type;
+    const VT v = __ldg(reinterpret_cast<const VT *>(p));
+    if constexpr (V == 1) {
+        d[0] = v;
+    } else if constexpr (V == 2) {
+        d[0] = v.x; d[1] = v.y;
+    } else {
+        d[0] = v.x; d[1] = v.y; d[2] = v.z; d[3] = v.w;
+    }
+}
+
+template <typename T, int V>
+__device__ __forceinline__ void vld(T (&d)[V], const T *p) {
+    using VT = typename Vec<T, V>::type;
+    const VT v = *reinterpret_cast<const VT *>(p);
+    if constexpr (V == 1) {
+        d[0] = v;
+    } else if constexpr (V == 2) {
+        d[0] = v.x; d[1] = v.y;
+    } else {
+        d[0] = v.x; d[1] = v.y; d[2] = v.z; d[3] = v.w;
+    }
+}
+
+template <typename T, int V>
+__device__ __forceinline__ void vst(T *p, const T (&s)[V]) {
+    using VT = typename Vec<T, V>::type;
+    VT v;
+    if constexpr (V == 1) {
+        v = s[0];
+    } else if constexpr (V == 2) {
+        v.x = s[0]; v.y = s[1];
+    } else {
+        v.x = s[0]; v.y = s[1]; v.z = s[2]; v.w = s[3];
+    }
+    *reinterpret_cast<VT *>(p) = v;
+}
+
+template <int V, int B, int R>
+struct WfGeom {
+    static constexpr int BR = B * R;
+    static constexpr int AX = (BR + V - 1) / V * V;   // left halo, whole vectors
+};
+
+}  // namespace
+
+template <typename T, int KIND, int B, int V, int NR, int WY>
+__global__ void __launch_bounds__(32 * WY) wavefront_kernel(const BlockedArgs<T> a) {
+    constexpr int R = KindTraits<KIND>::R;
+    constexpr int NA = KindTraits<KIND>::NARR;
+    static_assert(R == 1 && (KIND == J7_CONST || KIND == J7_VAR), "radius-1 kinds");
+    constexpr int RING = 2 * R + 1;
+    constexpr int PD = RING;              // level-0 planes are loaded PD steps ahead
+    constexpr int R0 = RING + PD;         // level-0 ring slots
+    constexpr int U = R0;                 // steps per unrolled block
+    static_assert(U % RING == 0 && U % 2 == 0, "static ring slots and buffer parity");
+    constexpr int TXE = 32 * V, TYE = WY * NR;
+    constexpr int BR = B * R;
+    constexpr int AX = WfGeom<V, B, R>::AX;
+    constexpr int SX = (TXE - BR - AX) / V * V;   // owned columns per tile
+    constexpr int SY = TYE - 2 * BR;              // owned rows per tile
+    static_assert(SX > 0 && SY > 0 && NR >= R, "tile too small for the depth");
+    constexpr int NK = B > 1 ? B - 1 : 1;
+
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    // edge rows [parity][level m][warp][R top rows, R bottom rows][TXE]
+    T *const xb = reinterpret_cast<T *>(smem_raw);
+    constexpr int XW = 2 * R * TXE;
+    constexpr int XL = WY * XW;
+    constexpr int XP = B * XL;
+
+    const Geom g = a.g;
+    const int lane = threadIdx.x, w = threadIdx.y;
+    const int bx = blockIdx.x, by = blockIdx.y;
+    const int c0 = bx * SX - AX + lane * V;      // padded column of element 0
+    const int r0 = by * SY - BR + w * NR;        // padded row of row 0
+    const int z0 = blockIdx.z * a.zchunk;
+    const int z1 = min(z0 + a.zchunk, g.nz);
+    const int qs = z0 - BR, qe = z1 + BR;
+    const int sy = (int)g.sy;
+
+    // ---- per-thread constants
+    const bool cmem = c0 >= 0 && c0 < g.px;      // vector inside the padded row
+    bool cin[V];
+    bool call = true, cany = false;
+#pragma unroll
+    for (int i = 0; i < V; ++i) {
+        cin[i] = c0 + i >= R && c0 + i < g.nx + R;
+        call = call && cin[i];
+        cany = cany || cin[i];
+    }
+    const bool cown = c0 >= bx * SX && c0 < (bx + 1) * SX;
+    uint32_t lmask = 0, rin = 0, smask = 0;
+#pragma unroll
+    for (int j = 0; j < NR; ++j) {
+        const int r = r0 + j;
+        if (cmem && r >= 0 && r < g.py) lmask |= 1u << j;
+        const bool ri = r >= R && r < g.ny + R;
+        if (ri) rin |= 1u << j;
+        if (ri && cown && cany && r >= by * SY && r < (by + 1) * SY) smask |= 1u << j;
+    }
+    const int off0 = r0 * sy + c0;               // in-plane offset of row 0
+
+    // constant kind: weights with the interior mask folded in
+    T wc[NR][V], wf[NR][V];
+    // variable kind: point mask bits (row j, column i) -> bit j V + i
+    uint32_t pmask = 0;
+    {
+        const T s0 = T(a.s.c[0]), s1 = T(a.s.c[1]);
+#pragma unroll
+        for (int j = 0; j < NR; ++j)
+#pragma unroll
+            for (int i = 0; i < V; ++i) {
+                const bool m = ((rin >> j) & 1u) && cin[i];
+                wc[j][i] = m ? s0 : T(0);
+                wf[j][i] = m ? s1 : T(0);
+                if (m) pmask |= 1u << (j * V + i);
+            }
+    }
+    (void)wc; (void)wf; (void)pmask;
+
+    T r0v[R0][NR][V];
+    T rk[NK][RING][NR][V];
+#pragma unroll
+    for (int s = 0; s < R0; ++s)
+#pragma unroll
+        for (int j = 0; j < NR; ++j)
+#pragma unroll
+            for (int i = 0; i < V; ++i) r0v[s][j][i] = T(0);
+#pragma unroll
+    for (int k = 0; k < NK; ++k)
+#pragma unroll
+        for (int s = 0; s < RING; ++s)
+#pragma unroll
+            for (int j = 0; j < NR; ++j)
+#pragma unroll
+                for (int i = 0; i < V; ++i) rk[k][s][j][i] = T(0);
+
+    // level-0 plane q (interior z) into d; zero outside the padded array
+    auto load0 = [&](int q, T (&d)[NR][V]) {
+        const bool zm = q >= -R && q < g.nz + R;
+        const T *pb = a.u + (int64_t)(q + R) * g.sz;
+#pragma unroll
+        for (int j = 0; j < NR; ++j) {
+            if (zm && ((lmask >> j) & 1u)) {
+                vld_g<T, V>(d[j], pb + (off0 + j * sy));
+            } else {
+#pragma unroll
+                for (int i = 0; i < V; ++i) d[j][i] = T(0);
+            }
+        }
+    };
+    // plane slot of level m at plane offset p (relative to the block start)
+    auto lev = [&](auto mI, auto pI) -> T (&)[NR][V] {
+        constexpr int m = decltype(mI)::value;
+        constexpr int p = decltype(pI)::value;
+        if constexpr (m == 0) return r0v[cmod(p, R0)];
+        else return rk[m - 1][cmod(p, RING)];
+    };
+    // store a plane of owned interior points
+    auto store_plane = [&](T *base, const T (*v)[V]) {
+#pragma unroll
+        for (int j = 0; j < NR; ++j) {
+            if (!((smask >> j) & 1u)) continue;
+            T *p = base + (off0 + j * sy);
+            if (call) {
+                vst<T, V>(p, v[j]);
+            } else {
+#pragma unroll
+                for (int i = 0; i < V; ++i)
+                    if (cin[i]) p[i] = v[j][i];
+            }
+        }
+    };
+    auto store_trace = [&](T *tr, const T (*v)[V]) {
+#pragma unroll
+        for (int j = 0; j < NR; ++j) {
+            if (!((smask >> j) & 1u)) continue;
+            T *p = tr + (int64_t)(r0 + j - R) * g.nx + (c0 - R);
+#pragma unroll
+            for (int i = 0; i < V; ++i)
+                if (cin[i]) p[i] = v[j][i];
+        }
+    };
+
+#pragma unroll
+    for (int s = 0; s < PD; ++s)
+        if (qs + s < qe) load0(qs + s, r0v[s]);
+
+    const unsigned FULL = 0xffffffffu;
+    const int wu = w > 0 ? w - 1 : 0, wd = w < WY - 1 ? w + 1 : WY - 1;
+    const int64_t plane_elems = (int64_t)g.nx * g.ny;
+
+    for (int qb = qs; qb < qe; qb += U) {
+        static_for<U>([&](auto jj) {
+            constexpr int j = decltype(jj)::value;
+            constexpr int par = j & 1;
+            const int q = qb + j;
+            if (q >= qe) return;
+            if (q + PD < qe) load0(q + PD, r0v[cmod(j + PD, R0)]);
+            // publish the edge rows of level m's plane q - (m+1)R (consumed by
+            // level m+1 in this step)
+            {
+                T *xp = xb + par * XP + w * XW + lane * V;
+                static_for<B>([&](auto mm) {
+                    constexpr int m = decltype(mm)::value;
+                    const T(&P)[NR][V] = lev(IC<m>{}, IC<j - (m + 1) * R>{});
+#pragma unroll
+                    for (int r = 0; r < R; ++r) {
+                        vst<T, V>(xp + m * XL + r * TXE, P[r]);
+                        vst<T, V>(xp + m * XL + (R + r) * TXE, P[NR - R + r]);
+                    }
+                });
+            }
+            __syncthreads();
+            static_for<B>([&](auto kk) {
+                constexpr int k = decltype(kk)::value + 1;
+                if (q < qs + 2 * k * R) return;
+                const int zk = q - k * R;
+                constexpr int pc = j - k * R;
+                T res[NR][V];
+                T(*D)[V];
+                if constexpr (k < B) D = rk[k - 1][cmod(pc, RING)];
+                else D = res;
+                if (k < B && (zk < 0 || zk >= g.nz)) {
+#pragma unroll
+                    for (int jr = 0; jr < NR; ++jr)
+#pragma unroll
+                        for (int i = 0; i < V; ++i) D[jr][i] = T(0);
+                } else {
+                    const T(&C)[NR][V] = lev(IC<k - 1>{}, IC<pc>{});
+                    const T(&Zd)[NR][V] = lev(IC<k - 1>{}, IC<pc - 1>{});
+                    const T(&Zu)[NR][V] = lev(IC<k - 1>{}, IC<pc + 1>{});
+                    const T *xk = xb + par * XP + (k - 1) * XL + lane * V;
+                    T up[V], dn[V];
+                    vld<T, V>(up, xk + wu * XW + (2 * R - 1) * TXE);   // last row of the warp above
+                    vld<T, V>(dn, xk + wd * XW);                      // first row of the warp below
+                    const T *cfb = nullptr;
+                    if constexpr (NA > 0) cfb = a.W + (int64_t)(zk + R) * g.sz;
+                    (void)cfb;
+#pragma unroll
+                    for (int jr = 0; jr < NR; ++jr) {
+                        T cf[NA > 0 ? NA : 1][V];
+                        (void)cf;
+                        if constexpr (NA > 0) {
+                            if ((lmask >> jr) & 1u) {
+#pragma unroll
+                                for (int t = 0; t < NA; ++t)
+                                    vld_g<T, V>(cf[t], cfb + t * g.nfield + (off0 + jr * sy));
+                            } else {
+#pragma unroll
+                                for (int t = 0; t < NA; ++t)
+#pragma unroll
+                                    for (int i = 0; i < V; ++i) cf[t][i] = T(0);
+                            }
+                        }
+                        const T left = __shfl_up_sync(FULL, C[jr][V - 1], 1);
+                        const T right = __shfl_down_sync(FULL, C[jr][0], 1);
+#pragma unroll
+                        for (int i = 0; i < V; ++i) {
+                            const T c = C[jr][i];
+                            const T xl = i > 0 ? C[jr][i - 1] : left;
+                            const T xr = i < V - 1 ? C[jr][i + 1] : right;
+                            const T yu = jr > 0 ? C[jr - 1][i] : up[i];
+                            const T yd = jr < NR - 1 ? C[jr + 1][i] : dn[i];
+                            const T zd = Zd[jr][i], zu = Zu[jr][i];
+                            T v;
+                            if constexpr (KIND == J7_CONST) {
+                                v = wc[jr][i] * c + wf[jr][i] * (((xl + xr) + (yu + yd)) + (zd + zu));
+                            } else {
+                                v = cf[0][i] * c;
+                                v = fma(cf[1][i], xl, v);
+                                v = fma(cf[2][i], xr, v);
+                                v = fma(cf[3][i], yu, v);
+                                v = fma(cf[4][i], yd, v);
+                                v = fma(cf[5][i], zd, v);
+                                v = fma(cf[6][i], zu, v);
+                                v = ((pmask >> (jr * V + i)) & 1u) ? v : T(0);
+                            }
+                            D[jr][i] = v;
+                        }
+                    }
+                }
+                if (a.trace && zk == a.rcv_z && zk >= z0 && zk < z1) store_trace(a.trace + (k - 1) * plane_elems, D);
+                if constexpr (k == B) {
+                    store_plane(a.out + (int64_t)(zk + R) * g.sz, D);
+                    if (a.out_prev) store_plane(a.out_prev + (int64_t)(zk + R) * g.sz, lev(IC<B - 1>{}, IC<pc>{}));
+                }
+            });
+        });
+    }
+}
+
+// ---------------------------------------------------------------- launch
+namespace {
+
+template <typename T, int KIND, int B, int V, int NR, int WY>
+cudaError_t launch_wf(const BlockedArgs<T> &a, cudaStream_t st, int num_sms) {
+    constexpr int R = KindTraits<KIND>::R;
+    constexpr int TXE = 32 * V, TYE = WY * NR;
+    constexpr int BR = B * R;
+    constexpr int AX = WfGeom<V, B, R>::AX;
+    constexpr int SX = (TXE - BR - AX) / V * V;
+    constexpr int SY = TYE - 2 * BR;
+    auto kern = wavefront_kernel<T, KIND, B, V, NR, WY>;
+    constexpr size_t smem = sizeof(T) * 2 * B * WY * 2 * R * TXE;
+    static_assert(smem <= 227 * 1024, "shared memory per CTA");
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    int per_sm = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 32 * WY, smem);
+    if (per_sm < 1) per_sm = 1;
+    const int gx = (a.g.nx + R + SX - 1) / SX;
+    const int gy = (a.g.ny + R + SY - 1) / SY;
+    // z chunks: minimise (waves of resident CTAs) x (steps per chunk); every
+    // chunk recomputes a ramp of 2BR planes, so chunks are >= 8BR planes
+    const int64_t resident = (int64_t)num_sms * per_sm;
+    const int64_t tiles = (int64_t)gx * gy;
+    const int min_chunk = 8 * BR > 16 ? 8 * BR : 16;
+    int best = 1;
+    double best_cost = 1e300;
+    for (int nzc = 1; nzc <= a.g.nz; ++nzc) {
+        const int chunk = (a.g.nz + nzc - 1) / nzc;
+        if (nzc > 1 && chunk < min_chunk) break;
+        const int64_t ctas = tiles * ((a.g.nz + chunk - 1) / chunk);
+        const int64_t waves = (ctas + resident - 1) / resident;
+        const double cost = (double)waves * (chunk + 2 * BR);
+        if (cost < best_cost * 0.999) { best_cost = cost; best = nzc; }
+    }
+    BlockedArgs<T> b = a;
+    b.zchunk = (a.g.nz + best - 1) / best;
+    const int gz = (a.g.nz + b.zchunk - 1) / b.zchunk;
+    dim3 grid(gx, gy, gz), block(32, WY, 1);
+    kern<<<grid, block, smem, st>>>(b);
+    return cudaGetLastError();
+}
+
+constexpr int kVec(int elem) { return elem == 4 ? 2 : 2; }
+
+template <typename T, int KIND, int B>
+cudaError_t launch_tile(const BlockedArgs<T> &a, int tile, cudaStream_t st, int num_sms) {
+    constexpr int V = kVec((int)sizeof(T));
+    switch (tile) {
+    case 2: return launch_wf<T, KIND, B, V, 2, 16>(a, st, num_sms);   // 64 x 32, 2 rows per thread
+    default: return launch_wf<T, KIND, B, V, 4, 8>(a, st, num_sms);   // 64 x 32, 4 rows per thread
+    }
+}
+
+template <typename T>
+cudaError_t launch_wavefront_impl(int kind, const BlockedArgs<T> &a, int tile, cudaStream_t st, int num_sms);
+
+template <typename T, int KIND>
+cudaError_t launch_depth(const BlockedArgs<T> &a, int tile, cudaStream_t st, int num_sms) {
+    switch (a.levels) {
+    case 1: return launch_tile<T, KIND, 1>(a, tile, st, num_sms);
+    case 2: return launch_tile<T, KIND, 2>(a, tile, st, num_sms);
+    case 3: if constexpr (sizeof(T) == 4) return launch_tile<T, KIND, 3>(a, tile, st, num_sms); else break;
+    case 4: if constexpr (sizeof(T) == 4) return launch_tile<T, KIND, 4>(a, tile, st, num_sms); else break;
+    default: break;
+    }
+    return cudaErrorNotSupported;
+}
+
+template <typename T>
+cudaError_t launch_wavefront_impl(int kind, const BlockedArgs<T> &a, int tile, cudaStream_t st, int num_sms) {
+    switch (kind) {
+    case J7_CONST: return launch_depth<T, J7_CONST>(a, tile, st, num_sms);
+    case J7_VAR: return launch_depth<T, J7_VAR>(a, tile, st, num_sms);
+    default: return cudaErrorNotSupported;
+    }
+}
+
+}  // namespace
+
+}  // namespace stc

@@ -38,8 +38,11 @@ def fp32_bound(kind, T, R):
     return 4.0 * (T + 1) * terms * EPS32
 
 
-def gpu_forward(plan_cls, wk, dtype, T=None, rcv_z=None, time_block=None, scheme=None):
-    """Run stencil_forward on a workload; returns numpy (u_prev, u, trace)."""
+def gpu_forward(plan_cls, wk, dtype, T=None, rcv_z=None, time_block=None, scheme=None, variant=None,
+                expect_block=None):
+    """Run stencil_forward on a workload; returns numpy (u_prev, u, trace).
+    expect_block: the block depth the plan must report (the requested pass
+    kernel serves the geometry)."""
     torch = torch_mod()
     T = wk.T if T is None else T
     nx, ny, nz = wk.n
@@ -48,6 +51,10 @@ def gpu_forward(plan_cls, wk, dtype, T=None, rcv_z=None, time_block=None, scheme
         plan.set(1, time_block)
     if scheme is not None:
         plan.set(2, scheme)
+    if variant is not None:
+        plan.set(5, variant)
+    if expect_block is not None:
+        assert plan.get(1) == expect_block
     up = to_dev(wk.u_prev, dtype)
     u = to_dev(wk.u, dtype)
     W = to_dev(wk.W, dtype) if wk.W is not None else None

@@ -92,3 +92,70 @@ def test_time_block_option_roundtrip(st):
     with pytest.raises(st.StencilError):
         p.set(1, 7)
     p.close()
+
+
+# ---- register wavefront (scheme 3; tile variants 10 and 11 for one-level passes)
+
+WF_SHAPES = [(130, 75, 70), (62, 37, 23), (200, 33, 18)]
+
+
+@pytest.mark.parametrize("kind", R1)
+@pytest.mark.parametrize("b", [1, 2, 3, 4])
+@pytest.mark.parametrize("variant", [10, 11])
+@pytest.mark.parametrize("shape", WF_SHAPES)
+@pytest.mark.parametrize("T", [9, 4])
+def test_wavefront_forward_fp32(st, kind, b, variant, shape, T):
+    """Register wavefront passes of depth b (b = 1: every pass one level)
+    against the oracle; the plan must run the requested depth."""
+    wk = wl.make(kind, shape, T, seed=13)
+    rz = shape[2] // 3
+    op, ou, otr = oracle.forward(kind, wk.u_prev, wk.u, wk.w, wk.W, T, rcv_z=rz, threads=8)
+    gp, gu, gtr = gpu_forward(st.Plan, wk, F32, rcv_z=rz, time_block=b, scheme=3, variant=variant,
+                              expect_block=b)
+    bound = fp32_bound(kind, T, wk.R)
+    assert normwise_err(gu, ou) <= bound
+    assert normwise_err(gp, op) <= bound
+    assert normwise_err(gtr, otr) <= bound
+    R = wk.R
+    halo = np.ones(gu.shape, bool)
+    halo[R:-R, R:-R, R:-R] = False
+    assert not gu[halo].any() and not gp[halo].any()
+
+
+@pytest.mark.parametrize("kind", R1)
+@pytest.mark.parametrize("b", [1, 2])
+@pytest.mark.parametrize("variant", [10, 11])
+@pytest.mark.parametrize("shape", [(70, 45, 40), (34, 19, 11)])
+def test_wavefront_forward_fp64(st, kind, b, variant, shape):
+    """FP64 register wavefront passes match the oracle to 1e-12."""
+    from gpu_util import F64
+    T = 7
+    wk = wl.make(kind, shape, T, seed=19)
+    rz = 3
+    op, ou, otr = oracle.forward(kind, wk.u_prev, wk.u, wk.w, wk.W, T, rcv_z=rz, threads=8)
+    gp, gu, gtr = gpu_forward(st.Plan, wk, F64, rcv_z=rz, time_block=b, scheme=3, variant=variant,
+                              expect_block=b)
+    assert normwise_err(gu, ou) <= 1e-12
+    assert normwise_err(gp, op) <= 1e-12
+    assert normwise_err(gtr, otr) <= 1e-12
+
+
+@pytest.mark.parametrize("kind", R1)
+def test_wavefront_matches_plain_gpu(st, kind):
+    """Depth-4 register wavefront vs the plain sweep: a few FP32 roundings
+    per step apart."""
+    shape, T = (256, 96, 80), 8
+    wk = wl.make(kind, shape, T, seed=21)
+    _, gu_w, _ = gpu_forward(st.Plan, wk, F32, time_block=4, scheme=3, expect_block=4)
+    _, gu_p, _ = gpu_forward(st.Plan, wk, F32, time_block=1)
+    assert normwise_err(gu_w, gu_p) <= 8 * T * 2.0 ** -24
+
+
+def test_wavefront_odd_row_falls_back(st):
+    """An odd padded row length has no aligned vector layout: the plan runs
+    plain passes (and still matches the oracle)."""
+    shape, T = (41, 37, 23), 5
+    wk = wl.make(1, shape, T, seed=2)
+    op, ou, _ = oracle.forward(1, wk.u_prev, wk.u, wk.w, wk.W, T, threads=8)
+    _, gu, _ = gpu_forward(st.Plan, wk, F32, time_block=2, scheme=3, variant=10, expect_block=1)
+    assert normwise_err(gu, ou) <= fp32_bound(1, T, 1)
