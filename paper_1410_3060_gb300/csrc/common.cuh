@@ -89,10 +89,13 @@ template <int BYTES>
 __device__ __forceinline__ void cp_async_zfill(void *smem, const void *gmem, bool valid) {
     const unsigned s = static_cast<unsigned>(__cvta_generic_to_shared(smem));
     const int src = valid ? BYTES : 0;
+    static_assert(BYTES == 4 || BYTES == 8 || BYTES == 16, "cp.async sizes");
     if constexpr (BYTES == 4)
         asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(s), "l"(gmem), "r"(src) : "memory");
-    else
+    else if constexpr (BYTES == 8)
         asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;\n" ::"r"(s), "l"(gmem), "r"(src) : "memory");
+    else
+        asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(s), "l"(gmem), "r"(src) : "memory");
 }
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
 template <int N>

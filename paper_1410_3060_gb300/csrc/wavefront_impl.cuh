@@ -95,32 +95,50 @@ struct WfGeom {
 
 }  // namespace
 
+// Tile constants of one (V, NR, WY, B, R) configuration.
+template <int V, int NR, int WY, int B, int R>
+struct WfTile {
+    static constexpr int TXE = 32 * V, TYE = WY * NR;
+    static constexpr int BR = B * R;
+    static constexpr int AX = WfGeom<V, B, R>::AX;
+    static constexpr int SX = (TXE - BR - AX) / V * V;   // owned columns per tile
+    static constexpr int SY = TYE - 2 * BR;              // owned rows per tile
+    static constexpr int RING = 2 * R + 1;
+    static constexpr int PD = 2;                          // level-0 planes in flight
+    static constexpr int NS = PD + 2;                     // level-0 shared slots
+    static constexpr int NX = RING;                       // edge-row buffers (one per step mod RING)
+};
+
+template <typename T, int V, int NR, int WY, int B, int R>
+constexpr size_t wf_smem() {
+    using TL = WfTile<V, NR, WY, B, R>;
+    return sizeof(T) * ((size_t)TL::NS * TL::TYE * TL::TXE + (size_t)TL::NX * B * WY * 2 * R * TL::TXE);
+}
+
 template <typename T, int KIND, int B, int V, int NR, int WY>
 __global__ void __launch_bounds__(32 * WY) wavefront_kernel(const BlockedArgs<T> a) {
     constexpr int R = KindTraits<KIND>::R;
     constexpr int NA = KindTraits<KIND>::NARR;
     static_assert(R == 1 && (KIND == J7_CONST || KIND == J7_VAR), "radius-1 kinds");
-    constexpr int RING = 2 * R + 1;
-    constexpr int PD = RING;              // level-0 planes are loaded PD steps ahead
-    constexpr int R0 = RING + PD;         // level-0 ring slots
-    constexpr int U = R0;                 // steps per unrolled block
-    static_assert(U % RING == 0 && U % 2 == 0, "static ring slots and buffer parity");
-    constexpr int TXE = 32 * V, TYE = WY * NR;
-    constexpr int BR = B * R;
-    constexpr int AX = WfGeom<V, B, R>::AX;
-    constexpr int SX = (TXE - BR - AX) / V * V;   // owned columns per tile
-    constexpr int SY = TYE - 2 * BR;              // owned rows per tile
+    using TL = WfTile<V, NR, WY, B, R>;
+    constexpr int RING = TL::RING;
+    constexpr int U = RING;               // steps per unrolled block: ring slots are constants
+    constexpr int PD = TL::PD, NS = TL::NS;
+    constexpr int TXE = TL::TXE, TYE = TL::TYE, BR = TL::BR, AX = TL::AX, SX = TL::SX, SY = TL::SY;
     static_assert(SX > 0 && SY > 0 && NR >= R, "tile too small for the depth");
     constexpr int NK = B > 1 ? B - 1 : 1;
-
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    // edge rows [parity][level m][warp][R top rows, R bottom rows][TXE]
-    T *const xb = reinterpret_cast<T *>(smem_raw);
+    // shared: level-0 planes [NS][WY][NR][32 lanes][V] (each thread copies
+    // and reads back only its own points), then the edge rows
+    // [U][level m][warp][R top rows, R bottom rows][TXE]
+    constexpr int S0 = TYE * TXE;
     constexpr int XW = 2 * R * TXE;
     constexpr int XL = WY * XW;
     constexpr int XP = B * XL;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T *const s0b = reinterpret_cast<T *>(smem_raw);
+    T *const xb = s0b + NS * S0;
 
-    const Geom g = a.g;
+    const Geom &g = a.g;
     const int lane = threadIdx.x, w = threadIdx.y;
     const int bx = blockIdx.x, by = blockIdx.y;
     const int c0 = bx * SX - AX + lane * V;      // padded column of element 0
@@ -129,6 +147,7 @@ __global__ void __launch_bounds__(32 * WY) wavefront_kernel(const BlockedArgs<T>
     const int z1 = min(z0 + a.zchunk, g.nz);
     const int qs = z0 - BR, qe = z1 + BR;
     const int sy = (int)g.sy;
+    const int64_t sz = g.sz;
 
     // ---- per-thread constants
     const bool cmem = c0 >= 0 && c0 < g.px;      // vector inside the padded row
@@ -141,39 +160,32 @@ __global__ void __launch_bounds__(32 * WY) wavefront_kernel(const BlockedArgs<T>
         cany = cany || cin[i];
     }
     const bool cown = c0 >= bx * SX && c0 < (bx + 1) * SX;
-    uint32_t lmask = 0, rin = 0, smask = 0;
+    uint32_t lmask = 0, smask = 0, pmask = 0;
+    const T s0 = T(a.s.c[0]), s1 = T(a.s.c[1]);
+    // constant kind: the two weights with the Dirichlet mask folded in;
+    // variable kind: point mask bits (row j, column i -> bit jV + i)
+    T wc[NR][V], wf[NR][V];
 #pragma unroll
     for (int j = 0; j < NR; ++j) {
         const int r = r0 + j;
         if (cmem && r >= 0 && r < g.py) lmask |= 1u << j;
         const bool ri = r >= R && r < g.ny + R;
-        if (ri) rin |= 1u << j;
         if (ri && cown && cany && r >= by * SY && r < (by + 1) * SY) smask |= 1u << j;
-    }
-    const int off0 = r0 * sy + c0;               // in-plane offset of row 0
-
-    // constant kind: weights with the interior mask folded in
-    T wc[NR][V], wf[NR][V];
-    // variable kind: point mask bits (row j, column i) -> bit j V + i
-    uint32_t pmask = 0;
-    {
-        const T s0 = T(a.s.c[0]), s1 = T(a.s.c[1]);
 #pragma unroll
-        for (int j = 0; j < NR; ++j)
-#pragma unroll
-            for (int i = 0; i < V; ++i) {
-                const bool m = ((rin >> j) & 1u) && cin[i];
-                wc[j][i] = m ? s0 : T(0);
-                wf[j][i] = m ? s1 : T(0);
-                if (m) pmask |= 1u << (j * V + i);
-            }
+        for (int i = 0; i < V; ++i) {
+            const bool m = ri && cin[i];
+            wc[j][i] = m ? s0 : T(0);
+            wf[j][i] = m ? s1 : T(0);
+            if (m) pmask |= 1u << (j * V + i);
+        }
     }
     (void)wc; (void)wf; (void)pmask;
+    const int off0 = r0 * sy + c0;               // in-plane offset of row 0 (used only when in the array)
 
-    T r0v[R0][NR][V];
+    T r0v[RING][NR][V];
     T rk[NK][RING][NR][V];
 #pragma unroll
-    for (int s = 0; s < R0; ++s)
+    for (int s = 0; s < RING; ++s)
 #pragma unroll
         for (int j = 0; j < NR; ++j)
 #pragma unroll
@@ -187,28 +199,28 @@ __global__ void __launch_bounds__(32 * WY) wavefront_kernel(const BlockedArgs<T>
 #pragma unroll
                 for (int i = 0; i < V; ++i) rk[k][s][j][i] = T(0);
 
-    // level-0 plane q (interior z) into d; zero outside the padded array
-    auto load0 = [&](int q, T (&d)[NR][V]) {
+    // this thread's points of a level-0 slot
+    T *const s0t = s0b + (w * NR) * TXE + lane * V;
+    // copy level-0 plane q (interior z) into slot `slot`; zeros outside the padded array
+    auto issue0 = [&](int q, int slot) {
         const bool zm = q >= -R && q < g.nz + R;
-        const T *pb = a.u + (int64_t)(q + R) * g.sz;
+        const T *pb = a.u + (zm ? (int64_t)(q + R) * sz : 0);
+        T *d = s0t + slot * S0;
 #pragma unroll
         for (int j = 0; j < NR; ++j) {
-            if (zm && ((lmask >> j) & 1u)) {
-                vld_g<T, V>(d[j], pb + (off0 + j * sy));
-            } else {
-#pragma unroll
-                for (int i = 0; i < V; ++i) d[j][i] = T(0);
-            }
+            const bool ok = zm && ((lmask >> j) & 1u);
+            cp_async_zfill<V * sizeof(T)>(d + j * TXE, ok ? (const void *)(pb + (off0 + j * sy)) : (const void *)a.u,
+                                           ok);
         }
     };
     // plane slot of level m at plane offset p (relative to the block start)
     auto lev = [&](auto mI, auto pI) -> T (&)[NR][V] {
         constexpr int m = decltype(mI)::value;
         constexpr int p = decltype(pI)::value;
-        if constexpr (m == 0) return r0v[cmod(p, R0)];
+        if constexpr (m == 0) return r0v[cmod(p, RING)];
         else return rk[m - 1][cmod(p, RING)];
     };
-    // store a plane of owned interior points
+    // store the owned interior points of a plane
     auto store_plane = [&](T *base, const T (*v)[V]) {
 #pragma unroll
         for (int j = 0; j < NR; ++j) {
@@ -235,35 +247,51 @@ __global__ void __launch_bounds__(32 * WY) wavefront_kernel(const BlockedArgs<T>
     };
 
 #pragma unroll
-    for (int s = 0; s < PD; ++s)
-        if (qs + s < qe) load0(qs + s, r0v[s]);
+    for (int s = 0; s < PD; ++s) {
+        if (qs + s < qe) issue0(qs + s, s);
+        cp_async_commit();
+    }
 
-    const unsigned FULL = 0xffffffffu;
+    const unsigned FULLMASK = 0xffffffffu;
     const int wu = w > 0 ? w - 1 : 0, wd = w < WY - 1 ? w + 1 : WY - 1;
     const int64_t plane_elems = (int64_t)g.nx * g.ny;
+    T *const xw = xb + w * XW + lane * V;                              // this warp's edge rows
+    const T *const xup = xb + wu * XW + (2 * R - 1) * TXE + lane * V;  // last row of the warp above
+    const T *const xdn = xb + wd * XW + lane * V;                      // first row of the warp below
+    int slot = 0;                                                      // level-0 slot of plane q
 
     for (int qb = qs; qb < qe; qb += U) {
         static_for<U>([&](auto jj) {
             constexpr int j = decltype(jj)::value;
-            constexpr int par = j & 1;
             const int q = qb + j;
             if (q >= qe) return;
-            if (q + PD < qe) load0(q + PD, r0v[cmod(j + PD, R0)]);
+            // level-0 plane q: this thread's own points
+            cp_async_wait<PD - 1>();
+            {
+                const T *sp = s0t + slot * S0;
+#pragma unroll
+                for (int jr = 0; jr < NR; ++jr) vld<T, V>(r0v[j][jr], sp + jr * TXE);
+            }
             // publish the edge rows of level m's plane q - (m+1)R (consumed by
             // level m+1 in this step)
-            {
-                T *xp = xb + par * XP + w * XW + lane * V;
-                static_for<B>([&](auto mm) {
-                    constexpr int m = decltype(mm)::value;
-                    const T(&P)[NR][V] = lev(IC<m>{}, IC<j - (m + 1) * R>{});
+            static_for<B>([&](auto mm) {
+                constexpr int m = decltype(mm)::value;
+                const T(&P)[NR][V] = lev(IC<m>{}, IC<j - (m + 1) * R>{});
 #pragma unroll
-                    for (int r = 0; r < R; ++r) {
-                        vst<T, V>(xp + m * XL + r * TXE, P[r]);
-                        vst<T, V>(xp + m * XL + (R + r) * TXE, P[NR - R + r]);
-                    }
-                });
-            }
+                for (int r = 0; r < R; ++r) {
+                    vst<T, V>(xw + j * XP + m * XL + r * TXE, P[r]);
+                    vst<T, V>(xw + j * XP + m * XL + (R + r) * TXE, P[NR - R + r]);
+                }
+            });
             __syncthreads();
+            // plane q + PD into the slot read two steps ago
+            {
+                int ns = slot + PD;
+                if (ns >= NS) ns -= NS;
+                if (q + PD < qe) issue0(q + PD, ns);
+                cp_async_commit();
+                slot = slot + 1 == NS ? 0 : slot + 1;
+            }
             static_for<B>([&](auto kk) {
                 constexpr int k = decltype(kk)::value + 1;
                 if (q < qs + 2 * k * R) return;
@@ -282,12 +310,11 @@ __global__ void __launch_bounds__(32 * WY) wavefront_kernel(const BlockedArgs<T>
                     const T(&C)[NR][V] = lev(IC<k - 1>{}, IC<pc>{});
                     const T(&Zd)[NR][V] = lev(IC<k - 1>{}, IC<pc - 1>{});
                     const T(&Zu)[NR][V] = lev(IC<k - 1>{}, IC<pc + 1>{});
-                    const T *xk = xb + par * XP + (k - 1) * XL + lane * V;
                     T up[V], dn[V];
-                    vld<T, V>(up, xk + wu * XW + (2 * R - 1) * TXE);   // last row of the warp above
-                    vld<T, V>(dn, xk + wd * XW);                      // first row of the warp below
+                    vld<T, V>(up, xup + j * XP + (k - 1) * XL);
+                    vld<T, V>(dn, xdn + j * XP + (k - 1) * XL);
                     const T *cfb = nullptr;
-                    if constexpr (NA > 0) cfb = a.W + (int64_t)(zk + R) * g.sz;
+                    if constexpr (NA > 0) cfb = a.W + (int64_t)(zk + R) * sz;
                     (void)cfb;
 #pragma unroll
                     for (int jr = 0; jr < NR; ++jr) {
@@ -295,9 +322,9 @@ __global__ void __launch_bounds__(32 * WY) wavefront_kernel(const BlockedArgs<T>
                         (void)cf;
                         if constexpr (NA > 0) {
                             if ((lmask >> jr) & 1u) {
+                                const int o = off0 + jr * sy;
 #pragma unroll
-                                for (int t = 0; t < NA; ++t)
-                                    vld_g<T, V>(cf[t], cfb + t * g.nfield + (off0 + jr * sy));
+                                for (int t = 0; t < NA; ++t) vld_g<T, V>(cf[t], cfb + t * g.nfield + o);
                             } else {
 #pragma unroll
                                 for (int t = 0; t < NA; ++t)
@@ -305,8 +332,8 @@ __global__ void __launch_bounds__(32 * WY) wavefront_kernel(const BlockedArgs<T>
                                     for (int i = 0; i < V; ++i) cf[t][i] = T(0);
                             }
                         }
-                        const T left = __shfl_up_sync(FULL, C[jr][V - 1], 1);
-                        const T right = __shfl_down_sync(FULL, C[jr][0], 1);
+                        const T left = __shfl_up_sync(FULLMASK, C[jr][V - 1], 1);
+                        const T right = __shfl_down_sync(FULLMASK, C[jr][0], 1);
 #pragma unroll
                         for (int i = 0; i < V; ++i) {
                             const T c = C[jr][i];
@@ -332,14 +359,15 @@ __global__ void __launch_bounds__(32 * WY) wavefront_kernel(const BlockedArgs<T>
                         }
                     }
                 }
-                if (a.trace && zk == a.rcv_z && zk >= z0 && zk < z1) store_trace(a.trace + (k - 1) * plane_elems, D);
+                if (zk == a.rcv_z && a.trace && zk >= z0 && zk < z1) store_trace(a.trace + (k - 1) * plane_elems, D);
                 if constexpr (k == B) {
-                    store_plane(a.out + (int64_t)(zk + R) * g.sz, D);
-                    if (a.out_prev) store_plane(a.out_prev + (int64_t)(zk + R) * g.sz, lev(IC<B - 1>{}, IC<pc>{}));
+                    store_plane(a.out + (int64_t)(zk + R) * sz, D);
+                    if (a.out_prev) store_plane(a.out_prev + (int64_t)(zk + R) * sz, lev(IC<B - 1>{}, IC<pc>{}));
                 }
             });
         });
     }
+    cp_async_wait<0>();
 }
 
 // ---------------------------------------------------------------- launch
@@ -354,7 +382,7 @@ cudaError_t launch_wf(const BlockedArgs<T> &a, cudaStream_t st, int num_sms) {
     constexpr int SX = (TXE - BR - AX) / V * V;
     constexpr int SY = TYE - 2 * BR;
     auto kern = wavefront_kernel<T, KIND, B, V, NR, WY>;
-    constexpr size_t smem = sizeof(T) * 2 * B * WY * 2 * R * TXE;
+    constexpr size_t smem = wf_smem<T, V, NR, WY, B, R>();
     static_assert(smem <= 227 * 1024, "shared memory per CTA");
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
@@ -393,6 +421,9 @@ cudaError_t launch_tile(const BlockedArgs<T> &a, int tile, cudaStream_t st, int 
     constexpr int V = kVec((int)sizeof(T));
     switch (tile) {
     case 2: return launch_wf<T, KIND, B, V, 2, 16>(a, st, num_sms);   // 64 x 32, 2 rows per thread
+    case 3:
+        if constexpr (B <= 3) return launch_wf<T, KIND, B, V, 4, 16>(a, st, num_sms);   // 64 x 64
+        else return launch_wf<T, KIND, B, V, 2, 16>(a, st, num_sms);
     default: return launch_wf<T, KIND, B, V, 4, 8>(a, st, num_sms);   // 64 x 32, 4 rows per thread
     }
 }

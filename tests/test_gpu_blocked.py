@@ -94,14 +94,14 @@ def test_time_block_option_roundtrip(st):
     p.close()
 
 
-# ---- register wavefront (scheme 3; tile variants 10 and 11 for one-level passes)
+# ---- register wavefront (scheme 3; tile variants 10-12 also for one-level passes)
 
 WF_SHAPES = [(130, 75, 70), (62, 37, 23), (200, 33, 18)]
 
 
 @pytest.mark.parametrize("kind", R1)
 @pytest.mark.parametrize("b", [1, 2, 3, 4])
-@pytest.mark.parametrize("variant", [10, 11])
+@pytest.mark.parametrize("variant", [10, 11, 12])
 @pytest.mark.parametrize("shape", WF_SHAPES)
 @pytest.mark.parametrize("T", [9, 4])
 def test_wavefront_forward_fp32(st, kind, b, variant, shape, T):
@@ -124,7 +124,7 @@ def test_wavefront_forward_fp32(st, kind, b, variant, shape, T):
 
 @pytest.mark.parametrize("kind", R1)
 @pytest.mark.parametrize("b", [1, 2])
-@pytest.mark.parametrize("variant", [10, 11])
+@pytest.mark.parametrize("variant", [10, 11, 12])
 @pytest.mark.parametrize("shape", [(70, 45, 40), (34, 19, 11)])
 def test_wavefront_forward_fp64(st, kind, b, variant, shape):
     """FP64 register wavefront passes match the oracle to 1e-12."""

@@ -163,7 +163,7 @@ def test_fma_peak_probe(st):
 
 @pytest.mark.parametrize("kind", KINDS)
 @pytest.mark.parametrize("dtype", [F64, F32])
-@pytest.mark.parametrize("variant", [1, 2, 3, 4, 5, 6, 7, 8, 9, 10, 11])
+@pytest.mark.parametrize("variant", [1, 2, 3, 4, 5, 6, 7, 8, 9, 10, 11, 12])
 def test_forward_tile_variants(st, kind, dtype, variant):
     """Every forward tile variant against the oracle (ragged tiles in x, y, z)."""
     shape, T = (150, 45, 40), 3
