@@ -78,11 +78,17 @@ enum stencil_status {
 /* Plan options (stencil_plan_set / stencil_plan_get). */
 enum stencil_option {
     /* Time levels applied per pass over the lattice (the temporal block
-       depth b).  0 = library default for the kind and dtype, 1 = plain
-       one-step-per-sweep kernel. */
+       depth b).  0 = library default for the kind, dtype and scheme (3 for
+       FP32 J7_CONST and 2 for FP32 J7_VAR on the register wavefront, 1 =
+       plain sweeps otherwise), 1 = plain one-step-per-sweep kernel. */
     STENCIL_OPT_TIME_BLOCK = 1,
-    /* Tiling scheme of a blocked pass: 0 = default, 1 = overlapped tiles in
-       x and y, 2 = diamond (split) tiles in y with overlapped x. */
+    /* Kernel family of a blocked pass: 0 = default (3 for FP32 7-point
+       plans whose padded row length nx + 2 is even, 2 otherwise), 1 =
+       shared-memory planes with overlapped tiles in x and y, 2 =
+       shared-memory planes with diamond (split) tiles in y and overlapped x,
+       3 = register wavefront with overlapped tiles (7-point kinds; FP32
+       depths 1-4, FP64 depths 1-2; needs an even padded row length, else
+       the plan runs plain passes). */
     STENCIL_OPT_SCHEME = 2,
     /* Read-only: bytes of device scratch the plan holds. */
     STENCIL_OPT_SCRATCH_BYTES = 3,
@@ -96,7 +102,10 @@ enum stencil_option {
        1..4, 6, 7 = asynchronously staged tiles of 32x8, 32x16, 32x16 (4 rows
        per thread), 64x8, 64x16 and 128x8 columns, 5 = register-staged 2.5D
        kernel, 8 and 9 = 32x8 and 32x16 tiles with the per-point inputs
-       (coefficients, u^{t-1}) staged asynchronously as well. */
+       (coefficients, u^{t-1}) staged asynchronously as well, 10..12 =
+       register wavefront tiles of 64x32 (4 rows per thread), 64x32 (2 rows
+       per thread) and 64x64 points (7-point kinds; the same tiles serve the
+       blocked passes of scheme 3; other kinds run the default plain tile). */
     STENCIL_OPT_VARIANT = 5
 };
 

@@ -188,7 +188,28 @@ struct stencil_plan_s {
 
 namespace {
 
+// FP32 7-point plans whose geometry the register wavefront serves default
+// to it (measured fastest on GB300 at 512^3: depth 3 with 64x32 tiles of
+// 4 rows per thread for the constant kind, depth 2 with 2 rows per thread
+// for the variable kind); all other plans to the shared-memory kernels.
+bool wavefront_default(const stencil_plan_s *p) {
+    return p->dtype == 1 && (p->kind == J7_CONST || p->kind == J7_VAR) &&
+           wavefront_supported(p->kind, p->dtype, 1, p->g);
+}
+
+int plan_scheme(const stencil_plan_s *p) {
+    if (p->scheme) return p->scheme;
+    return wavefront_default(p) ? 3 : 2;
+}
+
+int plan_variant(const stencil_plan_s *p) {
+    if (p->variant) return p->variant;
+    if (wavefront_default(p)) return p->kind == J7_CONST ? 10 : 11;
+    return default_variant(p->kind, p->dtype);
+}
+
 int default_time_block(const stencil_plan_s *p) {
+    if (plan_scheme(p) == 3 && wavefront_default(p)) return p->kind == J7_CONST ? 3 : 2;
     return blocked_default_levels(p->kind, p->dtype);
 }
 
@@ -196,7 +217,7 @@ int default_time_block(const stencil_plan_s *p) {
 // pass of tile variant >= 10) when it supports the kind, dtype, depth and
 // geometry; the shared-memory blocked kernels serve schemes 1 and 2.
 bool pass_supported(const stencil_plan_s *p, int levels) {
-    if (p->scheme == 3) return wavefront_supported(p->kind, p->dtype, levels, p->g);
+    if (plan_scheme(p) == 3) return wavefront_supported(p->kind, p->dtype, levels, p->g);
     return blocked_supported(p->kind, p->dtype, levels);
 }
 
@@ -241,7 +262,8 @@ template <typename T>
 cudaError_t plain_step(stencil_plan_s *p, bool adjoint, const Scalars &s, const stencil_coeffs_t *coeffs,
                        const void *in_p, const void *in_c, void *out, T *trace, const T *inject, int64_t rcv_z,
                        cudaStream_t st) {
-    if (!adjoint && p->variant >= 10 && wavefront_supported(p->kind, p->dtype, 1, p->g)) {
+    const int variant = plan_variant(p);
+    if (!adjoint && variant >= 10 && wavefront_supported(p->kind, p->dtype, 1, p->g)) {
         BlockedArgs<T> w;
         memset(&w, 0, sizeof(w));
         w.u = (const T *)in_c;
@@ -252,7 +274,7 @@ cudaError_t plain_step(stencil_plan_s *p, bool adjoint, const Scalars &s, const 
         w.rcv_z = (int)rcv_z;
         w.trace = trace;
         w.levels = 1;
-        return launch_wavefront<T>(p->kind, w, p->variant - 9, st, p->num_sms);
+        return launch_wavefront<T>(p->kind, w, variant - 9, st, p->num_sms);
     }
     SweepArgs<T> a;
     memset(&a, 0, sizeof(a));
@@ -265,7 +287,7 @@ cudaError_t plain_step(stencil_plan_s *p, bool adjoint, const Scalars &s, const 
     a.rcv_z = (int)rcv_z;
     a.trace = trace;
     a.inject = inject;
-    a.variant = p->variant < 10 ? p->variant : 0;  // 10+: register wavefront tiles
+    a.variant = variant < 10 ? variant : 0;  // 10+: register wavefront tiles
     return launch_plain<T>(p->kind, adjoint, a, st, p->num_sms);
 }
 
@@ -331,12 +353,13 @@ int run_program(stencil_plan_s *p, void *pair_p, void *pair_c, const stencil_coe
             a.trace = trace ? (T *)trace + t * plane : nullptr;
             a.levels = o.levels;
             cudaError_t e;
-            if (p->scheme == 3) {
-                e = launch_wavefront<T>(p->kind, a, p->variant >= 10 ? p->variant - 9 : 0, st, p->num_sms);
+            const int scheme = plan_scheme(p), variant = plan_variant(p);
+            if (scheme == 3) {
+                e = launch_wavefront<T>(p->kind, a, variant >= 10 ? variant - 9 : 0, st, p->num_sms);
             } else {
                 if (blocked_scratch_levels(o.levels) > p->nbands) return STENCIL_EUNSUPPORTED;
                 for (int k = 1; k < o.levels; ++k) a.bands[k] = (T *)p->bands[k - 1];
-                e = launch_blocked<T>(p->kind, a, st, p->num_sms, p->scheme);
+                e = launch_blocked<T>(p->kind, a, st, p->num_sms, scheme);
             }
             if (e != cudaSuccess) return cuda_fail(e);
         }
@@ -422,7 +445,7 @@ void free_bands(stencil_plan_s *p) {
 // Allocate the band buffers of the effective block depth (plan time only).
 int ensure_bands(stencil_plan_s *p) {
     const int b = effective_time_block(p);
-    const int need = (b > 1 && p->scheme != 3) ? blocked_scratch_levels(b) : 0;
+    const int need = (b > 1 && plan_scheme(p) != 3) ? blocked_scratch_levels(b) : 0;
     if (need <= p->nbands) return STENCIL_OK;
     free_bands(p);
     for (int i = 0; i < need; ++i) {
@@ -553,9 +576,9 @@ int stencil_plan_get(stencil_plan_t p, int option, int64_t *value) {
     if (!p || !value) return STENCIL_EINVAL;
     switch (option) {
     case STENCIL_OPT_TIME_BLOCK: *value = effective_time_block(p); return STENCIL_OK;
-    case STENCIL_OPT_SCHEME: *value = p->scheme; return STENCIL_OK;
+    case STENCIL_OPT_SCHEME: *value = plan_scheme(p); return STENCIL_OK;
     case STENCIL_OPT_GRAD_BATCH: *value = p->grad_batch; return STENCIL_OK;
-    case STENCIL_OPT_VARIANT: *value = p->variant ? p->variant : default_variant(p->kind, p->dtype); return STENCIL_OK;
+    case STENCIL_OPT_VARIANT: *value = plan_variant(p); return STENCIL_OK;
     case STENCIL_OPT_SCRATCH_BYTES:
         *value = (int64_t)((p->scratch[0] ? 2 * p->field_bytes : 0) + (p->nbands + p->ngring) * p->field_bytes +
                            p->npartials * sizeof(double));

@@ -84,6 +84,8 @@ def test_blocked_forward_fp64(st, kind, scheme, shape):
 
 def test_time_block_option_roundtrip(st):
     p = st.Plan(1, 32, 32, 32, F32)
+    assert p.get(2) == 3 and p.get(1) == 3 and p.get(5) == 10   # FP32 7-point defaults
+    p.set(2, 2)                                                  # shared-memory diamond tiles
     p.set(1, 4)
     assert p.get(1) == 4
     assert p.get(3) >= 3 * 34 * 34 * 34 * 4  # three band fields
