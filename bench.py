@@ -434,8 +434,13 @@ def run_ours(args):
     if tr is not None:
         roofline["traffic"] = tr[0] * float(n) ** 3
         roofline["traffic_source"] = tr[1] + " (bytes per update x updates per launch)"
-    roofline["kernel"] = ("plain_sweep_kernel" if main["time_block"] == 1 else "blocked_kernel (phase A + B)") + \
-        f"<{'double' if dtype == st.F64 else 'float'}, {args.kind}>"
+    if main["scheme"] == 3 or main["variant"] >= 10:
+        kname = f"wavefront_kernel (register wavefront, {main['time_block']} levels per pass)"
+    elif main["time_block"] == 1:
+        kname = "plain_stream_kernel" if main["variant"] != 5 else "plain_sweep_kernel"
+    else:
+        kname = "blocked_kernel (phase A + B)" if main["scheme"] == 2 else "blocked_kernel (overlapped)"
+    roofline["kernel"] = kname + f"<{'double' if dtype == st.F64 else 'float'}, {args.kind}>"
     roofline["peak_source"] = ("2 FP64 FMA/clk/SM x %d SMs x %.0f MHz (measured clock); FMA-chain probe %.3f TFLOP/s"
                                % (num_sms, clk / 1e6, probe_f64 / 1e12)) if dtype == st.F64 else \
         "MEASURED_PEAKS.json hbm_gbs (copy, measured)"
