@@ -287,7 +287,11 @@ cudaError_t plain_step(stencil_plan_s *p, bool adjoint, const Scalars &s, const 
     a.rcv_z = (int)rcv_z;
     a.trace = trace;
     a.inject = inject;
-    a.variant = variant < 10 ? variant : 0;  // 10+: register wavefront tiles
+    // the vectorised 25-point sweep (forward; the constant kind is its own adjoint)
+    if ((variant == 13 || variant == 14) && (!adjoint || p->kind == W25_CONST) &&
+        (p->dtype == 1 ? plainv_supported_f32(p->kind, p->g) : plainv_supported_f64(p->kind, p->g)))
+        return launch_plainv_kind<T>(p->kind, a, variant, st, p->num_sms);
+    a.variant = variant < 10 ? variant : 0;  // 10+: register wavefront / vectorised tiles
     return launch_plain<T>(p->kind, adjoint, a, st, p->num_sms);
 }
 
@@ -560,7 +564,7 @@ int stencil_plan_set(stencil_plan_t p, int option, int64_t value) {
         p->scheme = (int)value;
         return ensure_bands(p);
     case STENCIL_OPT_VARIANT:
-        if (value < 0 || value > 12) return STENCIL_EINVAL;
+        if (value < 0 || value > 14) return STENCIL_EINVAL;
         p->variant = (int)value;
         return STENCIL_OK;
     case STENCIL_OPT_GRAD_BATCH:

@@ -43,6 +43,14 @@ template <typename T>
 cudaError_t launch_axpby(double alpha, const T *x, double beta, const T *y, T *out, int64_t n, int num_sms,
                          cudaStream_t st);
 
+// Vectorised plain sweep of the 25-point kinds (plainv_impl.cuh): tile
+// variant 13 = 8 rows per CTA, 14 = 16 rows per CTA.  Served when the kind
+// has radius 4 and nx is a multiple of the vector width (4 FP32, 2 FP64).
+bool plainv_supported_f32(int kind, const Geom &g);
+bool plainv_supported_f64(int kind, const Geom &g);
+template <typename T>
+cudaError_t launch_plainv_kind(int kind, const SweepArgs<T> &a, int variant, cudaStream_t st, int num_sms);
+
 // FP64 / FP32 FMA throughput probe.
 cudaError_t run_fma_peak(int dtype, cudaStream_t st, double *flops, double *clock_hz);
 

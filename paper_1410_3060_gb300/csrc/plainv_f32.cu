@@ -1,0 +1,10 @@
+// plainv_f32.cu -- FP32 instances of the vectorised plain sweep of the 25-point kinds.
+#include "plainv_impl.cuh"
+
+namespace stc {
+
+bool plainv_supported_f32(int kind, const Geom &g) { return plainv_supported<float>(kind, g); }
+
+template cudaError_t launch_plainv_kind<float>(int, const SweepArgs<float> &, int, cudaStream_t, int);
+
+}  // namespace stc

@@ -1,0 +1,10 @@
+// plainv_f64.cu -- FP64 instances of the vectorised plain sweep of the 25-point kinds.
+#include "plainv_impl.cuh"
+
+namespace stc {
+
+bool plainv_supported_f64(int kind, const Geom &g) { return plainv_supported<double>(kind, g); }
+
+template cudaError_t launch_plainv_kind<double>(int, const SweepArgs<double> &, int, cudaStream_t, int);
+
+}  // namespace stc

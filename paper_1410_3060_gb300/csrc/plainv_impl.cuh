@@ -1,0 +1,328 @@
+// plainv_impl.cuh -- vectorised plain sweep (one level per launch) of the
+// 25-point kinds (Fig. 1d, 1e structures, R = 4), written for few
+// instructions per lattice update.
+//
+// Per thread: V consecutive x points (16-byte vectors: 4 FP32 or 2 FP64
+// values) of one row; a warp covers 32 V columns, a CTA WY rows.  The field
+// plane (tile plus an R-point halo on every side) is staged by cp.async PD
+// planes ahead into a ring of shared slots (16-byte copies, zero fill outside
+// the padded array); x and y neighbours are 16-byte shared loads (R is a
+// multiple of V, so every neighbour vector is aligned); the 2R+1 planes along
+// z of the thread's points live in a register ring (the step loop is unrolled
+// by 2R+1 so ring slots are registers); u^{t-1} and the coefficients of the
+// thread's points are 16-byte global loads.  Compared with the one-point-per-
+// thread kernels every address, copy and load serves V points.
+#pragma once
+#include "plain.cuh"
+
+namespace stc {
+
+namespace pv {
+
+template <typename T> struct V16;
+template <> struct V16<float> { using type = float4; static constexpr int n = 4; };
+template <> struct V16<double> { using type = double2; static constexpr int n = 2; };
+
+template <typename T>
+__device__ __forceinline__ void ld16(T (&d)[V16<T>::n], const T *p) {
+    const auto v = *reinterpret_cast<const typename V16<T>::type *>(p);
+    if constexpr (V16<T>::n == 4) {
+        d[0] = v.x; d[1] = v.y; d[2] = v.z; d[3] = v.w;
+    } else {
+        d[0] = v.x; d[1] = v.y;
+    }
+}
+template <typename T>
+__device__ __forceinline__ void ldg16(T (&d)[V16<T>::n], const T *p) {
+    const auto v = __ldg(reinterpret_cast<const typename V16<T>::type *>(p));
+    if constexpr (V16<T>::n == 4) {
+        d[0] = v.x; d[1] = v.y; d[2] = v.z; d[3] = v.w;
+    } else {
+        d[0] = v.x; d[1] = v.y;
+    }
+}
+template <typename T>
+__device__ __forceinline__ void st16(T *p, const T (&s)[V16<T>::n]) {
+    typename V16<T>::type v;
+    if constexpr (V16<T>::n == 4) {
+        v.x = s[0]; v.y = s[1]; v.z = s[2]; v.w = s[3];
+    } else {
+        v.x = s[0]; v.y = s[1];
+    }
+    *reinterpret_cast<typename V16<T>::type *>(p) = v;
+}
+
+template <typename T, int KIND, int WY>
+struct Tile {
+    static constexpr int R = KindTraits<KIND>::R;
+    static constexpr int V = V16<T>::n;
+    static constexpr int TX = 32 * V, TY = WY;
+    static constexpr int SW = TX + 2 * R, SH = TY + 2 * R, SP = SW * SH;
+    static constexpr int PD = 2;                 // planes in flight
+    static constexpr int NS = R + 1 + PD;        // shared plane slots
+    static constexpr size_t smem = sizeof(T) * (size_t)NS * SP;
+};
+
+}  // namespace pv
+
+template <typename T, int KIND, int WY>
+__global__ void __launch_bounds__(32 * WY) plainv_kernel(const SweepArgs<T> a) {
+    using TL = pv::Tile<T, KIND, WY>;
+    constexpr int R = TL::R, V = TL::V;
+    constexpr bool WAVE = KindTraits<KIND>::WAVE;
+    constexpr int NA = KindTraits<KIND>::NARR;
+    static_assert(R % V == 0, "neighbour vectors aligned");
+    constexpr int RING = 2 * R + 1;
+    constexpr int PD = TL::PD, NS = TL::NS;
+    constexpr int TX = TL::TX, TY = TL::TY, SW = TL::SW, SH = TL::SH, SP = TL::SP;
+    constexpr int VPR = SW / V;                  // vectors per shared row
+    constexpr int NVEC = VPR * SH;               // vectors per plane
+    constexpr int NT = 32 * WY;
+    constexpr int NC = (NVEC + NT - 1) / NT;     // copies per thread per plane
+    static_assert(NC <= 32, "copy mask");
+
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    T *const sb = reinterpret_cast<T *>(smem_raw);
+
+    const Geom &g = a.g;
+    const int lane = threadIdx.x, w = threadIdx.y, tid = w * 32 + lane;
+    const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;   // padded origin of the shared tile
+    const int z0 = blockIdx.z * a.zchunk;
+    const int z1 = min(z0 + a.zchunk, g.nz);
+    const int qs = z0 - R, qe = z1 + R;
+    const int sy = (int)g.sy;
+    const int64_t sz = g.sz;
+
+    // copy plan: vector v = tid + c NT of the shared tile
+    int goff[NC], soff[NC];
+    uint32_t cmask = 0;
+#pragma unroll
+    for (int c = 0; c < NC; ++c) {
+        const int v = tid + c * NT;
+        const int row = v / VPR, vc = v - row * VPR;
+        const int gx = x0 + vc * V, gy = y0 + row;
+        goff[c] = gy * sy + gx;
+        soff[c] = row * SW + vc * V;
+        if (v < NVEC && gx < g.px && gy < g.py) cmask |= 1u << c;
+        if (v >= NVEC) soff[c] = 0;
+    }
+    auto issue = [&](int q, int slot) {
+        const bool zm = q >= -R && q < g.nz + R;
+        const T *pb = a.u + (zm ? (int64_t)(q + R) * sz : 0);
+        T *d = sb + slot * SP;
+#pragma unroll
+        for (int c = 0; c < NC; ++c) {
+            if (tid + c * NT >= NVEC) continue;
+            const bool ok = zm && ((cmask >> c) & 1u);
+            cp_async_zfill<16>(d + soff[c], ok ? (const void *)(pb + goff[c]) : (const void *)a.u, ok);
+        }
+    };
+
+    // this thread's points: padded row y0 + R + w, columns x0 + R + lane V ..
+    const int px = x0 + R + lane * V, py = y0 + R + w;
+    const bool own = px < g.nx + R && py < g.ny + R;   // nx % V == 0: whole vector in or out
+    const int poff = py * sy + px;
+    const int scen = (R + w) * SW + R + lane * V;      // shared offset of the own vector
+
+    T ring[RING][V];
+#pragma unroll
+    for (int s = 0; s < RING; ++s)
+#pragma unroll
+        for (int i = 0; i < V; ++i) ring[s][i] = T(0);
+
+#pragma unroll
+    for (int s = 0; s < PD; ++s) {
+        if (qs + s < qe) issue(qs + s, s);
+        cp_async_commit();
+    }
+    const T s0 = T(a.s.c[0]), s1 = T(a.s.c[1]), s2 = T(a.s.c[2]);
+    const T s3 = T(a.s.c[3]), s4 = T(a.s.c[4]);
+    (void)s0; (void)s1; (void)s2; (void)s3; (void)s4;
+
+    int slot = 0;   // shared slot of plane q
+    for (int qb = qs; qb < qe; qb += RING) {
+        static_for<RING>([&](auto jj) {
+            constexpr int j = decltype(jj)::value;
+            const int q = qb + j;
+            if (q >= qe) return;
+            cp_async_wait<PD - 1>();
+            __syncthreads();
+            pv::ld16<T>(ring[j], sb + slot * SP + scen);
+            {
+                int ns = slot + PD;
+                if (ns >= NS) ns -= NS;
+                if (q + PD < qe) issue(q + PD, ns);
+                cp_async_commit();
+            }
+            const int z = q - R;
+            int zslot = slot - R;
+            if (zslot < 0) zslot += NS;
+            slot = slot + 1 == NS ? 0 : slot + 1;
+            if (z < z0) return;
+            // centre plane z: in-plane neighbours from shared memory
+            const T *sc = sb + zslot * SP + scen;
+            T lv[R / V][V], rv[R / V][V];   // the R columns left and right of the own vector
+#pragma unroll
+            for (int m = 0; m < R / V; ++m) {
+                pv::ld16<T>(lv[m], sc - (m + 1) * V);   // columns -V(m+1) .. -V m - 1
+                pv::ld16<T>(rv[m], sc + (m + 1) * V);   // columns V(m+1) .. V(m+2) - 1
+            }
+            T yv[2][R][V];
+#pragma unroll
+            for (int d = 1; d <= R; ++d) {
+                pv::ld16<T>(yv[0][d - 1], sc - d * SW);
+                pv::ld16<T>(yv[1][d - 1], sc + d * SW);
+            }
+            const int64_t zo = (int64_t)(z + R) * sz + poff;
+            T pvv[V];
+            if constexpr (WAVE) {
+                if (own) {
+                    pv::ld16<T>(pvv, a.u_prev + zo);
+                } else {
+#pragma unroll
+                    for (int i = 0; i < V; ++i) pvv[i] = T(0);
+                }
+            }
+            (void)pvv;
+            T res[V];
+            // neighbour value of point i at x offset e (|e| <= R)
+            auto xval = [&](int i, int e) -> T {
+                const int c = i + e;   // column relative to the own vector start
+                if (c < 0) {
+                    const int m = (-c - 1) / V;            // vector m to the left
+                    return lv[m][V - 1 - ((-c - 1) % V)];
+                } else if (c >= V) {
+                    const int m = (c - V) / V;
+                    return rv[m][(c - V) % V];
+                }
+                return ring[cmod(j - R, RING)][c];
+            };
+            if constexpr (KIND == W25_VAR || KIND == J25_VAR) {
+                T cf[NA][V];
+                if (own) {
+#pragma unroll
+                    for (int t = 0; t < NA; ++t) pv::ldg16<T>(cf[t], a.W + t * g.nfield + zo);
+                } else {
+#pragma unroll
+                    for (int t = 0; t < NA; ++t)
+#pragma unroll
+                        for (int i = 0; i < V; ++i) cf[t][i] = T(0);
+                }
+#pragma unroll
+                for (int i = 0; i < V; ++i) {
+                    const T c = ring[cmod(j - R, RING)][i];
+                    T acc = cf[0][i] * c;
+                    if constexpr (WAVE) acc = fma(T(2), c, acc) - pvv[i];
+#pragma unroll
+                    for (int r = 0; r < 4; ++r) {
+                        const int d = r + 1;
+                        acc = fma(cf[3 * r + 1][i], xval(i, -d) + xval(i, d), acc);
+                        acc = fma(cf[3 * r + 2][i], yv[0][r][i] + yv[1][r][i], acc);
+                        acc = fma(cf[3 * r + 3][i], ring[cmod(j - R - d, RING)][i] + ring[cmod(j - R + d, RING)][i], acc);
+                    }
+                    res[i] = acc;
+                }
+            } else {
+                T al[V];
+                if constexpr (KIND == W25_ALPHA) {
+                    if (own) {
+                        pv::ldg16<T>(al, a.W + zo);
+                    } else {
+#pragma unroll
+                        for (int i = 0; i < V; ++i) al[i] = T(0);
+                    }
+                }
+                (void)al;
+                const T wr[4] = {s1, s2, s3, s4};
+#pragma unroll
+                for (int i = 0; i < V; ++i) {
+                    const T c = ring[cmod(j - R, RING)][i];
+                    if constexpr (KIND == W25_CONST) {
+                        T acc = s0 * c - pvv[i];
+#pragma unroll
+                        for (int r = 0; r < 4; ++r) {
+                            const int d = r + 1;
+                            acc = fma(wr[r], ((xval(i, -d) + xval(i, d)) + (yv[0][r][i] + yv[1][r][i])) +
+                                                 (ring[cmod(j - R - d, RING)][i] + ring[cmod(j - R + d, RING)][i]),
+                                      acc);
+                        }
+                        res[i] = acc;
+                    } else {  // W25_ALPHA
+                        T sacc = s0 * c;
+#pragma unroll
+                        for (int r = 0; r < 4; ++r) {
+                            const int d = r + 1;
+                            sacc = fma(wr[r], ((xval(i, -d) + xval(i, d)) + (yv[0][r][i] + yv[1][r][i])) +
+                                                  (ring[cmod(j - R - d, RING)][i] + ring[cmod(j - R + d, RING)][i]),
+                                       sacc);
+                        }
+                        res[i] = fma(al[i], sacc, T(2) * c - pvv[i]);
+                    }
+                }
+            }
+            if (own) {
+                if (z == a.rcv_z) {
+                    const int64_t pl = (int64_t)(py - R) * g.nx + (px - R);
+#pragma unroll
+                    for (int i = 0; i < V; ++i) {
+                        if (a.inject) res[i] += a.inject[pl + i];
+                        if (a.trace) a.trace[pl + i] = res[i];
+                    }
+                }
+                pv::st16<T>(a.out + zo, res);
+            }
+        });
+    }
+    cp_async_wait<0>();
+}
+
+// Whether the vectorised sweep serves this kind and geometry.
+template <typename T>
+inline bool plainv_supported(int kind, const Geom &g) {
+    constexpr int V = pv::V16<T>::n;
+    return kind_radius(kind) == 4 && g.nx % V == 0 && (int64_t)g.px * g.py < ((int64_t)1 << 30);
+}
+
+template <typename T, int KIND, int WY>
+cudaError_t launch_plainv(const SweepArgs<T> &a, cudaStream_t st, int num_sms) {
+    using TL = pv::Tile<T, KIND, WY>;
+    constexpr int R = TL::R;
+    auto kern = plainv_kernel<T, KIND, WY>;
+    static_assert(TL::smem <= 227 * 1024, "shared memory per CTA");
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TL::smem);
+    if (e != cudaSuccess) return e;
+    int per_sm = 0;
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 32 * WY, TL::smem);
+    if (per_sm < 1) per_sm = 1;
+    const int gx = (a.g.nx + TL::TX - 1) / TL::TX, gy = (a.g.ny + TL::TY - 1) / TL::TY;
+    // z chunks: minimise (waves of resident CTAs) x (planes per chunk incl. the 2R re-read)
+    const int64_t resident = (int64_t)num_sms * per_sm, tiles = (int64_t)gx * gy;
+    int best = 1;
+    double best_cost = 1e300;
+    for (int nzc = 1; nzc <= a.g.nz; ++nzc) {
+        const int chunk = (a.g.nz + nzc - 1) / nzc;
+        if (nzc > 1 && chunk < 4 * R) break;
+        const int64_t ctas = tiles * ((a.g.nz + chunk - 1) / chunk);
+        const double cost = (double)((ctas + resident - 1) / resident) * (chunk + 2 * R);
+        if (cost < best_cost * 0.999) { best_cost = cost; best = nzc; }
+    }
+    SweepArgs<T> b = a;
+    b.zchunk = (a.g.nz + best - 1) / best;
+    dim3 grid(gx, gy, (a.g.nz + b.zchunk - 1) / b.zchunk), block(32, WY, 1);
+    kern<<<grid, block, TL::smem, st>>>(b);
+    return cudaGetLastError();
+}
+
+template <typename T>
+cudaError_t launch_plainv_kind(int kind, const SweepArgs<T> &a, int variant, cudaStream_t st, int num_sms) {
+    const bool big = variant == 14;
+    switch (kind) {
+    case W25_CONST: return big ? launch_plainv<T, W25_CONST, 16>(a, st, num_sms) : launch_plainv<T, W25_CONST, 8>(a, st, num_sms);
+    case W25_VAR: return big ? launch_plainv<T, W25_VAR, 16>(a, st, num_sms) : launch_plainv<T, W25_VAR, 8>(a, st, num_sms);
+    case J25_VAR: return big ? launch_plainv<T, J25_VAR, 16>(a, st, num_sms) : launch_plainv<T, J25_VAR, 8>(a, st, num_sms);
+    case W25_ALPHA: return big ? launch_plainv<T, W25_ALPHA, 16>(a, st, num_sms) : launch_plainv<T, W25_ALPHA, 8>(a, st, num_sms);
+    default: return cudaErrorNotSupported;
+    }
+}
+
+}  // namespace stc

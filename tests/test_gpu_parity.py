@@ -82,11 +82,13 @@ def rand_interior(n, R, rng):
 
 @pytest.mark.parametrize("kind", KINDS)
 @pytest.mark.parametrize("dtype", [F64, F32])
-@pytest.mark.parametrize("variant", [0, 5])
+@pytest.mark.parametrize("variant", [0, 5, 13])
 def test_adjoint_with_residual_and_gradient(st, kind, dtype, variant):
+    """Adjoint sweeps (variant 13: the vectorised 25-point sweep serves the
+    self-adjoint constant kind; other kinds keep their adjoint kernels)."""
     import torch
     rng = np.random.default_rng(10 + kind)
-    n = (37, 29, 21)
+    n = (37, 29, 21) if variant != 13 else (40, 29, 21)
     T = 4
     wk = wl.make(kind, n, T, seed=4)
     R = wk.R
@@ -163,12 +165,26 @@ def test_fma_peak_probe(st):
 
 @pytest.mark.parametrize("kind", KINDS)
 @pytest.mark.parametrize("dtype", [F64, F32])
-@pytest.mark.parametrize("variant", [1, 2, 3, 4, 5, 6, 7, 8, 9, 10, 11, 12])
+@pytest.mark.parametrize("variant", [1, 2, 3, 4, 5, 6, 7, 8, 9, 10, 11, 12, 13, 14])
 def test_forward_tile_variants(st, kind, dtype, variant):
     """Every forward tile variant against the oracle (ragged tiles in x, y, z)."""
-    shape, T = (150, 45, 40), 3
+    check_forward_variant(st, kind, dtype, variant, (150, 45, 40))
+
+
+@pytest.mark.parametrize("kind", [3, 4, 5, 6])
+@pytest.mark.parametrize("dtype", [F64, F32])
+@pytest.mark.parametrize("variant", [13, 14])
+@pytest.mark.parametrize("shape", [(136, 45, 40), (64, 19, 11), (264, 9, 30)])
+def test_vectorised_25pt_sweep(st, kind, dtype, variant, shape):
+    """The vectorised 25-point sweep (nx a multiple of the vector width)
+    against the oracle: ragged tiles in x, y and z, receiver trace."""
+    check_forward_variant(st, kind, dtype, variant, shape)
+
+
+def check_forward_variant(st, kind, dtype, variant, shape):
+    T = 3
     wk = wl.make(kind, shape, T, seed=8)
-    rz = 11
+    rz = min(11, shape[2] - 1)
     op, ou, otr = oracle_forward(wk, T, rcv_z=rz)
     import gpu_util
     torch = gpu_util.torch_mod()
