@@ -44,7 +44,8 @@ cudaError_t launch_axpby(double alpha, const T *x, double beta, const T *y, T *o
                          cudaStream_t st);
 
 // Vectorised plain sweep of the 25-point kinds (plainv_impl.cuh): tile
-// variant 13 = 8 rows per CTA, 14 = 16 rows per CTA.  Served when the kind
+// variant 13 = 8 rows per CTA, 14 = 16 rows per CTA (4 for the 13-array
+// kinds).  Served when the kind
 // has radius 4 and nx is a multiple of the vector width (4 FP32, 2 FP64).
 bool plainv_supported_f32(int kind, const Geom &g);
 bool plainv_supported_f64(int kind, const Geom &g);

@@ -60,13 +60,19 @@ struct Tile {
     static constexpr int SW = TX + 2 * R, SH = TY + 2 * R, SP = SW * SH;
     static constexpr int PD = 2;                 // planes in flight
     static constexpr int NS = R + 1 + PD;        // shared plane slots
-    static constexpr size_t smem = sizeof(T) * (size_t)NS * SP;
+    // per-point inputs staged with the field plane: u^{t-1} (second-order
+    // kinds) and a single coefficient array (alpha); 13-array kinds load
+    // their coefficients directly
+    static constexpr int NPS = (KindTraits<KIND>::WAVE ? 1 : 0) + (KindTraits<KIND>::NARR == 1 ? 1 : 0);
+    static constexpr int PP = TX * TY;           // one per-point plane
+    static constexpr size_t smem = sizeof(T) * ((size_t)NS * SP + (size_t)NS * NPS * PP);
+    static constexpr int MINB = 1;
 };
 
 }  // namespace pv
 
 template <typename T, int KIND, int WY>
-__global__ void __launch_bounds__(32 * WY) plainv_kernel(const SweepArgs<T> a) {
+__global__ void __launch_bounds__(32 * WY, pv::Tile<T, KIND, WY>::MINB) plainv_kernel(const SweepArgs<T> a) {
     using TL = pv::Tile<T, KIND, WY>;
     constexpr int R = TL::R, V = TL::V;
     constexpr bool WAVE = KindTraits<KIND>::WAVE;
@@ -81,8 +87,10 @@ __global__ void __launch_bounds__(32 * WY) plainv_kernel(const SweepArgs<T> a) {
     constexpr int NC = (NVEC + NT - 1) / NT;     // copies per thread per plane
     static_assert(NC <= 32, "copy mask");
 
+    constexpr int NPS = TL::NPS, PP = TL::PP;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T *const sb = reinterpret_cast<T *>(smem_raw);
+    T *const spp = sb + NS * SP;                 // [NS][NPS][TY][TX]
 
     const Geom &g = a.g;
     const int lane = threadIdx.x, w = threadIdx.y, tid = w * 32 + lane;
@@ -106,6 +114,14 @@ __global__ void __launch_bounds__(32 * WY) plainv_kernel(const SweepArgs<T> a) {
         if (v < NVEC && gx < g.px && gy < g.py) cmask |= 1u << c;
         if (v >= NVEC) soff[c] = 0;
     }
+    // this thread's points: padded row y0 + R + w, columns x0 + R + lane V ..
+    const int px = x0 + R + lane * V, py = y0 + R + w;
+    const bool own = px < g.nx + R && py < g.ny + R;   // nx % V == 0: whole vector in or out
+    const int poff = py * sy + px;
+    const int scen = (R + w) * SW + R + lane * V;      // shared offset of the own vector
+    const int pown = w * TX + lane * V;                // offset in a per-point plane
+    // field plane q (tile and halo) and the per-point inputs of output plane
+    // q - R into slot `slot`
     auto issue = [&](int q, int slot) {
         const bool zm = q >= -R && q < g.nz + R;
         const T *pb = a.u + (zm ? (int64_t)(q + R) * sz : 0);
@@ -116,13 +132,19 @@ __global__ void __launch_bounds__(32 * WY) plainv_kernel(const SweepArgs<T> a) {
             const bool ok = zm && ((cmask >> c) & 1u);
             cp_async_zfill<16>(d + soff[c], ok ? (const void *)(pb + goff[c]) : (const void *)a.u, ok);
         }
+        if constexpr (NPS > 0) {
+            // own points of planes this chunk computes only (an in-place
+            // update overwrites u^{t-1} of the planes it owns)
+            const int zq = q - R;
+            const bool ok = own && zq >= z0 && zq < z1;
+            const int64_t zo = ok ? (int64_t)(zq + R) * sz + poff : 0;
+            T *dp = spp + slot * (NPS * PP) + pown;
+            if constexpr (KindTraits<KIND>::WAVE)
+                cp_async_zfill<16>(dp, ok ? (const void *)(a.u_prev + zo) : (const void *)a.u, ok);
+            if constexpr (NA == 1)
+                cp_async_zfill<16>(dp + (NPS - 1) * PP, ok ? (const void *)(a.W + zo) : (const void *)a.u, ok);
+        }
     };
-
-    // this thread's points: padded row y0 + R + w, columns x0 + R + lane V ..
-    const int px = x0 + R + lane * V, py = y0 + R + w;
-    const bool own = px < g.nx + R && py < g.ny + R;   // nx % V == 0: whole vector in or out
-    const int poff = py * sy + px;
-    const int scen = (R + w) * SW + R + lane * V;      // shared offset of the own vector
 
     T ring[RING][V];
 #pragma unroll
@@ -145,16 +167,37 @@ __global__ void __launch_bounds__(32 * WY) plainv_kernel(const SweepArgs<T> a) {
             constexpr int j = decltype(jj)::value;
             const int q = qb + j;
             if (q >= qe) return;
+            const int z = q - R;
+            const int64_t zo = (int64_t)(z + R) * sz + poff;
+            // 13-array kinds: the coefficients of output plane z, issued before
+            // the wait so that their latency overlaps it
+            T cf[NA > 1 ? NA : 1][V];
+            (void)cf;
+            if constexpr (NA > 1) {
+                if (own && z >= z0) {
+#pragma unroll
+                    for (int t = 0; t < NA; ++t) pv::ldg16<T>(cf[t], a.W + t * g.nfield + zo);
+                } else {
+#pragma unroll
+                    for (int t = 0; t < NA; ++t)
+#pragma unroll
+                        for (int i = 0; i < V; ++i) cf[t][i] = T(0);
+                }
+            }
             cp_async_wait<PD - 1>();
             __syncthreads();
             pv::ld16<T>(ring[j], sb + slot * SP + scen);
+            // staged per-point inputs of output plane z
+            T pvv[V], al[V];
+            (void)pvv; (void)al;
+            if constexpr (KindTraits<KIND>::WAVE) pv::ld16<T>(pvv, spp + slot * (NPS * PP) + pown);
+            if constexpr (NA == 1) pv::ld16<T>(al, spp + slot * (NPS * PP) + (NPS - 1) * PP + pown);
             {
                 int ns = slot + PD;
                 if (ns >= NS) ns -= NS;
                 if (q + PD < qe) issue(q + PD, ns);
                 cp_async_commit();
             }
-            const int z = q - R;
             int zslot = slot - R;
             if (zslot < 0) zslot += NS;
             slot = slot + 1 == NS ? 0 : slot + 1;
@@ -173,17 +216,6 @@ __global__ void __launch_bounds__(32 * WY) plainv_kernel(const SweepArgs<T> a) {
                 pv::ld16<T>(yv[0][d - 1], sc - d * SW);
                 pv::ld16<T>(yv[1][d - 1], sc + d * SW);
             }
-            const int64_t zo = (int64_t)(z + R) * sz + poff;
-            T pvv[V];
-            if constexpr (WAVE) {
-                if (own) {
-                    pv::ld16<T>(pvv, a.u_prev + zo);
-                } else {
-#pragma unroll
-                    for (int i = 0; i < V; ++i) pvv[i] = T(0);
-                }
-            }
-            (void)pvv;
             T res[V];
             // neighbour value of point i at x offset e (|e| <= R)
             auto xval = [&](int i, int e) -> T {
@@ -198,16 +230,6 @@ __global__ void __launch_bounds__(32 * WY) plainv_kernel(const SweepArgs<T> a) {
                 return ring[cmod(j - R, RING)][c];
             };
             if constexpr (KIND == W25_VAR || KIND == J25_VAR) {
-                T cf[NA][V];
-                if (own) {
-#pragma unroll
-                    for (int t = 0; t < NA; ++t) pv::ldg16<T>(cf[t], a.W + t * g.nfield + zo);
-                } else {
-#pragma unroll
-                    for (int t = 0; t < NA; ++t)
-#pragma unroll
-                        for (int i = 0; i < V; ++i) cf[t][i] = T(0);
-                }
 #pragma unroll
                 for (int i = 0; i < V; ++i) {
                     const T c = ring[cmod(j - R, RING)][i];
@@ -223,16 +245,6 @@ __global__ void __launch_bounds__(32 * WY) plainv_kernel(const SweepArgs<T> a) {
                     res[i] = acc;
                 }
             } else {
-                T al[V];
-                if constexpr (KIND == W25_ALPHA) {
-                    if (own) {
-                        pv::ldg16<T>(al, a.W + zo);
-                    } else {
-#pragma unroll
-                        for (int i = 0; i < V; ++i) al[i] = T(0);
-                    }
-                }
-                (void)al;
                 const T wr[4] = {s1, s2, s3, s4};
 #pragma unroll
                 for (int i = 0; i < V; ++i) {
@@ -318,8 +330,10 @@ cudaError_t launch_plainv_kind(int kind, const SweepArgs<T> &a, int variant, cud
     const bool big = variant == 14;
     switch (kind) {
     case W25_CONST: return big ? launch_plainv<T, W25_CONST, 16>(a, st, num_sms) : launch_plainv<T, W25_CONST, 8>(a, st, num_sms);
-    case W25_VAR: return big ? launch_plainv<T, W25_VAR, 16>(a, st, num_sms) : launch_plainv<T, W25_VAR, 8>(a, st, num_sms);
-    case J25_VAR: return big ? launch_plainv<T, J25_VAR, 16>(a, st, num_sms) : launch_plainv<T, J25_VAR, 8>(a, st, num_sms);
+    // the 13-array kinds hold 13 coefficient vectors per thread: their second
+    // tile is 4 rows (more CTAs per SM) instead of 16
+    case W25_VAR: return big ? launch_plainv<T, W25_VAR, 4>(a, st, num_sms) : launch_plainv<T, W25_VAR, 8>(a, st, num_sms);
+    case J25_VAR: return big ? launch_plainv<T, J25_VAR, 4>(a, st, num_sms) : launch_plainv<T, J25_VAR, 8>(a, st, num_sms);
     case W25_ALPHA: return big ? launch_plainv<T, W25_ALPHA, 16>(a, st, num_sms) : launch_plainv<T, W25_ALPHA, 8>(a, st, num_sms);
     default: return cudaErrorNotSupported;
     }
