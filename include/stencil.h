@@ -105,7 +105,13 @@ enum stencil_option {
        (coefficients, u^{t-1}) staged asynchronously as well, 10..12 =
        register wavefront tiles of 64x32 (4 rows per thread), 64x32 (2 rows
        per thread) and 64x64 points (7-point kinds; the same tiles serve the
-       blocked passes of scheme 3; other kinds run the default plain tile). */
+       blocked passes of scheme 3), 13 and 14 = vectorised sweep of the
+       25-point kinds with 16-byte vectors along x, 8 and 16 rows per CTA
+       (4 rows for the 13-array kinds; needs nx a multiple of 4 in FP32, of
+       2 in FP64).  A variant a kind or geometry cannot use runs the default
+       streaming tile.  The default is the measured best: 10 / 11 for FP32
+       J7_CONST / J7_VAR, 13 for FP32 W25_CONST and W25_ALPHA, 14 for
+       W25_VAR and J25_VAR, else a streaming tile. */
     STENCIL_OPT_VARIANT = 5
 };
 
