@@ -298,10 +298,10 @@ cudaError_t plain_step(stencil_plan_s *p, bool adjoint, const Scalars &s, const 
     a.rcv_z = (int)rcv_z;
     a.trace = trace;
     a.inject = inject;
-    // the vectorised 25-point sweep (forward; the constant kind is its own adjoint)
-    if ((variant == 13 || variant == 14) && (!adjoint || p->kind == W25_CONST) &&
+    // the vectorised 25-point sweep (forward and adjoint)
+    if ((variant == 13 || variant == 14) &&
         (p->dtype == 1 ? plainv_supported_f32(p->kind, p->g) : plainv_supported_f64(p->kind, p->g)))
-        return launch_plainv_kind<T>(p->kind, a, variant, st, p->num_sms);
+        return launch_plainv_kind<T>(p->kind, adjoint, a, variant, st, p->num_sms);
     a.variant = variant < 10 ? variant : 0;  // 10+: register wavefront / vectorised tiles
     return launch_plain<T>(p->kind, adjoint, a, st, p->num_sms);
 }

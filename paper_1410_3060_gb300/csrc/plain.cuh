@@ -50,7 +50,8 @@ cudaError_t launch_axpby(double alpha, const T *x, double beta, const T *y, T *o
 bool plainv_supported_f32(int kind, const Geom &g);
 bool plainv_supported_f64(int kind, const Geom &g);
 template <typename T>
-cudaError_t launch_plainv_kind(int kind, const SweepArgs<T> &a, int variant, cudaStream_t st, int num_sms);
+cudaError_t launch_plainv_kind(int kind, bool adjoint, const SweepArgs<T> &a, int variant, cudaStream_t st,
+                               int num_sms);
 
 // FP64 / FP32 FMA throughput probe.
 cudaError_t run_fma_peak(int dtype, cudaStream_t st, double *flops, double *clock_hz);

@@ -5,6 +5,6 @@ namespace stc {
 
 bool plainv_supported_f32(int kind, const Geom &g) { return plainv_supported<float>(kind, g); }
 
-template cudaError_t launch_plainv_kind<float>(int, const SweepArgs<float> &, int, cudaStream_t, int);
+template cudaError_t launch_plainv_kind<float>(int, bool, const SweepArgs<float> &, int, cudaStream_t, int);
 
 }  // namespace stc

@@ -5,6 +5,6 @@ namespace stc {
 
 bool plainv_supported_f64(int kind, const Geom &g) { return plainv_supported<double>(kind, g); }
 
-template cudaError_t launch_plainv_kind<double>(int, const SweepArgs<double> &, int, cudaStream_t, int);
+template cudaError_t launch_plainv_kind<double>(int, bool, const SweepArgs<double> &, int, cudaStream_t, int);
 
 }  // namespace stc

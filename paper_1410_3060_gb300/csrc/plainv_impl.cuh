@@ -52,7 +52,7 @@ __device__ __forceinline__ void st16(T *p, const T (&s)[V16<T>::n]) {
     *reinterpret_cast<typename V16<T>::type *>(p) = v;
 }
 
-template <typename T, int KIND, int WY>
+template <typename T, int KIND, int WY, bool ADJ = false>
 struct Tile {
     static constexpr int R = KindTraits<KIND>::R;
     static constexpr int V = V16<T>::n;
@@ -63,7 +63,7 @@ struct Tile {
     // per-point inputs staged with the field plane: u^{t-1} (second-order
     // kinds) and a single coefficient array (alpha); 13-array kinds load
     // their coefficients directly
-    static constexpr int NPS = (KindTraits<KIND>::WAVE ? 1 : 0) + (KindTraits<KIND>::NARR == 1 ? 1 : 0);
+    static constexpr int NPS = (KindTraits<KIND>::WAVE ? 1 : 0) + ((KindTraits<KIND>::NARR == 1 && !ADJ) ? 1 : 0);
     static constexpr int PP = TX * TY;           // one per-point plane
     static constexpr size_t smem = sizeof(T) * ((size_t)NS * SP + (size_t)NS * NPS * PP);
     static constexpr int MINB = 1;
@@ -71,9 +71,13 @@ struct Tile {
 
 }  // namespace pv
 
-template <typename T, int KIND, int WY>
-__global__ void __launch_bounds__(32 * WY, pv::Tile<T, KIND, WY>::MINB) plainv_kernel(const SweepArgs<T> a) {
-    using TL = pv::Tile<T, KIND, WY>;
+// ADJ: the adjoint (transposed) sweep of a variable-coefficient kind: every
+// term's coefficient is read at its source point,
+// (A^T y)(q) = sum_k A_k(q - o_k) y(q - o_k); x-shifted coefficients come
+// from the three (FP32) or five (FP64) aligned vectors around the own one.
+template <typename T, int KIND, int WY, bool ADJ = false>
+__global__ void __launch_bounds__(32 * WY, pv::Tile<T, KIND, WY, ADJ>::MINB) plainv_kernel(const SweepArgs<T> a) {
+    using TL = pv::Tile<T, KIND, WY, ADJ>;
     constexpr int R = TL::R, V = TL::V;
     constexpr bool WAVE = KindTraits<KIND>::WAVE;
     constexpr int NA = KindTraits<KIND>::NARR;
@@ -141,7 +145,7 @@ __global__ void __launch_bounds__(32 * WY, pv::Tile<T, KIND, WY>::MINB) plainv_k
             T *dp = spp + slot * (NPS * PP) + pown;
             if constexpr (KindTraits<KIND>::WAVE)
                 cp_async_zfill<16>(dp, ok ? (const void *)(a.u_prev + zo) : (const void *)a.u, ok);
-            if constexpr (NA == 1)
+            if constexpr (NA == 1 && !ADJ)
                 cp_async_zfill<16>(dp + (NPS - 1) * PP, ok ? (const void *)(a.W + zo) : (const void *)a.u, ok);
         }
     };
@@ -173,7 +177,7 @@ __global__ void __launch_bounds__(32 * WY, pv::Tile<T, KIND, WY>::MINB) plainv_k
             // the wait so that their latency overlaps it
             T cf[NA > 1 ? NA : 1][V];
             (void)cf;
-            if constexpr (NA > 1) {
+            if constexpr (NA > 1 && !ADJ) {
                 if (own && z >= z0) {
 #pragma unroll
                     for (int t = 0; t < NA; ++t) pv::ldg16<T>(cf[t], a.W + t * g.nfield + zo);
@@ -191,7 +195,7 @@ __global__ void __launch_bounds__(32 * WY, pv::Tile<T, KIND, WY>::MINB) plainv_k
             T pvv[V], al[V];
             (void)pvv; (void)al;
             if constexpr (KindTraits<KIND>::WAVE) pv::ld16<T>(pvv, spp + slot * (NPS * PP) + pown);
-            if constexpr (NA == 1) pv::ld16<T>(al, spp + slot * (NPS * PP) + (NPS - 1) * PP + pown);
+            if constexpr (NA == 1 && !ADJ) pv::ld16<T>(al, spp + slot * (NPS * PP) + (NPS - 1) * PP + pown);
             {
                 int ns = slot + PD;
                 if (ns >= NS) ns -= NS;
@@ -229,7 +233,95 @@ __global__ void __launch_bounds__(32 * WY, pv::Tile<T, KIND, WY>::MINB) plainv_k
                 }
                 return ring[cmod(j - R, RING)][c];
             };
-            if constexpr (KIND == W25_VAR || KIND == J25_VAR) {
+            // adjoint: coefficient vector of array t at (dz planes, dy rows, dx
+            // columns) from the own vector; dx a multiple of V
+            auto cvec = [&](T (&d)[V], int t, int dz, int dy, int dx) {
+                if (own) {
+                    pv::ldg16<T>(d, a.W + t * g.nfield + zo + (int64_t)dz * sz + dy * sy + dx);
+                } else {
+#pragma unroll
+                    for (int i = 0; i < V; ++i) d[i] = T(0);
+                }
+            };
+            // x-shifted coefficients of array t: cl (R columns left), cm (own), cr (R right)
+            auto cx_load = [&](int t, T (&cl)[R / V][V], T (&cm)[V], T (&cr)[R / V][V]) {
+#pragma unroll
+                for (int m = 0; m < R / V; ++m) {
+                    cvec(cl[m], t, 0, 0, -(m + 1) * V);
+                    cvec(cr[m], t, 0, 0, (m + 1) * V);
+                }
+                cvec(cm, t, 0, 0, 0);
+            };
+            auto cx_at = [&](const T (&cl)[R / V][V], const T (&cm)[V], const T (&cr)[R / V][V], int c) -> T {
+                if (c < 0) return cl[(-c - 1) / V][V - 1 - ((-c - 1) % V)];
+                if (c >= V) return cr[(c - V) / V][(c - V) % V];
+                return cm[c];
+            };
+            (void)cvec; (void)cx_load; (void)cx_at;
+            if constexpr (ADJ && (KIND == W25_VAR || KIND == J25_VAR)) {
+                T c0v[V];
+                cvec(c0v, 0, 0, 0, 0);
+#pragma unroll
+                for (int i = 0; i < V; ++i) {
+                    const T c = ring[cmod(j - R, RING)][i];
+                    res[i] = c0v[i] * c;
+                    if constexpr (WAVE) res[i] = fma(T(2), c, res[i]) - pvv[i];
+                }
+#pragma unroll
+                for (int r = 0; r < 4; ++r) {
+                    const int d = r + 1;
+                    T cl[R / V][V], cm[V], cr[R / V][V], cyu[V], cyd[V], czd[V], czu[V];
+                    cx_load(3 * r + 1, cl, cm, cr);
+                    cvec(cyu, 3 * r + 2, 0, -d, 0);
+                    cvec(cyd, 3 * r + 2, 0, d, 0);
+                    cvec(czd, 3 * r + 3, -d, 0, 0);
+                    cvec(czu, 3 * r + 3, d, 0, 0);
+#pragma unroll
+                    for (int i = 0; i < V; ++i) {
+                        T acc = res[i];
+                        acc = fma(cx_at(cl, cm, cr, i - d), xval(i, -d), acc);
+                        acc = fma(cx_at(cl, cm, cr, i + d), xval(i, d), acc);
+                        acc = fma(cyu[i], yv[0][r][i], acc);
+                        acc = fma(cyd[i], yv[1][r][i], acc);
+                        acc = fma(czd[i], ring[cmod(j - R - d, RING)][i], acc);
+                        acc = fma(czu[i], ring[cmod(j - R + d, RING)][i], acc);
+                        res[i] = acc;
+                    }
+                }
+            } else if constexpr (ADJ) {  // W25_ALPHA: A^T y = L (alpha y) + 2y - y_prev
+                const T wr[4] = {s1, s2, s3, s4};
+                T a0[V];
+                cvec(a0, 0, 0, 0, 0);
+                T sacc[V];
+#pragma unroll
+                for (int i = 0; i < V; ++i) sacc[i] = s0 * (a0[i] * ring[cmod(j - R, RING)][i]);
+                T cl[R / V][V], cr[R / V][V];
+                cx_load(0, cl, a0, cr);
+#pragma unroll
+                for (int r = 0; r < 4; ++r) {
+                    const int d = r + 1;
+                    T ayu[V], ayd[V], azd[V], azu[V];
+                    cvec(ayu, 0, 0, -d, 0);
+                    cvec(ayd, 0, 0, d, 0);
+                    cvec(azd, 0, -d, 0, 0);
+                    cvec(azu, 0, d, 0, 0);
+#pragma unroll
+                    for (int i = 0; i < V; ++i) {
+                        T pr = cx_at(cl, a0, cr, i - d) * xval(i, -d);
+                        pr = fma(cx_at(cl, a0, cr, i + d), xval(i, d), pr);
+                        pr = fma(ayu[i], yv[0][r][i], pr);
+                        pr = fma(ayd[i], yv[1][r][i], pr);
+                        pr = fma(azd[i], ring[cmod(j - R - d, RING)][i], pr);
+                        pr = fma(azu[i], ring[cmod(j - R + d, RING)][i], pr);
+                        sacc[i] = fma(wr[r], pr, sacc[i]);
+                    }
+                }
+#pragma unroll
+                for (int i = 0; i < V; ++i) {
+                    const T c = ring[cmod(j - R, RING)][i];
+                    res[i] = sacc[i] + (T(2) * c - pvv[i]);
+                }
+            } else if constexpr (KIND == W25_VAR || KIND == J25_VAR) {
 #pragma unroll
                 for (int i = 0; i < V; ++i) {
                     const T c = ring[cmod(j - R, RING)][i];
@@ -295,11 +387,11 @@ inline bool plainv_supported(int kind, const Geom &g) {
     return kind_radius(kind) == 4 && g.nx % V == 0 && (int64_t)g.px * g.py < ((int64_t)1 << 30);
 }
 
-template <typename T, int KIND, int WY>
+template <typename T, int KIND, int WY, bool ADJ = false>
 cudaError_t launch_plainv(const SweepArgs<T> &a, cudaStream_t st, int num_sms) {
-    using TL = pv::Tile<T, KIND, WY>;
+    using TL = pv::Tile<T, KIND, WY, ADJ>;
     constexpr int R = TL::R;
-    auto kern = plainv_kernel<T, KIND, WY>;
+    auto kern = plainv_kernel<T, KIND, WY, ADJ>;
     static_assert(TL::smem <= 227 * 1024, "shared memory per CTA");
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TL::smem);
     if (e != cudaSuccess) return e;
@@ -326,8 +418,18 @@ cudaError_t launch_plainv(const SweepArgs<T> &a, cudaStream_t st, int num_sms) {
 }
 
 template <typename T>
-cudaError_t launch_plainv_kind(int kind, const SweepArgs<T> &a, int variant, cudaStream_t st, int num_sms) {
+cudaError_t launch_plainv_kind(int kind, bool adjoint, const SweepArgs<T> &a, int variant, cudaStream_t st,
+                               int num_sms) {
     const bool big = variant == 14;
+    if (adjoint) {  // variable kinds (the constant kind is self-adjoint: forward sweep below)
+        switch (kind) {
+        case W25_VAR: return big ? launch_plainv<T, W25_VAR, 4, true>(a, st, num_sms) : launch_plainv<T, W25_VAR, 8, true>(a, st, num_sms);
+        case J25_VAR: return big ? launch_plainv<T, J25_VAR, 4, true>(a, st, num_sms) : launch_plainv<T, J25_VAR, 8, true>(a, st, num_sms);
+        case W25_ALPHA: return big ? launch_plainv<T, W25_ALPHA, 4, true>(a, st, num_sms) : launch_plainv<T, W25_ALPHA, 8, true>(a, st, num_sms);
+        case W25_CONST: break;
+        default: return cudaErrorNotSupported;
+        }
+    }
     switch (kind) {
     case W25_CONST: return big ? launch_plainv<T, W25_CONST, 16>(a, st, num_sms) : launch_plainv<T, W25_CONST, 8>(a, st, num_sms);
     // the 13-array kinds hold 13 coefficient vectors per thread: their second
