@@ -104,134 +104,8 @@ __global__ void __launch_bounds__(256) grad_kernel(const GradArgs<T> a) {
     }
 }
 
-// Two-point variant for the 25-point kinds (nx even): each thread owns two
-// consecutive x points, so every load of u^n and lam^{n+1} is one 8-byte
-// (FP32) or 16-byte (FP64) vector and serves both points; the x neighbours
-// at distance 1..4 of the pair come from the five aligned vectors at column
-// offsets -4, -2, 0, 2, 4.  Summation exactly as grad_kernel.
-template <typename T> struct Pair;
-template <> struct Pair<float> { using type = float2; };
-template <> struct Pair<double> { using type = double2; };
-
-template <typename T>
-__device__ __forceinline__ void ld2(T (&d)[2], const T *p) {
-    const auto v = *reinterpret_cast<const typename Pair<T>::type *>(p);
-    d[0] = v.x;
-    d[1] = v.y;
-}
-
-template <typename T, int KIND>
-__global__ void __launch_bounds__(256) grad_kernel_pair(const GradArgs<T> a) {
-    constexpr int R = KindTraits<KIND>::R;
-    constexpr int NA = KindTraits<KIND>::NARR;
-    static_assert(R == 4, "25-point kinds");
-    const Geom g = a.g;
-    const int x = (blockIdx.x * 32 + threadIdx.x) * 2;
-    const int y = blockIdx.y * 8 + threadIdx.y;
-    const int z = blockIdx.z;
-    if (x >= g.nx || y >= g.ny) return;
-    const int64_t idx = (int64_t)(z + R) * g.sz + (int64_t)(y + R) * g.sy + (x + R);
-    const int64_t st3[3] = {1, g.sy, g.sz};
-    // terms of one step for both points: d[k][i]
-    auto terms = [&](int s, T (&d)[NA][2]) {
-        const T *u = a.u[s] + idx;
-        T l[2], c[2];
-        ld2<T>(l, a.lam[s] + idx);
-        ld2<T>(c, u);
-        T xv[5][2];   // columns -4..5 in pairs: offsets -4, -2, 0, 2, 4
-#pragma unroll
-        for (int m = 0; m < 5; ++m) {
-            if (m == 2) { xv[m][0] = c[0]; xv[m][1] = c[1]; }
-            else ld2<T>(xv[m], u + 2 * (m - 2));
-        }
-        auto ux = [&](int col) -> T { return xv[(col + 4) >> 1][(col + 4) & 1]; };
-        if constexpr (KIND == W25_ALPHA) {
-#pragma unroll
-            for (int i = 0; i < 2; ++i) d[0][i] = T(a.s.c[0]) * c[i];
-        } else {
-#pragma unroll
-            for (int i = 0; i < 2; ++i) d[0][i] = l[i] * c[i];
-        }
-#pragma unroll
-        for (int r = 1; r <= 4; ++r) {
-            T ym[2], yp[2], zm[2], zp[2];
-            ld2<T>(ym, u - r * st3[1]);
-            ld2<T>(yp, u + r * st3[1]);
-            ld2<T>(zm, u - r * st3[2]);
-            ld2<T>(zp, u + r * st3[2]);
-#pragma unroll
-            for (int i = 0; i < 2; ++i) {
-                const T px = ux(i - r) + ux(i + r), py = ym[i] + yp[i], pz = zm[i] + zp[i];
-                if constexpr (KIND == W25_ALPHA) {
-                    d[0][i] = fma(T(a.s.c[r]), (px + py) + pz, d[0][i]);
-                } else {
-                    d[3 * (r - 1) + 1][i] = l[i] * px;
-                    d[3 * (r - 1) + 2][i] = l[i] * py;
-                    d[3 * (r - 1) + 3][i] = l[i] * pz;
-                }
-            }
-        }
-        if constexpr (KIND == W25_ALPHA) {
-#pragma unroll
-            for (int i = 0; i < 2; ++i) d[0][i] = l[i] * d[0][i];
-        }
-    };
-    T d[NA][2];
-    if constexpr (sizeof(T) == 8) {
-        double acc[NA][2];
-#pragma unroll
-        for (int k = 0; k < NA; ++k) acc[k][0] = acc[k][1] = 0.0;
-        for (int s = 0; s < a.nsteps; ++s) {
-            terms(s, d);
-#pragma unroll
-            for (int k = 0; k < NA; ++k) { acc[k][0] += d[k][0]; acc[k][1] += d[k][1]; }
-        }
-#pragma unroll
-        for (int k = 0; k < NA; ++k) {
-            double2 *gp = reinterpret_cast<double2 *>(a.grad + (int64_t)k * g.nfield + idx);
-            double2 v = *gp;
-            v.x += acc[k][0];
-            v.y += acc[k][1];
-            *gp = v;
-        }
-    } else {
-        float sum[NA][2], cmp[NA][2];
-#pragma unroll
-        for (int k = 0; k < NA; ++k) sum[k][0] = sum[k][1] = cmp[k][0] = cmp[k][1] = 0.f;
-        for (int s = 0; s < a.nsteps; ++s) {
-            terms(s, d);
-#pragma unroll
-            for (int k = 0; k < NA; ++k)
-#pragma unroll
-                for (int i = 0; i < 2; ++i) {
-                    const float yk = __fsub_rn(d[k][i], cmp[k][i]);
-                    const float tk = __fadd_rn(sum[k][i], yk);
-                    cmp[k][i] = __fsub_rn(__fsub_rn(tk, sum[k][i]), yk);
-                    sum[k][i] = tk;
-                }
-        }
-#pragma unroll
-        for (int k = 0; k < NA; ++k) {
-            double2 *gp = reinterpret_cast<double2 *>(a.grad + (int64_t)k * g.nfield + idx);
-            double2 v = *gp;
-            v.x += (double)sum[k][0] - (double)cmp[k][0];
-            v.y += (double)sum[k][1] - (double)cmp[k][1];
-            *gp = v;
-        }
-    }
-}
-
 template <typename T>
 cudaError_t launch_grad(int kind, const GradArgs<T> &a, cudaStream_t st) {
-    if (kind_radius(kind) == 4 && a.g.nx % 2 == 0) {
-        dim3 block(32, 8, 1), grid((a.g.nx + 63) / 64, (a.g.ny + 7) / 8, a.g.nz);
-        switch (kind) {
-        case W25_VAR: grad_kernel_pair<T, W25_VAR><<<grid, block, 0, st>>>(a); return cudaGetLastError();
-        case J25_VAR: grad_kernel_pair<T, J25_VAR><<<grid, block, 0, st>>>(a); return cudaGetLastError();
-        case W25_ALPHA: grad_kernel_pair<T, W25_ALPHA><<<grid, block, 0, st>>>(a); return cudaGetLastError();
-        default: break;
-        }
-    }
     dim3 block(32, 8, 1), grid((a.g.nx + 31) / 32, (a.g.ny + 7) / 8, a.g.nz);
     switch (kind) {
     case J7_VAR: grad_kernel<T, J7_VAR><<<grid, block, 0, st>>>(a); break;
