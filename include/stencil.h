@@ -112,7 +112,15 @@ enum stencil_option {
        streaming tile.  The default is the measured best: 10 / 11 for FP32
        J7_CONST / J7_VAR, 13 for FP32 W25_CONST and W25_ALPHA, 14 for
        W25_VAR and J25_VAR, else a streaming tile. */
-    STENCIL_OPT_VARIANT = 5
+    STENCIL_OPT_VARIANT = 5,
+    /* 1: stencil_forward captures its pass program (every launch and copy of
+       the T steps) into a CUDA graph the first time it sees an argument set
+       (state pair, coefficients, T, trace, rcv_z and the tuning options) and
+       replays that graph on the caller's stream while the arguments stay
+       the same; a new argument set or any stencil_plan_set replaces the
+       graph.  Capture runs on a plan-owned stream, so the caller's stream
+       may be the legacy default stream.  0 (default): direct launches. */
+    STENCIL_OPT_GRAPH = 6
 };
 
 typedef struct stencil_plan_s *stencil_plan_t;

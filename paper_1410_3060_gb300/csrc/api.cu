@@ -184,6 +184,27 @@ struct stencil_plan_s {
     int ngring;
     double *partials;
     int npartials;
+    // CUDA graph of the forward pass program (STENCIL_OPT_GRAPH)
+    int graph;
+    cudaStream_t cap_stream;
+    cudaGraphExec_t gexec;
+    bool gvalid;
+    struct GraphKey {
+        void *up, *u, *trace;
+        const void *arrays;
+        double w[8];
+        int nw;
+        int64_t T, rcv_z;
+        int tb, scheme, variant;
+        bool operator==(const GraphKey &o) const {
+            if (up != o.up || u != o.u || trace != o.trace || arrays != o.arrays || nw != o.nw || T != o.T ||
+                rcv_z != o.rcv_z || tb != o.tb || scheme != o.scheme || variant != o.variant)
+                return false;
+            for (int i = 0; i < nw; ++i)
+                if (w[i] != o.w[i]) return false;
+            return true;
+        }
+    } gkey;
 };
 
 namespace {
@@ -517,6 +538,11 @@ void free_scratch(stencil_plan_s *p) {
 
 extern "C" {
 
+static void drop_graph(stencil_plan_s *p) {
+    if (p->gvalid) cudaGraphExecDestroy(p->gexec);
+    p->gvalid = false;
+}
+
 int stencil_plan(stencil_plan_t *plan, int kind, int64_t nx, int64_t ny, int64_t nz, int radius, int dtype) {
     if (!plan) return STENCIL_EINVAL;
     *plan = nullptr;
@@ -562,6 +588,7 @@ int stencil_plan(stencil_plan_t *plan, int kind, int64_t nx, int64_t ny, int64_t
 
 int stencil_plan_set(stencil_plan_t p, int option, int64_t value) {
     if (!p) return STENCIL_EINVAL;
+    drop_graph(p);   // any option may change the pass program or its scratch
     switch (option) {
     case STENCIL_OPT_TIME_BLOCK:
         if (value < 0 || value > 64) return STENCIL_EINVAL;
@@ -582,6 +609,10 @@ int stencil_plan_set(stencil_plan_t p, int option, int64_t value) {
         if (value < 1 || value > GRAD_MAX_STEPS) return STENCIL_EINVAL;
         p->grad_batch = (int)value;
         return ensure_gring(p);
+    case STENCIL_OPT_GRAPH:
+        if (value < 0 || value > 1) return STENCIL_EINVAL;
+        p->graph = (int)value;
+        return STENCIL_OK;
     default:
         return STENCIL_EINVAL;
     }
@@ -594,6 +625,7 @@ int stencil_plan_get(stencil_plan_t p, int option, int64_t *value) {
     case STENCIL_OPT_SCHEME: *value = plan_scheme(p); return STENCIL_OK;
     case STENCIL_OPT_GRAD_BATCH: *value = p->grad_batch; return STENCIL_OK;
     case STENCIL_OPT_VARIANT: *value = plan_variant(p); return STENCIL_OK;
+    case STENCIL_OPT_GRAPH: *value = p->graph; return STENCIL_OK;
     case STENCIL_OPT_SCRATCH_BYTES:
         *value = (int64_t)((p->scratch[0] ? 2 * p->field_bytes : 0) + (p->nbands + p->ngring) * p->field_bytes +
                            p->npartials * sizeof(double));
@@ -605,6 +637,8 @@ int stencil_plan_get(stencil_plan_t p, int option, int64_t *value) {
 void stencil_plan_destroy(stencil_plan_t p) {
     if (!p) return;
     cudaDeviceSynchronize();
+    drop_graph(p);
+    if (p->cap_stream) cudaStreamDestroy(p->cap_stream);
     free_scratch(p);
     delete p;
 }
@@ -624,11 +658,53 @@ int stencil_forward(stencil_plan_t p, void *u_prev, void *u, const stencil_coeff
     if ((st = check_coeffs(p, coeffs))) return st;
     if (trace && (rcv_z < 0 || rcv_z >= p->g.nz)) return STENCIL_EINVAL;
     if (T == 0) return STENCIL_OK;
-    if (p->dtype == STENCIL_F64)
-        return run_program<double>(p, u_prev, u, coeffs, T, (cudaStream_t)stream, false, trace, nullptr,
-                                   trace ? rcv_z : -1, nullptr, nullptr);
-    return run_program<float>(p, u_prev, u, coeffs, T, (cudaStream_t)stream, false, trace, nullptr,
-                              trace ? rcv_z : -1, nullptr, nullptr);
+    auto run = [&](cudaStream_t s) {
+        if (p->dtype == STENCIL_F64)
+            return run_program<double>(p, u_prev, u, coeffs, T, s, false, trace, nullptr, trace ? rcv_z : -1,
+                                       nullptr, nullptr);
+        return run_program<float>(p, u_prev, u, coeffs, T, s, false, trace, nullptr, trace ? rcv_z : -1, nullptr,
+                                  nullptr);
+    };
+    if (!p->graph) return run((cudaStream_t)stream);
+    // graph mode: the pass program of these arguments is captured once (on a
+    // plan-owned stream, so the caller's stream may be the legacy default
+    // stream) and replayed on the caller's stream
+    stencil_plan_s::GraphKey key;
+    memset(&key, 0, sizeof(key));
+    key.up = u_prev;
+    key.u = u;
+    key.trace = trace;
+    key.arrays = coeffs ? coeffs->arrays : nullptr;
+    key.nw = coeffs && coeffs->w ? std::min<int>(coeffs->nw, 8) : 0;
+    for (int i = 0; i < key.nw; ++i) key.w[i] = coeffs->w[i];
+    key.T = T;
+    key.rcv_z = trace ? rcv_z : -1;
+    key.tb = effective_time_block(p);
+    key.scheme = plan_scheme(p);
+    key.variant = plan_variant(p);
+    if (!p->gvalid || !(key == p->gkey)) {
+        drop_graph(p);
+        cudaError_t e = cudaSuccess;
+        if (!p->cap_stream) e = cudaStreamCreateWithFlags(&p->cap_stream, cudaStreamNonBlocking);
+        if (e != cudaSuccess) return cuda_fail(e);
+        e = cudaStreamBeginCapture(p->cap_stream, cudaStreamCaptureModeRelaxed);
+        if (e != cudaSuccess) return cuda_fail(e);
+        const int r = run(p->cap_stream);
+        cudaGraph_t graph = nullptr;
+        e = cudaStreamEndCapture(p->cap_stream, &graph);
+        if (r != STENCIL_OK) {
+            if (graph) cudaGraphDestroy(graph);
+            return r;
+        }
+        if (e != cudaSuccess) return cuda_fail(e);
+        e = cudaGraphInstantiate(&p->gexec, graph, 0);
+        cudaGraphDestroy(graph);
+        if (e != cudaSuccess) return cuda_fail(e);
+        p->gvalid = true;
+        p->gkey = key;
+    }
+    cudaError_t e = cudaGraphLaunch(p->gexec, (cudaStream_t)stream);
+    return e == cudaSuccess ? STENCIL_OK : cuda_fail(e);
 }
 
 int stencil_adjoint(stencil_plan_t p, void *lam_next, void *lam, const stencil_coeffs_t *coeffs, int64_t T,

@@ -16,7 +16,7 @@ from . import build as _build
 
 J7_CONST, J7_VAR, W25_CONST, W25_VAR, J25_VAR, W25_ALPHA = 1, 2, 3, 4, 5, 6
 F64, F32 = 0, 1
-OPT_TIME_BLOCK, OPT_SCHEME, OPT_SCRATCH_BYTES, OPT_GRAD_BATCH, OPT_VARIANT = 1, 2, 3, 4, 5
+OPT_TIME_BLOCK, OPT_SCHEME, OPT_SCRATCH_BYTES, OPT_GRAD_BATCH, OPT_VARIANT, OPT_GRAPH = 1, 2, 3, 4, 5, 6
 RADIUS = {J7_CONST: 1, J7_VAR: 1, W25_CONST: 4, W25_VAR: 4, J25_VAR: 4, W25_ALPHA: 4}
 NUM_ARRAYS = {J7_CONST: 0, J7_VAR: 7, W25_CONST: 0, W25_VAR: 13, J25_VAR: 13, W25_ALPHA: 1}
 NUM_WEIGHTS = {J7_CONST: 2, J7_VAR: 0, W25_CONST: 6, W25_VAR: 0, J25_VAR: 0, W25_ALPHA: 5}
