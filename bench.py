@@ -52,6 +52,7 @@ def parse():
     p.add_argument("--scheme", type=int, default=None,
                    help="1 overlapped tiles, 2 diamond tiles in y, 3 register wavefront")
     p.add_argument("--variant", type=int, default=None, help="plain forward tile variant (0 = default)")
+    p.add_argument("--graph", action="store_true", help="replay the captured CUDA graph of the pass program")
     p.add_argument("--sweep", action="store_true", help="time every tile variant and block depth, one line each")
     p.add_argument("--sweep-kinds", default="j7_const,j7_var,w25_const,w25_var",
                    help="comma-separated kinds of the tuning sweep")
@@ -217,7 +218,7 @@ def job_rate(units_per_rank, ws, ms_max):
 
 
 def forward_case(torch, st, wl, kind, n, T, dtype, steps, warmup, ws, stream, time_block=None, e2e=False,
-                 wk=None, scheme=None, variant=None):
+                 wk=None, scheme=None, variant=None, graph=False):
     """Time `steps` calls of stencil_forward(T) on the workload; returns dict."""
     tdt = torch.float64 if dtype == st.F64 else torch.float32
     if wk is None:
@@ -229,6 +230,8 @@ def forward_case(torch, st, wl, kind, n, T, dtype, steps, warmup, ws, stream, ti
         plan.set(st.OPT_SCHEME, scheme)
     if variant is not None:
         plan.set(st.OPT_VARIANT, variant)
+    if graph:
+        plan.set(st.OPT_GRAPH, 1)
     b = plan.get(st.OPT_TIME_BLOCK)
     up = torch.from_numpy(wk.u_prev).to("cuda", tdt)
     u = torch.from_numpy(wk.u).to("cuda", tdt)
@@ -427,7 +430,7 @@ def run_ours(args):
     with sampler:
         main, _ = forward_case(torch, st, wl, kind, n, T, dtype, args.steps, args.warmup, ws, stream,
                                time_block=args.time_block, e2e=not args.no_e2e, wk=wk, scheme=args.scheme,
-                               variant=args.variant)
+                               variant=args.variant, graph=args.graph)
     clocks = sampler.summary()
     roofline = roofline_of(pm, kind, args.dtype, n, main, peak_f64, hbm_peak, peak_f32)
     tr = MEASURED_TRAFFIC.get((args.kind, args.dtype, main["time_block"], main["variant"]))

@@ -161,3 +161,27 @@ def test_wavefront_odd_row_falls_back(st):
     op, ou, _ = oracle.forward(1, wk.u_prev, wk.u, wk.w, wk.W, T, threads=8)
     _, gu, _ = gpu_forward(st.Plan, wk, F32, time_block=2, scheme=3, variant=10, expect_block=1)
     assert normwise_err(gu, ou) <= fp32_bound(1, T, 1)
+
+
+@pytest.mark.parametrize("kind,dtype", [(1, F32), (3, F32)])
+def test_tune_forward_picks_a_valid_configuration(st, kind, dtype):
+    """Run-time tuning times every candidate on copies of the caller's state,
+    leaves the caller's state untouched, and the tuned plan still matches the
+    oracle."""
+    import torch
+    from paper_1410_3060_gb300 import tune
+    from gpu_util import to_dev, to_np
+    shape, T = (80, 48, 40), 4
+    wk = wl.make(kind, shape, T, seed=6)
+    plan = st.Plan(kind, *shape, dtype)
+    up, u = to_dev(wk.u_prev, dtype), to_dev(wk.u, dtype)
+    W = to_dev(wk.W, dtype) if wk.W is not None else None
+    res = tune.tune_forward(plan, up, u, wk.w, W, T=T, reps=1)
+    assert len(res["table"]) >= 10
+    assert plan.get(1) == res["time_block"]
+    np.testing.assert_array_equal(to_np(u), wk.u.astype(np.float32))   # caller's state untouched
+    op, ou, _ = oracle.forward(kind, wk.u_prev, wk.u, wk.w, wk.W, T, threads=8)
+    plan.forward(up, u, wk.w, W, T)
+    torch.cuda.synchronize()
+    assert normwise_err(to_np(u), ou) <= fp32_bound(kind, T, wk.R)
+    plan.close()
