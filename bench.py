@@ -306,8 +306,14 @@ def roofline_of(pm, kind, dtype_name, n, res, peak_f64, hbm_peak, fp32_peak):
            "frac": bytes_pass / t_pass / 1e9 / hbm_peak}
     if dtype_name == "f64":
         ach = flops_pass / t_pass / 1e12
+        # the FP64 pipe executes one add, multiply or FMA per lane-slot: the
+        # instruction view counts adds as full pipe slots (flops count them
+        # as half an FMA)
+        instr = pm.FP_INSTR_PER_LUP[kind] * pts * b / t_pass
+        pipe = {"fp64_instr_per_update": pm.FP_INSTR_PER_LUP[kind], "achieved_ginstr_s": instr / 1e9,
+                "peak_ginstr_s": peak_f64 / 2 / 1e9, "frac": instr / (peak_f64 / 2)}
         return {"bound": "alu", "achieved": ach, "peak": peak_f64 / 1e12, "unit": "TFLOP/s",
-                "frac": ach / (peak_f64 / 1e12), "traffic": None, "hbm_view": hbm}
+                "frac": ach / (peak_f64 / 1e12), "traffic": None, "hbm_view": hbm, "fp64_pipe_view": pipe}
     return {"bound": "hbm", "achieved": hbm["achieved_gbs"], "peak": hbm_peak, "unit": "GB/s",
             "frac": hbm["frac"], "traffic": None,
             "alu_view": {"achieved_tflops": flops_pass / t_pass / 1e12, "peak_tflops": fp32_peak / 1e12}}
