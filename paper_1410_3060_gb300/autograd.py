@@ -10,7 +10,9 @@ the library blocks the kind), keeping the state pair at every checkpoint
 and the residual.
 
 Backward, segment by segment from the last: stencil_forward_states
-recomputes the K states of the segment from its checkpoint, then
+recomputes the K states of the segment from its checkpoint (on a second
+stream, one segment ahead, into the other of two state-buffer sets, so that
+the recompute of segment i-1 overlaps the adjoint of segment i), then
 stencil_adjoint runs the transposed sweep backward over the segment,
 injecting the residual on the receiver plane and accumulating the
 coefficient gradients in FP64 (batched over steps).  The top segment starts
@@ -55,7 +57,7 @@ class MisfitRunner:
     """
 
     def __init__(self, kind, n, T, K, rcv_z, dtype=st.F32, w=None, grad_batch=16, time_block=None,
-                 device="cuda"):
+                 device="cuda", overlap=True):
         self.kind, self.n, self.T, self.K, self.rcv_z, self.w = kind, tuple(n), int(T), int(K), int(rcv_z), w
         self.plan = st.Plan(kind, *n, dtype)
         if time_block is not None:
@@ -75,10 +77,14 @@ class MisfitRunner:
         self._loss = new(1, dt=torch.float64)
         self._lam = (new(*shape), new(*shape))
         self._grad = new(st.NUM_ARRAYS[kind], *shape, dt=torch.float64)
-        self._bufs = [new(*shape) for _ in range(self.K)]
+        self.overlap = bool(overlap)
+        self._sets = [[new(*shape) for _ in range(self.K)] for _ in range(2 if self.overlap else 1)]
+        self._bufs = self._sets[0]
         self._du0 = new(*shape)
-        for b in self._bufs:
-            st.fill_zero(b)   # zero halos (only interiors are ever written)
+        for bs in self._sets:
+            for b in bs:
+                st.fill_zero(b)   # zero halos (only interiors are ever written)
+        self._side = torch.cuda.Stream(device=device) if self.overlap else None
 
     def close(self):
         self.plan.close()
@@ -125,12 +131,40 @@ class MisfitRunner:
         grad = self._grad
         for t_ in (lam_next, lam, grad):
             st.fill_zero(t_)
-        bufs = self._bufs
-        top = True
-        for c, cp, cu in reversed(state["ckpts"]):
+        segs = list(reversed(state["ckpts"]))
+        main = torch.cuda.current_stream()
+        nsets = len(self._sets)
+        rec_ev, adj_ev = [None] * nsets, [None] * nsets
+
+        def recompute(i, stream):
+            # u^{c+1} .. u^{c+k} of segment i into buffer set i mod nsets
+            c, cp, cu = segs[i]
             k = min(K, T - c)
-            # u^{c+1} .. u^{c+k} into bufs[0..k-1]
-            plan.forward_states(cp, cu, self.w, W, bufs[:k])
+            plan.forward_states(cp, cu, self.w, W, self._sets[i % nsets][:k], stream=stream)
+
+        if self.overlap:
+            self._side.wait_stream(main)          # checkpoints, residual and cleared buffers are ready
+            with torch.cuda.stream(self._side):
+                recompute(0, self._side)
+                rec_ev[0] = self._side.record_event()
+        top = True
+        for i, (c, cp, cu) in enumerate(segs):
+            k = min(K, T - c)
+            if self.overlap:
+                if i + 1 < len(segs):
+                    # the next segment's states go into the set the adjoint of
+                    # segment i - 1 read: wait for it, then recompute alongside
+                    # this segment's adjoint
+                    j = (i + 1) % nsets
+                    with torch.cuda.stream(self._side):
+                        if adj_ev[j] is not None:
+                            self._side.wait_event(adj_ev[j])
+                        recompute(i + 1, self._side)
+                        rec_ev[j] = self._side.record_event()
+                main.wait_event(rec_ev[i % nsets])
+            else:
+                recompute(i, main)
+            bufs = self._sets[i % nsets]
             states = [cu] + bufs[:k - 1]
             if top:
                 # start at level T+1 with (lam^{T+2}, lam^{T+1}) = 0: one extra step forms lam^T = g^T
@@ -141,6 +175,8 @@ class MisfitRunner:
             else:
                 plan.adjoint(lam_next, lam, self.w, W, k, fwd_states=states, residual=res[c:c + k],
                              rcv_z=self.rcv_z, grad=grad)
+            if self.overlap:
+                adj_ev[i % nsets] = main.record_event()
         du0 = self._du0
         if st.SECOND_ORDER[self.kind]:
             plan.axpby(1.0, lam, -1.0, lam_next, du0)

@@ -211,7 +211,7 @@ namespace {
 
 // FP32 7-point plans whose geometry the register wavefront serves default
 // to it (measured fastest on GB300 at 512^3: depth 3 with 64x32 tiles of
-// 4 rows per thread for the constant kind, depth 2 with 2 rows per thread
+// 4 rows per thread for the constant kind, depth 4 with 2 rows per thread
 // for the variable kind); all other plans to the shared-memory kernels.
 bool wavefront_default(const stencil_plan_s *p) {
     return p->dtype == 1 && (p->kind == J7_CONST || p->kind == J7_VAR) &&
@@ -241,7 +241,7 @@ int plan_variant(const stencil_plan_s *p) {
 }
 
 int default_time_block(const stencil_plan_s *p) {
-    if (plan_scheme(p) == 3 && wavefront_default(p)) return p->kind == J7_CONST ? 3 : 2;
+    if (plan_scheme(p) == 3 && wavefront_default(p)) return p->kind == J7_CONST ? 3 : 4;
     return blocked_default_levels(p->kind, p->dtype);
 }
 

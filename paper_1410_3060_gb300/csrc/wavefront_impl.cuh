@@ -265,6 +265,28 @@ __global__ void __launch_bounds__(32 * WY) wavefront_kernel(const BlockedArgs<T>
             constexpr int j = decltype(jj)::value;
             const int q = qb + j;
             if (q >= qe) return;
+            // variable kind: level 1's coefficients (plane q - R, first touch
+            // from HBM) are issued before the wait and the barrier so that
+            // their latency overlaps them
+            T cf1[NA > 0 ? NR : 1][NA > 0 ? NA : 1][V];
+            (void)cf1;
+            if constexpr (NA > 0) {
+                const T *cb = a.W + (int64_t)(q - R + R) * sz;
+                const bool zin = q - R >= 0 && q - R < g.nz;
+#pragma unroll
+                for (int jr = 0; jr < NR; ++jr) {
+                    if (zin && ((lmask >> jr) & 1u)) {
+                        const int o = off0 + jr * sy;
+#pragma unroll
+                        for (int t = 0; t < NA; ++t) vld_g<T, V>(cf1[jr][t], cb + t * g.nfield + o);
+                    } else {
+#pragma unroll
+                        for (int t = 0; t < NA; ++t)
+#pragma unroll
+                            for (int i = 0; i < V; ++i) cf1[jr][t][i] = T(0);
+                    }
+                }
+            }
             // level-0 plane q: this thread's own points
             cp_async_wait<PD - 1>();
             {
@@ -320,7 +342,12 @@ __global__ void __launch_bounds__(32 * WY) wavefront_kernel(const BlockedArgs<T>
                     for (int jr = 0; jr < NR; ++jr) {
                         T cf[NA > 0 ? NA : 1][V];
                         (void)cf;
-                        if constexpr (NA > 0) {
+                        if constexpr (NA > 0 && k == 1) {
+#pragma unroll
+                            for (int t = 0; t < NA; ++t)
+#pragma unroll
+                                for (int i = 0; i < V; ++i) cf[t][i] = cf1[jr][t][i];
+                        } else if constexpr (NA > 0) {
                             if ((lmask >> jr) & 1u) {
                                 const int o = off0 + jr * sy;
 #pragma unroll
