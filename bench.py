@@ -319,7 +319,7 @@ def roofline_of(pm, kind, dtype_name, n, res, peak_f64, hbm_peak, fp32_peak):
             "alu_view": {"achieved_tflops": flops_pass / t_pass / 1e12, "peak_tflops": fp32_peak / 1e12}}
 
 
-def fwd_adj_case(torch, st, wl, n, T, K, dtype, steps, warmup, ws, stream, fw=None):
+def fwd_adj_case(torch, st, wl, n, T, K, dtype, steps, warmup, ws, stream, fw=None, variant=None):
     """Differentiable 25-point variable wave workload: one step = the
     checkpointed forward (T steps, state pair kept every K steps, receiver
     trace, FP64 misfit) plus the backward (recompute of every segment and the
@@ -332,6 +332,8 @@ def fwd_adj_case(torch, st, wl, n, T, K, dtype, steps, warmup, ws, stream, fw=No
         fw = wl.fwi(n, T=T, K=K, seed=0)
     nx, ny, nz = fw.n
     run = MisfitRunner(wl.W25_VAR, fw.n, T, K, fw.rcv_z, dtype=dtype)
+    if variant is not None:
+        run.plan.set(st.OPT_VARIANT, variant)
     u0 = torch.from_numpy(fw.u0).to("cuda", tdt)
     W = torch.from_numpy(fw.W).to("cuda", tdt)
     Wt = torch.from_numpy(fw.W_true).to("cuda", tdt)
@@ -427,7 +429,8 @@ def run_ours(args):
         run_sweep(args, torch, st, wl, pm, stream, ws, peak_f64, hbm_peak, peak_f32)
         return
     if args.fwd_adj:
-        r, _ = fwd_adj_case(torch, st, wl, n, T, 20, dtype, args.steps, args.warmup, ws, stream)
+        r, _ = fwd_adj_case(torch, st, wl, n, T, 20, dtype, args.steps, args.warmup, ws, stream,
+                            variant=args.variant)
         print(json.dumps({"fwd_adj": r}), flush=True)
         return
     dev_index = torch.cuda.current_device()
