@@ -94,8 +94,11 @@ enum stencil_option {
     STENCIL_OPT_SCRATCH_BYTES = 3,
     /* Adjoint steps whose coefficient-gradient terms are summed in FP64
        registers before one read-modify-write of the gradient arrays
-       (1..16, default 1).  G > 1 makes the plan hold G + 2 state fields of
-       scratch in which stencil_adjoint keeps the adjoint levels of a batch. */
+       (1..16, default 1).  G > 1 makes the plan hold 2G + 2 state fields of
+       scratch in which stencil_adjoint keeps the adjoint levels of two
+       batches: the gradient of one batch runs on a plan-owned stream while
+       the sweeps of the next batch run on the caller's stream (the call
+       still returns with all of its work ordered on the caller's stream). */
     STENCIL_OPT_GRAD_BATCH = 4,
     /* Tile variant of the plain forward sweep (the tuning parameter of the
        one-level kernel): 0 = measured default for the kind and dtype,

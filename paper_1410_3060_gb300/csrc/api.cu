@@ -180,7 +180,9 @@ struct stencil_plan_s {
     int nbands;
     int variant;      // forward sweep tile variant (0 = default)
     int grad_batch;   // adjoint steps per FP64 gradient update
-    void *gring[GRAD_MAX_STEPS + 2];  // adjoint levels of one gradient batch
+    void *gring[2 * GRAD_MAX_STEPS + 2];  // adjoint levels of two gradient batches
+    cudaStream_t grad_stream;         // gradient batches run here, overlapping the next batch's sweeps
+    cudaEvent_t ev_sweeps, ev_grad[2];
     int ngring;
     double *partials;
     int npartials;
@@ -433,7 +435,12 @@ template <typename T>
 int run_adjoint_ring(stencil_plan_s *p, void *lam_next, void *lam, const stencil_coeffs_t *coeffs, int64_t nsteps,
                      cudaStream_t st, const void *inject, int64_t rcv_z, const void *const *fwd_states,
                      double *grad) {
-    const int G = p->grad_batch, NSL = G + 2;
+    // The adjoint levels live in a ring of 2G + 2 plan fields: the gradient
+    // of batch b (levels bG .. bG+G-1) runs on the plan's gradient stream
+    // while the sweeps of batch b+1 (which write levels up to (b+2)G) run on
+    // the caller's stream; the sweeps of batch b+2 wait for it.  Gradient
+    // batches stay in order on their stream (they update the same arrays).
+    const int G = p->grad_batch, NSL = 2 * G + 2;
     const Scalars s = fold_scalars(p->kind, coeffs);
     const int64_t plane = (int64_t)p->g.nx * p->g.ny;
     auto level = [&](int64_t j) -> void * {  // buffer holding lam^{m-j}
@@ -441,6 +448,13 @@ int run_adjoint_ring(stencil_plan_s *p, void *lam_next, void *lam, const stencil
         if (j == 0) return lam;
         return p->gring[(j - 1) % NSL];
     };
+    cudaError_t e = cudaSuccess;
+    if (!p->grad_stream) {
+        e = cudaStreamCreateWithFlags(&p->grad_stream, cudaStreamNonBlocking);
+        if (e == cudaSuccess) e = cudaEventCreateWithFlags(&p->ev_sweeps, cudaEventDisableTiming);
+        for (int i = 0; i < 2 && e == cudaSuccess; ++i) e = cudaEventCreateWithFlags(&p->ev_grad[i], cudaEventDisableTiming);
+        if (e != cudaSuccess) return cuda_fail(e);
+    }
     GradArgs<T> ga;
     memset(&ga, 0, sizeof(ga));
     ga.grad = grad;
@@ -448,22 +462,37 @@ int run_adjoint_ring(stencil_plan_s *p, void *lam_next, void *lam, const stencil
     if (p->kind == W25_ALPHA)
         for (int r = 0; r <= 4; ++r) ga.s.c[r] = coeffs->w[r];
     ga.g = p->g;
+    int64_t batch = 0;   // batches launched
     for (int64_t j = 1; j <= nsteps; ++j) {
+        // first sweep of batch b >= 2 overwrites the levels batch b-2's gradient reads
+        if ((j - 1) % G == 0 && batch >= 2) {
+            e = cudaStreamWaitEvent(st, p->ev_grad[batch % 2], 0);
+            if (e != cudaSuccess) return cuda_fail(e);
+        }
         const T *inj = inject ? (const T *)inject + (nsteps - j) * plane : nullptr;
-        cudaError_t e = plain_step<T>(p, true, s, coeffs, level(j - 2), level(j - 1), level(j), nullptr, inj,
-                                      rcv_z, st);
+        e = plain_step<T>(p, true, s, coeffs, level(j - 2), level(j - 1), level(j), nullptr, inj, rcv_z, st);
         if (e != cudaSuccess) return cuda_fail(e);
         ga.u[ga.nsteps] = (const T *)fwd_states[nsteps - j];
         ga.lam[ga.nsteps] = (const T *)level(j - 1);
         ++ga.nsteps;
         if (ga.nsteps == G || j == nsteps) {
-            e = launch_grad<T>(p->kind, ga, st);
+            // the gradient stream starts this batch once its sweeps (and all
+            // earlier work of the caller's stream) are done
+            e = cudaEventRecord(p->ev_sweeps, st);
+            if (e == cudaSuccess) e = cudaStreamWaitEvent(p->grad_stream, p->ev_sweeps, 0);
+            if (e == cudaSuccess) e = launch_grad<T>(p->kind, ga, p->grad_stream);
+            if (e == cudaSuccess) e = cudaEventRecord(p->ev_grad[batch % 2], p->grad_stream);
             if (e != cudaSuccess) return cuda_fail(e);
+            ++batch;
             ga.nsteps = 0;
         }
     }
+    // the caller's stream continues after every gradient batch
+    if (batch > 0) {
+        e = cudaStreamWaitEvent(st, p->ev_grad[(batch - 1) % 2], 0);
+        if (e != cudaSuccess) return cuda_fail(e);
+    }
     // final pair (lam^{m-T+1}, lam^{m-T}) back into the caller's buffers
-    cudaError_t e = cudaSuccess;
     if (level(nsteps - 1) != lam_next)
         e = cudaMemcpyAsync(lam_next, level(nsteps - 1), p->field_bytes, cudaMemcpyDeviceToDevice, st);
     if (e == cudaSuccess) e = cudaMemcpyAsync(lam, level(nsteps), p->field_bytes, cudaMemcpyDeviceToDevice, st);
@@ -498,7 +527,7 @@ int ensure_bands(stencil_plan_s *p) {
 }
 
 void free_gring(stencil_plan_s *p) {
-    for (int i = 0; i < GRAD_MAX_STEPS + 2; ++i) {
+    for (int i = 0; i < 2 * GRAD_MAX_STEPS + 2; ++i) {
         if (p->gring[i]) cudaFree(p->gring[i]);
         p->gring[i] = nullptr;
     }
@@ -506,7 +535,7 @@ void free_gring(stencil_plan_s *p) {
 }
 
 int ensure_gring(stencil_plan_s *p) {
-    const int need = p->grad_batch > 1 ? p->grad_batch + 2 : 0;
+    const int need = p->grad_batch > 1 ? 2 * p->grad_batch + 2 : 0;
     if (need <= p->ngring) return STENCIL_OK;
     free_gring(p);
     for (int i = 0; i < need; ++i) {
@@ -639,6 +668,12 @@ void stencil_plan_destroy(stencil_plan_t p) {
     cudaDeviceSynchronize();
     drop_graph(p);
     if (p->cap_stream) cudaStreamDestroy(p->cap_stream);
+    if (p->grad_stream) {
+        cudaStreamDestroy(p->grad_stream);
+        cudaEventDestroy(p->ev_sweeps);
+        cudaEventDestroy(p->ev_grad[0]);
+        cudaEventDestroy(p->ev_grad[1]);
+    }
     free_scratch(p);
     delete p;
 }
