@@ -474,13 +474,12 @@ plain_stream_kernel(const SweepArgs<T> a) {
                     zn[d - 1][0] = ring[cmod(j - R - d, RING)][jr];
                     zn[d - 1][1] = ring[cmod(j - R + d, RING)][jr];
                 }
-                constexpr int CO = WAVE ? 1 : 0;
+                constexpr int CO = WAVE ? 1 : 0;   // per-point input index of the first coefficient
+                (void)CO;
                 const T pv = WAVE ? pin[0][jr] : T(0);
                 (void)pv;
                 T v;
                 if constexpr (ADJ && KIND == J7_VAR) {
-                    const T *q = &pin[CO][0];
-                    (void)q;
                     v = pin[CO + 0][jr] * c;
                     v = fma(pin[CO + 1][jr], xn[0][1], v);
                     v = fma(pin[CO + 2][jr], xn[0][0], v);
