@@ -111,8 +111,9 @@ enum stencil_option {
        blocked passes of scheme 3), 13 and 14 = vectorised sweep of the
        25-point kinds with 16-byte vectors along x, 8 and 16 rows per CTA
        (4 rows for the 13-array kinds; needs nx a multiple of 4 in FP32, of
-       2 in FP64).  A variant a kind or geometry cannot use runs the default
-       streaming tile.  The default is the measured best: 10 / 11 for FP32
+       2 in FP64), 15 and 16 = the same tiles staged by TMA (one tensor copy
+       per plane tile, mbarrier completion).  A variant a kind or geometry
+       cannot use runs the default streaming tile.  The default is the measured best: 10 / 11 for FP32
        J7_CONST / J7_VAR, 13 for FP32 W25_CONST and W25_ALPHA, 14 for
        W25_VAR and J25_VAR, else a streaming tile. */
     STENCIL_OPT_VARIANT = 5,
@@ -274,6 +275,12 @@ const char *stencil_strerror(int status);
 /* The last CUDA error code recorded by a call that returned STENCIL_ECUDA
  * in this thread (cudaError_t as int), or 0. */
 int stencil_last_cuda_error(void);
+
+/* Number of bounded device waits (the TMA-staged sweeps' waits for their
+ * plane copies) that gave up since the library was loaded, on the current
+ * device, into *count; such a wait ends its thread instead of hanging.  0
+ * on a healthy run.  Synchronises the device. */
+int stencil_wait_timeouts(int64_t *count);
 
 #ifdef __cplusplus
 }

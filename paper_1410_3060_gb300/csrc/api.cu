@@ -322,7 +322,7 @@ cudaError_t plain_step(stencil_plan_s *p, bool adjoint, const Scalars &s, const 
     a.trace = trace;
     a.inject = inject;
     // the vectorised 25-point sweep (forward and adjoint)
-    if ((variant == 13 || variant == 14) &&
+    if (variant >= 13 && variant <= 16 &&
         (p->dtype == 1 ? plainv_supported_f32(p->kind, p->g) : plainv_supported_f64(p->kind, p->g)))
         return launch_plainv_kind<T>(p->kind, adjoint, a, variant, st, p->num_sms);
     a.variant = variant < 10 ? variant : 0;  // 10+: register wavefront / vectorised tiles
@@ -631,7 +631,7 @@ int stencil_plan_set(stencil_plan_t p, int option, int64_t value) {
         p->scheme = (int)value;
         return ensure_bands(p);
     case STENCIL_OPT_VARIANT:
-        if (value < 0 || value > 14) return STENCIL_EINVAL;
+        if (value < 0 || value > 16) return STENCIL_EINVAL;
         p->variant = (int)value;
         return STENCIL_OK;
     case STENCIL_OPT_GRAD_BATCH:
@@ -878,5 +878,13 @@ const char *stencil_strerror(int status) {
 }
 
 int stencil_last_cuda_error(void) { return g_last_cuda_error; }
+
+int stencil_wait_timeouts(int64_t *count) {
+    if (!count) return STENCIL_EINVAL;
+    cudaError_t e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) return cuda_fail(e);
+    *count = (int64_t)plainv_timeouts_f32() + (int64_t)plainv_timeouts_f64();
+    return STENCIL_OK;
+}
 
 }  // extern "C"

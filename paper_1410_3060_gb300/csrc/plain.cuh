@@ -45,10 +45,13 @@ cudaError_t launch_axpby(double alpha, const T *x, double beta, const T *y, T *o
 
 // Vectorised plain sweep of the 25-point kinds (plainv_impl.cuh): tile
 // variant 13 = 8 rows per CTA, 14 = 16 rows per CTA (4 for the 13-array
-// kinds).  Served when the kind
+// kinds); 15 and 16 the same tiles staged by TMA.  Served when the kind
 // has radius 4 and nx is a multiple of the vector width (4 FP32, 2 FP64).
 bool plainv_supported_f32(int kind, const Geom &g);
 bool plainv_supported_f64(int kind, const Geom &g);
+// bounded waits of the TMA-staged sweeps that gave up (device counters)
+unsigned int plainv_timeouts_f32();
+unsigned int plainv_timeouts_f64();
 template <typename T>
 cudaError_t launch_plainv_kind(int kind, bool adjoint, const SweepArgs<T> &a, int variant, cudaStream_t st,
                                int num_sms);

@@ -12,7 +12,18 @@
 // by 2R+1 so ring slots are registers); u^{t-1} and the coefficients of the
 // thread's points are 16-byte global loads.  Compared with the one-point-per-
 // thread kernels every address, copy and load serves V points.
+//
+// TMA staging (template flag TMA): one thread issues each plane tile (and the
+// per-point planes) as a single cp.async.bulk.tensor copy described by a
+// tensor map, completing on a per-slot mbarrier that every thread waits on
+// (bounded: a wait that gives up counts a timeout and ends the thread); the
+// tensor unit zero-fills everything outside the padded array.  The copy then
+// costs no per-thread instructions.
 #pragma once
+#include <cuda.h>
+#include <cudaTypedefs.h>
+#include <string.h>
+
 #include "plain.cuh"
 
 namespace stc {
@@ -65,18 +76,64 @@ struct Tile {
     // their coefficients directly
     static constexpr int NPS = (KindTraits<KIND>::WAVE ? 1 : 0) + ((KindTraits<KIND>::NARR == 1 && !ADJ) ? 1 : 0);
     static constexpr int PP = TX * TY;           // one per-point plane
-    static constexpr size_t smem = sizeof(T) * ((size_t)NS * SP + (size_t)NS * NPS * PP);
+    static constexpr size_t smem = sizeof(T) * ((size_t)NS * SP + (size_t)NS * NPS * PP) + 8 * NS + 128;
+    static_assert((sizeof(T) * SP) % 128 == 0 && (sizeof(T) * PP) % 128 == 0, "128-byte aligned slots");
     static constexpr int MINB = 1;
 };
 
+// ---- TMA / mbarrier helpers (inline PTX)
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_init_fence() {
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+// 3D tile copy global -> shared, completing on `bar`; coordinates are
+// elements (x innermost); x * element size must be a multiple of 16 bytes
+__device__ __forceinline__ void tma_load_3d(void *dst, const CUtensorMap *map, int x, int y, int z, uint64_t *bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], "
+        "[%5];\n" ::"r"(smem_u32(dst)),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(z), "r"(smem_u32(bar))
+        : "memory");
+}
+// wait for phase `parity` of `bar`; false when the bounded wait gives up
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity) {
+    const uint32_t b = smem_u32(bar);
+    for (int it = 0; it < (1 << 22); ++it) {
+        uint32_t ok;
+        asm volatile(
+            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+            : "=r"(ok)
+            : "r"(b), "r"(parity)
+            : "memory");
+        if (ok) return true;
+    }
+    return false;
+}
+
 }  // namespace pv
+
+// Waits that gave up (a counter per translation unit; read through
+// plainv_timeouts_f32 / _f64).
+static __device__ unsigned int g_wait_timeouts;
 
 // ADJ: the adjoint (transposed) sweep of a variable-coefficient kind: every
 // term's coefficient is read at its source point,
 // (A^T y)(q) = sum_k A_k(q - o_k) y(q - o_k); x-shifted coefficients come
 // from the three (FP32) or five (FP64) aligned vectors around the own one.
-template <typename T, int KIND, int WY, bool ADJ = false>
-__global__ void __launch_bounds__(32 * WY, pv::Tile<T, KIND, WY, ADJ>::MINB) plainv_kernel(const SweepArgs<T> a) {
+template <typename T, int KIND, int WY, bool ADJ = false, bool TMA = false>
+__global__ void __launch_bounds__(32 * WY, pv::Tile<T, KIND, WY, ADJ>::MINB)
+plainv_kernel(const SweepArgs<T> a, const __grid_constant__ CUtensorMap tm_u,
+              const __grid_constant__ CUtensorMap tm_p, const __grid_constant__ CUtensorMap tm_a) {
     using TL = pv::Tile<T, KIND, WY, ADJ>;
     constexpr int R = TL::R, V = TL::V;
     constexpr bool WAVE = KindTraits<KIND>::WAVE;
@@ -92,9 +149,13 @@ __global__ void __launch_bounds__(32 * WY, pv::Tile<T, KIND, WY, ADJ>::MINB) pla
     static_assert(NC <= 32, "copy mask");
 
     constexpr int NPS = TL::NPS, PP = TL::PP;
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    T *const sb = reinterpret_cast<T *>(smem_raw);
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    // slots start on 128-byte boundaries (TMA destinations); the launch adds
+    // 128 bytes for this round-up
+    T *const sb = reinterpret_cast<T *>((reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
     T *const spp = sb + NS * SP;                 // [NS][NPS][TY][TX]
+    uint64_t *const bars = reinterpret_cast<uint64_t *>(spp + NS * NPS * PP);   // TMA: one per slot
+    (void)bars; (void)tm_u; (void)tm_p; (void)tm_a;
 
     const Geom &g = a.g;
     const int lane = threadIdx.x, w = threadIdx.y, tid = w * 32 + lane;
@@ -127,6 +188,19 @@ __global__ void __launch_bounds__(32 * WY, pv::Tile<T, KIND, WY, ADJ>::MINB) pla
     // field plane q (tile and halo) and the per-point inputs of output plane
     // q - R into slot `slot`
     auto issue = [&](int q, int slot) {
+        if constexpr (TMA) {
+            // thread 0: the tile with its halo, and the per-point planes of
+            // output plane q - R (outside the padded array: zero fill)
+            if (tid == 0) {
+                pv::mbar_expect_tx(&bars[slot], (uint32_t)(sizeof(T) * (SP + NPS * PP)));
+                pv::tma_load_3d(sb + slot * SP, &tm_u, x0, y0, q + R, &bars[slot]);
+                if constexpr (KindTraits<KIND>::WAVE)
+                    pv::tma_load_3d(spp + slot * (NPS * PP), &tm_p, x0 + R, y0 + R, q, &bars[slot]);
+                if constexpr (NA == 1 && !ADJ)
+                    pv::tma_load_3d(spp + slot * (NPS * PP) + (NPS - 1) * PP, &tm_a, x0 + R, y0 + R, q, &bars[slot]);
+            }
+            return;
+        }
         const bool zm = q >= -R && q < g.nz + R;
         const T *pb = a.u + (zm ? (int64_t)(q + R) * sz : 0);
         T *d = sb + slot * SP;
@@ -156,10 +230,15 @@ __global__ void __launch_bounds__(32 * WY, pv::Tile<T, KIND, WY, ADJ>::MINB) pla
 #pragma unroll
         for (int i = 0; i < V; ++i) ring[s][i] = T(0);
 
+    if constexpr (TMA) {
+        if (tid < NS) pv::mbar_init(&bars[tid], 1);
+        pv::mbar_init_fence();
+        __syncthreads();
+    }
 #pragma unroll
     for (int s = 0; s < PD; ++s) {
         if (qs + s < qe) issue(qs + s, s);
-        cp_async_commit();
+        if constexpr (!TMA) cp_async_commit();
     }
     const T s0 = T(a.s.c[0]), s1 = T(a.s.c[1]), s2 = T(a.s.c[2]);
     const T s3 = T(a.s.c[3]), s4 = T(a.s.c[4]);
@@ -188,7 +267,15 @@ __global__ void __launch_bounds__(32 * WY, pv::Tile<T, KIND, WY, ADJ>::MINB) pla
                         for (int i = 0; i < V; ++i) cf[t][i] = T(0);
                 }
             }
-            cp_async_wait<PD - 1>();
+            if constexpr (TMA) {
+                // k-th use of a slot completes phase k (parity k & 1)
+                if (!pv::mbar_wait(&bars[slot], (uint32_t)(((q - qs) / NS) & 1))) {
+                    atomicAdd(&g_wait_timeouts, 1u);
+                    return;
+                }
+            } else {
+                cp_async_wait<PD - 1>();
+            }
             __syncthreads();
             pv::ld16<T>(ring[j], sb + slot * SP + scen);
             // staged per-point inputs of output plane z
@@ -200,7 +287,7 @@ __global__ void __launch_bounds__(32 * WY, pv::Tile<T, KIND, WY, ADJ>::MINB) pla
                 int ns = slot + PD;
                 if (ns >= NS) ns -= NS;
                 if (q + PD < qe) issue(q + PD, ns);
-                cp_async_commit();
+                if constexpr (!TMA) cp_async_commit();
             }
             int zslot = slot - R;
             if (zslot < 0) zslot += NS;
@@ -377,7 +464,7 @@ __global__ void __launch_bounds__(32 * WY, pv::Tile<T, KIND, WY, ADJ>::MINB) pla
             }
         });
     }
-    cp_async_wait<0>();
+    if constexpr (!TMA) cp_async_wait<0>();
 }
 
 // Whether the vectorised sweep serves this kind and geometry.
@@ -387,11 +474,47 @@ inline bool plainv_supported(int kind, const Geom &g) {
     return kind_radius(kind) == 4 && g.nx % V == 0 && (int64_t)g.px * g.py < ((int64_t)1 << 30);
 }
 
-template <typename T, int KIND, int WY, bool ADJ = false>
+namespace pv {
+// Tensor map of one padded field (3D: x fastest) with a box of bx x by x 1
+// elements; the tensor unit fills zeros outside the array.  The encoder is
+// the driver's, looked up through the runtime (no link against the driver
+// library).
+inline cudaError_t make_tmap(CUtensorMap *m, const void *base, int elem_bytes, const Geom &g, int bx, int by) {
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    if (!fn) {
+        void *f = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        cudaError_t e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q);
+        if (e != cudaSuccess || q != cudaDriverEntryPointSuccess || !f) return e != cudaSuccess ? e : cudaErrorNotSupported;
+        fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(f);
+    }
+    const cuuint64_t dims[3] = {(cuuint64_t)g.px, (cuuint64_t)g.py, (cuuint64_t)g.pz};
+    const cuuint64_t strides[2] = {(cuuint64_t)g.px * elem_bytes, (cuuint64_t)g.px * g.py * elem_bytes};
+    const cuuint32_t box[3] = {(cuuint32_t)bx, (cuuint32_t)by, 1};
+    const cuuint32_t es[3] = {1, 1, 1};
+    const CUresult r = fn(m, elem_bytes == 4 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 3,
+                          const_cast<void *>(base), dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                          CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                          CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
+}  // namespace pv
+
+template <typename T, int KIND, int WY, bool ADJ = false, bool TMA = false>
 cudaError_t launch_plainv(const SweepArgs<T> &a, cudaStream_t st, int num_sms) {
     using TL = pv::Tile<T, KIND, WY, ADJ>;
     constexpr int R = TL::R;
-    auto kern = plainv_kernel<T, KIND, WY, ADJ>;
+    auto kern = plainv_kernel<T, KIND, WY, ADJ, TMA>;
+    CUtensorMap tm_u, tm_p, tm_a;
+    memset(&tm_u, 0, sizeof(tm_u));
+    memset(&tm_p, 0, sizeof(tm_p));
+    memset(&tm_a, 0, sizeof(tm_a));
+    if constexpr (TMA) {
+        cudaError_t e = pv::make_tmap(&tm_u, a.u, sizeof(T), a.g, TL::SW, TL::SH);
+        if (e == cudaSuccess && KindTraits<KIND>::WAVE) e = pv::make_tmap(&tm_p, a.u_prev, sizeof(T), a.g, TL::TX, TL::TY);
+        if (e == cudaSuccess && KindTraits<KIND>::NARR == 1 && !ADJ) e = pv::make_tmap(&tm_a, a.W, sizeof(T), a.g, TL::TX, TL::TY);
+        if (e != cudaSuccess) return e;
+    }
     static_assert(TL::smem <= 227 * 1024, "shared memory per CTA");
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TL::smem);
     if (e != cudaSuccess) return e;
@@ -413,36 +536,51 @@ cudaError_t launch_plainv(const SweepArgs<T> &a, cudaStream_t st, int num_sms) {
     SweepArgs<T> b = a;
     b.zchunk = (a.g.nz + best - 1) / best;
     dim3 grid(gx, gy, (a.g.nz + b.zchunk - 1) / b.zchunk), block(32, WY, 1);
-    kern<<<grid, block, TL::smem, st>>>(b);
+    kern<<<grid, block, TL::smem, st>>>(b, tm_u, tm_p, tm_a);
     return cudaGetLastError();
 }
 
-template <typename T>
-cudaError_t launch_plainv_kind(int kind, bool adjoint, const SweepArgs<T> &a, int variant, cudaStream_t st,
-                               int num_sms) {
-    const bool big = variant == 14;
+template <typename T, bool TMA>
+cudaError_t launch_plainv_kind_t(int kind, bool adjoint, const SweepArgs<T> &a, bool big, cudaStream_t st,
+                                 int num_sms) {
     if (adjoint) {  // variable kinds (the constant kind is self-adjoint: forward sweep below)
         // the 13-array adjoint runs 8-row tiles for both variants: its
         // source-point coefficients reach 4 rows up and down, which 8-row
         // tiles keep in L1 more often (measured: 142.7 vs 150.2 ms for the
         // 256^3 forward+adjoint backward pass)
         switch (kind) {
-        case W25_VAR: return launch_plainv<T, W25_VAR, 8, true>(a, st, num_sms);
-        case J25_VAR: return launch_plainv<T, J25_VAR, 8, true>(a, st, num_sms);
-        case W25_ALPHA: return big ? launch_plainv<T, W25_ALPHA, 4, true>(a, st, num_sms) : launch_plainv<T, W25_ALPHA, 8, true>(a, st, num_sms);
+        case W25_VAR: return launch_plainv<T, W25_VAR, 8, true, TMA>(a, st, num_sms);
+        case J25_VAR: return launch_plainv<T, J25_VAR, 8, true, TMA>(a, st, num_sms);
+        case W25_ALPHA: return big ? launch_plainv<T, W25_ALPHA, 4, true, TMA>(a, st, num_sms) : launch_plainv<T, W25_ALPHA, 8, true, TMA>(a, st, num_sms);
         case W25_CONST: break;
         default: return cudaErrorNotSupported;
         }
     }
     switch (kind) {
-    case W25_CONST: return big ? launch_plainv<T, W25_CONST, 16>(a, st, num_sms) : launch_plainv<T, W25_CONST, 8>(a, st, num_sms);
+    case W25_CONST: return big ? launch_plainv<T, W25_CONST, 16, false, TMA>(a, st, num_sms) : launch_plainv<T, W25_CONST, 8, false, TMA>(a, st, num_sms);
     // the 13-array kinds hold 13 coefficient vectors per thread: their second
     // tile is 4 rows (more CTAs per SM) instead of 16
-    case W25_VAR: return big ? launch_plainv<T, W25_VAR, 4>(a, st, num_sms) : launch_plainv<T, W25_VAR, 8>(a, st, num_sms);
-    case J25_VAR: return big ? launch_plainv<T, J25_VAR, 4>(a, st, num_sms) : launch_plainv<T, J25_VAR, 8>(a, st, num_sms);
-    case W25_ALPHA: return big ? launch_plainv<T, W25_ALPHA, 16>(a, st, num_sms) : launch_plainv<T, W25_ALPHA, 8>(a, st, num_sms);
+    case W25_VAR: return big ? launch_plainv<T, W25_VAR, 4, false, TMA>(a, st, num_sms) : launch_plainv<T, W25_VAR, 8, false, TMA>(a, st, num_sms);
+    case J25_VAR: return big ? launch_plainv<T, J25_VAR, 4, false, TMA>(a, st, num_sms) : launch_plainv<T, J25_VAR, 8, false, TMA>(a, st, num_sms);
+    case W25_ALPHA: return big ? launch_plainv<T, W25_ALPHA, 16, false, TMA>(a, st, num_sms) : launch_plainv<T, W25_ALPHA, 8, false, TMA>(a, st, num_sms);
     default: return cudaErrorNotSupported;
     }
+}
+
+// Variants 13 / 14: cp.async staging; 15 / 16: the same tiles with TMA staging.
+template <typename T>
+cudaError_t launch_plainv_kind(int kind, bool adjoint, const SweepArgs<T> &a, int variant, cudaStream_t st,
+                               int num_sms) {
+    const bool big = variant == 14 || variant == 16;
+    if (variant >= 15) return launch_plainv_kind_t<T, true>(kind, adjoint, a, big, st, num_sms);
+    return launch_plainv_kind_t<T, false>(kind, adjoint, a, big, st, num_sms);
+}
+
+// Waits of this translation unit's kernels that gave up.
+inline unsigned int plainv_read_timeouts() {
+    unsigned int v = 0;
+    cudaMemcpyFromSymbol(&v, g_wait_timeouts, sizeof(v));
+    return v;
 }
 
 }  // namespace stc

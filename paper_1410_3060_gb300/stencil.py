@@ -27,7 +27,7 @@ SECOND_ORDER = {J7_CONST: False, J7_VAR: False, W25_CONST: True, W25_VAR: True, 
 EXPORTED = ("stencil_plan", "stencil_plan_set", "stencil_plan_get", "stencil_plan_destroy",
             "stencil_forward", "stencil_forward_states", "stencil_adjoint", "stencil_axpby",
             "stencil_misfit", "stencil_misfit_static", "stencil_fill_zero", "stencil_schedule", "stencil_fma_peak",
-            "stencil_strerror", "stencil_last_cuda_error")
+            "stencil_strerror", "stencil_last_cuda_error", "stencil_wait_timeouts")
 MISFIT_STATIC_MAX_ELEMS = 8192 * 2048
 
 _lock = threading.Lock()
@@ -82,10 +82,11 @@ def lib():
             L.stencil_strerror.argtypes = [i32]
             L.stencil_strerror.restype = ctypes.c_char_p
             L.stencil_last_cuda_error.argtypes = []
+            L.stencil_wait_timeouts.argtypes = [ctypes.POINTER(i64)]
             for fn in ("stencil_plan", "stencil_plan_set", "stencil_plan_get", "stencil_forward",
                        "stencil_forward_states", "stencil_adjoint", "stencil_axpby", "stencil_misfit",
                        "stencil_misfit_static", "stencil_fill_zero",
-                       "stencil_schedule", "stencil_fma_peak", "stencil_last_cuda_error"):
+                       "stencil_schedule", "stencil_fma_peak", "stencil_last_cuda_error", "stencil_wait_timeouts"):
                 getattr(L, fn).restype = i32
             _lib = L
     return _lib
@@ -144,6 +145,13 @@ def fma_peak(dtype: int, stream=None):
     _check("stencil_fma_peak", lib().stencil_fma_peak(dtype, _stream_handle(stream), ctypes.byref(f),
                                                       ctypes.byref(c)))
     return f.value, c.value
+
+
+def wait_timeouts() -> int:
+    """stencil_wait_timeouts: bounded device waits that gave up (0 when healthy)."""
+    n = ctypes.c_int64(0)
+    _check("stencil_wait_timeouts", lib().stencil_wait_timeouts(ctypes.byref(n)))
+    return n.value
 
 
 class Plan:
