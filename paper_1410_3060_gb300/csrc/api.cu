@@ -226,18 +226,19 @@ int plan_scheme(const stencil_plan_s *p) {
 }
 
 // Default tile variant: the register wavefront tiles for FP32 7-point plans,
-// the vectorised 25-point sweep where the geometry allows it (measured at
-// 512^3: FP32 W25_CONST 391 vs 274 GLUP/s, W25_VAR 103 vs 76; FP64 W25_VAR
-// 20.6 vs 18.6; FP64 W25_CONST is FP64-bound either way and keeps the
-// streaming kernel), else the streaming-kernel default.
+// the TMA-staged vectorised 25-point sweep where the geometry allows it
+// (measured at 512^3: FP32 W25_CONST 402 vs 274 GLUP/s for the best
+// streaming tile, W25_VAR 105 vs 76; FP64 W25_VAR 20.6 vs 18.6; FP64
+// W25_CONST is FP64-bound either way and keeps the streaming kernel), else
+// the streaming-kernel default.
 int plan_variant(const stencil_plan_s *p) {
     if (p->variant) return p->variant;
     if (wavefront_default(p)) return p->kind == J7_CONST ? 10 : 11;
     const bool vec = p->dtype == 1 ? plainv_supported_f32(p->kind, p->g) : plainv_supported_f64(p->kind, p->g);
     if (vec) {
         const bool arrays13 = p->kind == W25_VAR || p->kind == J25_VAR;
-        if (arrays13) return 14;
-        if (p->dtype == 1) return 13;
+        if (arrays13) return 16;
+        if (p->dtype == 1) return 15;
     }
     return default_variant(p->kind, p->dtype);
 }
