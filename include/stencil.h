@@ -114,7 +114,7 @@ enum stencil_option {
        2 in FP64), 15 and 16 = the same tiles staged by TMA (one tensor copy
        per plane tile, mbarrier completion).  A variant a kind or geometry
        cannot use runs the default streaming tile.  The default is the measured best: 10 / 11 for FP32
-       J7_CONST / J7_VAR, 13 for FP32 W25_CONST and W25_ALPHA, 14 for
+       J7_CONST / J7_VAR, 15 for FP32 W25_CONST and W25_ALPHA, 16 for
        W25_VAR and J25_VAR, else a streaming tile. */
     STENCIL_OPT_VARIANT = 5,
     /* 1: stencil_forward captures its pass program (every launch and copy of
