@@ -384,7 +384,7 @@ def run_sweep(args, torch, st, wl, pm, stream, ws, peak_f64, hbm_peak, peak_f32)
         wk = wl.make(kind, n, T, seed=0) if kind != wl.J7_VAR else wl.j7_var(n, T, seed=0)
         r1 = wl.RADIUS[kind] == 1
         for dtype in dtypes:
-            for v in (1, 2, 3, 4, 5, 6, 7, 8, 9) + ((10, 11, 12) if r1 else (13, 14, 15, 16)):
+            for v in (1, 2, 3, 4, 5, 6, 7, 8, 9) + ((10, 11, 12, 13, 14, 15, 16) if r1 else (13, 14, 15, 16)):
                 r, _ = forward_case(torch, st, wl, kind, n, T, dtype, args.steps, 1, ws, stream, time_block=1,
                                     wk=wk, variant=v)
                 r["roofline"] = roofline_of(pm, kind, r["dtype"], n, r, peak_f64, hbm_peak, peak_f32)

@@ -323,7 +323,7 @@ cudaError_t plain_step(stencil_plan_s *p, bool adjoint, const Scalars &s, const 
     a.trace = trace;
     a.inject = inject;
     // the vectorised 25-point sweep (forward and adjoint)
-    if (variant >= 13 && variant <= 16 &&
+    if (variant >= 13 && variant <= 16 && (!adjoint || kind_radius(p->kind) == 4) &&
         (p->dtype == 1 ? plainv_supported_f32(p->kind, p->g) : plainv_supported_f64(p->kind, p->g)))
         return launch_plainv_kind<T>(p->kind, adjoint, a, variant, st, p->num_sms);
     a.variant = variant < 10 ? variant : 0;  // 10+: register wavefront / vectorised tiles

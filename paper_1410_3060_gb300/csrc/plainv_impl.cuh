@@ -68,7 +68,10 @@ struct Tile {
     static constexpr int R = KindTraits<KIND>::R;
     static constexpr int V = V16<T>::n;
     static constexpr int TX = 32 * V, TY = WY;
-    static constexpr int SW = TX + 2 * R, SH = TY + 2 * R, SP = SW * SH;
+    static constexpr int RH = (R + V - 1) / V * V;   // halo columns, whole vectors
+    static constexpr int OS = R - R % V;             // own columns of tile bx start at bx TX + OS (aligned)
+    static constexpr int SW = TX + 2 * RH, SH = TY + 2 * R, SP0 = SW * SH;
+    static constexpr int SP = (int)((SP0 * sizeof(T) + 127) / 128 * 128 / sizeof(T));   // slot stride
     static constexpr int PD = 2;                 // planes in flight
     static constexpr int NS = R + 1 + PD;        // shared plane slots
     // per-point inputs staged with the field plane: u^{t-1} (second-order
@@ -138,10 +141,11 @@ plainv_kernel(const SweepArgs<T> a, const __grid_constant__ CUtensorMap tm_u,
     constexpr int R = TL::R, V = TL::V;
     constexpr bool WAVE = KindTraits<KIND>::WAVE;
     constexpr int NA = KindTraits<KIND>::NARR;
-    static_assert(R % V == 0, "neighbour vectors aligned");
+    constexpr int RH = TL::RH, OS = TL::OS, SP0 = TL::SP0;
     constexpr int RING = 2 * R + 1;
     constexpr int PD = TL::PD, NS = TL::NS;
     constexpr int TX = TL::TX, TY = TL::TY, SW = TL::SW, SH = TL::SH, SP = TL::SP;
+    static_assert(R % V == 0 || (R == 1 && KIND == J7_CONST) || (R == 1 && KIND == J7_VAR), "aligned own vectors");
     constexpr int VPR = SW / V;                  // vectors per shared row
     constexpr int NVEC = VPR * SH;               // vectors per plane
     constexpr int NT = 32 * WY;
@@ -159,7 +163,8 @@ plainv_kernel(const SweepArgs<T> a, const __grid_constant__ CUtensorMap tm_u,
 
     const Geom &g = a.g;
     const int lane = threadIdx.x, w = threadIdx.y, tid = w * 32 + lane;
-    const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;   // padded origin of the shared tile
+    const int xo = blockIdx.x * TX + OS;                      // padded column of the tile's first own point
+    const int x0 = xo - RH, y0 = blockIdx.y * TY;            // padded origin of the shared tile
     const int z0 = blockIdx.z * a.zchunk;
     const int z1 = min(z0 + a.zchunk, g.nz);
     const int qs = z0 - R, qe = z1 + R;
@@ -176,14 +181,21 @@ plainv_kernel(const SweepArgs<T> a, const __grid_constant__ CUtensorMap tm_u,
         const int gx = x0 + vc * V, gy = y0 + row;
         goff[c] = gy * sy + gx;
         soff[c] = row * SW + vc * V;
-        if (v < NVEC && gx < g.px && gy < g.py) cmask |= 1u << c;
+        if (v < NVEC && gx >= 0 && gx < g.px && gy < g.py) cmask |= 1u << c;
         if (v >= NVEC) soff[c] = 0;
     }
-    // this thread's points: padded row y0 + R + w, columns x0 + R + lane V ..
-    const int px = x0 + R + lane * V, py = y0 + R + w;
-    const bool own = px < g.nx + R && py < g.ny + R;   // nx % V == 0: whole vector in or out
+    // this thread's points: padded row y0 + R + w, columns xo + lane V ..
+    const int px = xo + lane * V, py = y0 + R + w;
+    bool cin[V];
+    bool call = py < g.ny + R, own = false;   // own: any point of the vector is interior
+#pragma unroll
+    for (int i = 0; i < V; ++i) {
+        cin[i] = py < g.ny + R && px + i >= R && px + i < g.nx + R;
+        call = call && cin[i];
+        own = own || cin[i];
+    }
     const int poff = py * sy + px;
-    const int scen = (R + w) * SW + R + lane * V;      // shared offset of the own vector
+    const int scen = (R + w) * SW + RH + lane * V;     // shared offset of the own vector
     const int pown = w * TX + lane * V;                // offset in a per-point plane
     // field plane q (tile and halo) and the per-point inputs of output plane
     // q - R into slot `slot`
@@ -192,12 +204,12 @@ plainv_kernel(const SweepArgs<T> a, const __grid_constant__ CUtensorMap tm_u,
             // thread 0: the tile with its halo, and the per-point planes of
             // output plane q - R (outside the padded array: zero fill)
             if (tid == 0) {
-                pv::mbar_expect_tx(&bars[slot], (uint32_t)(sizeof(T) * (SP + NPS * PP)));
+                pv::mbar_expect_tx(&bars[slot], (uint32_t)(sizeof(T) * (SP0 + NPS * PP)));
                 pv::tma_load_3d(sb + slot * SP, &tm_u, x0, y0, q + R, &bars[slot]);
                 if constexpr (KindTraits<KIND>::WAVE)
-                    pv::tma_load_3d(spp + slot * (NPS * PP), &tm_p, x0 + R, y0 + R, q, &bars[slot]);
+                    pv::tma_load_3d(spp + slot * (NPS * PP), &tm_p, xo, y0 + R, q, &bars[slot]);
                 if constexpr (NA == 1 && !ADJ)
-                    pv::tma_load_3d(spp + slot * (NPS * PP) + (NPS - 1) * PP, &tm_a, x0 + R, y0 + R, q, &bars[slot]);
+                    pv::tma_load_3d(spp + slot * (NPS * PP) + (NPS - 1) * PP, &tm_a, xo, y0 + R, q, &bars[slot]);
             }
             return;
         }
@@ -295,9 +307,9 @@ plainv_kernel(const SweepArgs<T> a, const __grid_constant__ CUtensorMap tm_u,
             if (z < z0) return;
             // centre plane z: in-plane neighbours from shared memory
             const T *sc = sb + zslot * SP + scen;
-            T lv[R / V][V], rv[R / V][V];   // the R columns left and right of the own vector
+            T lv[RH / V][V], rv[RH / V][V];   // the RH columns left and right of the own vector
 #pragma unroll
-            for (int m = 0; m < R / V; ++m) {
+            for (int m = 0; m < RH / V; ++m) {
                 pv::ld16<T>(lv[m], sc - (m + 1) * V);   // columns -V(m+1) .. -V m - 1
                 pv::ld16<T>(rv[m], sc + (m + 1) * V);   // columns V(m+1) .. V(m+2) - 1
             }
@@ -331,15 +343,15 @@ plainv_kernel(const SweepArgs<T> a, const __grid_constant__ CUtensorMap tm_u,
                 }
             };
             // x-shifted coefficients of array t: cl (R columns left), cm (own), cr (R right)
-            auto cx_load = [&](int t, T (&cl)[R / V][V], T (&cm)[V], T (&cr)[R / V][V]) {
+            auto cx_load = [&](int t, T (&cl)[RH / V][V], T (&cm)[V], T (&cr)[RH / V][V]) {
 #pragma unroll
-                for (int m = 0; m < R / V; ++m) {
+                for (int m = 0; m < RH / V; ++m) {
                     cvec(cl[m], t, 0, 0, -(m + 1) * V);
                     cvec(cr[m], t, 0, 0, (m + 1) * V);
                 }
                 cvec(cm, t, 0, 0, 0);
             };
-            auto cx_at = [&](const T (&cl)[R / V][V], const T (&cm)[V], const T (&cr)[R / V][V], int c) -> T {
+            auto cx_at = [&](const T (&cl)[RH / V][V], const T (&cm)[V], const T (&cr)[RH / V][V], int c) -> T {
                 if (c < 0) return cl[(-c - 1) / V][V - 1 - ((-c - 1) % V)];
                 if (c >= V) return cr[(c - V) / V][(c - V) % V];
                 return cm[c];
@@ -357,7 +369,7 @@ plainv_kernel(const SweepArgs<T> a, const __grid_constant__ CUtensorMap tm_u,
 #pragma unroll
                 for (int r = 0; r < 4; ++r) {
                     const int d = r + 1;
-                    T cl[R / V][V], cm[V], cr[R / V][V], cyu[V], cyd[V], czd[V], czu[V];
+                    T cl[RH / V][V], cm[V], cr[RH / V][V], cyu[V], cyd[V], czd[V], czu[V];
                     cx_load(3 * r + 1, cl, cm, cr);
                     cvec(cyu, 3 * r + 2, 0, -d, 0);
                     cvec(cyd, 3 * r + 2, 0, d, 0);
@@ -382,7 +394,7 @@ plainv_kernel(const SweepArgs<T> a, const __grid_constant__ CUtensorMap tm_u,
                 T sacc[V];
 #pragma unroll
                 for (int i = 0; i < V; ++i) sacc[i] = s0 * (a0[i] * ring[cmod(j - R, RING)][i]);
-                T cl[R / V][V], cr[R / V][V];
+                T cl[RH / V][V], cr[RH / V][V];
                 cx_load(0, cl, a0, cr);
 #pragma unroll
                 for (int r = 0; r < 4; ++r) {
@@ -407,6 +419,27 @@ plainv_kernel(const SweepArgs<T> a, const __grid_constant__ CUtensorMap tm_u,
                 for (int i = 0; i < V; ++i) {
                     const T c = ring[cmod(j - R, RING)][i];
                     res[i] = sacc[i] + (T(2) * c - pvv[i]);
+                }
+            } else if constexpr (KIND == J7_CONST) {
+                // Fig. 1b, the plain sweep's expression
+#pragma unroll
+                for (int i = 0; i < V; ++i) {
+                    const T c = ring[cmod(j - R, RING)][i];
+                    res[i] = s0 * c + s1 * (((xval(i, -1) + xval(i, 1)) + (yv[0][0][i] + yv[1][0][i])) +
+                                            (ring[cmod(j - R - 1, RING)][i] + ring[cmod(j - R + 1, RING)][i]));
+                }
+            } else if constexpr (KIND == J7_VAR) {
+                // Fig. 1c, the plain sweep's order of terms
+#pragma unroll
+                for (int i = 0; i < V; ++i) {
+                    T v = cf[0][i] * ring[cmod(j - R, RING)][i];
+                    v = fma(cf[1][i], xval(i, -1), v);
+                    v = fma(cf[2][i], xval(i, 1), v);
+                    v = fma(cf[3][i], yv[0][0][i], v);
+                    v = fma(cf[4][i], yv[1][0][i], v);
+                    v = fma(cf[5][i], ring[cmod(j - R - 1, RING)][i], v);
+                    v = fma(cf[6][i], ring[cmod(j - R + 1, RING)][i], v);
+                    res[i] = v;
                 }
             } else if constexpr (KIND == W25_VAR || KIND == J25_VAR) {
 #pragma unroll
@@ -456,11 +489,19 @@ plainv_kernel(const SweepArgs<T> a, const __grid_constant__ CUtensorMap tm_u,
                     const int64_t pl = (int64_t)(py - R) * g.nx + (px - R);
 #pragma unroll
                     for (int i = 0; i < V; ++i) {
+                        if (!cin[i]) continue;
                         if (a.inject) res[i] += a.inject[pl + i];
                         if (a.trace) a.trace[pl + i] = res[i];
                     }
                 }
-                pv::st16<T>(a.out + zo, res);
+                if (call) {
+                    pv::st16<T>(a.out + zo, res);
+                } else {
+                    // a vector that straddles the edge of the interior (radius 1)
+#pragma unroll
+                    for (int i = 0; i < V; ++i)
+                        if (cin[i]) a.out[zo + i] = res[i];
+                }
             }
         });
     }
@@ -471,7 +512,10 @@ plainv_kernel(const SweepArgs<T> a, const __grid_constant__ CUtensorMap tm_u,
 template <typename T>
 inline bool plainv_supported(int kind, const Geom &g) {
     constexpr int V = pv::V16<T>::n;
-    return kind_radius(kind) == 4 && g.nx % V == 0 && (int64_t)g.px * g.py < ((int64_t)1 << 30);
+    if ((int64_t)g.px * g.py >= ((int64_t)1 << 30)) return false;
+    if (kind_radius(kind) == 4) return g.nx % V == 0;
+    // 7-point kinds: FP64 vectors of two with an even padded row (16-byte rows)
+    return sizeof(T) == 8 && (kind == J7_CONST || kind == J7_VAR) && g.px % V == 0;
 }
 
 namespace pv {
@@ -521,7 +565,7 @@ cudaError_t launch_plainv(const SweepArgs<T> &a, cudaStream_t st, int num_sms) {
     int per_sm = 0;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 32 * WY, TL::smem);
     if (per_sm < 1) per_sm = 1;
-    const int gx = (a.g.nx + TL::TX - 1) / TL::TX, gy = (a.g.ny + TL::TY - 1) / TL::TY;
+    const int gx = (a.g.nx + R - TL::OS + TL::TX - 1) / TL::TX, gy = (a.g.ny + TL::TY - 1) / TL::TY;
     // z chunks: minimise (waves of resident CTAs) x (planes per chunk incl. the 2R re-read)
     const int64_t resident = (int64_t)num_sms * per_sm, tiles = (int64_t)gx * gy;
     int best = 1;
@@ -557,6 +601,14 @@ cudaError_t launch_plainv_kind_t(int kind, bool adjoint, const SweepArgs<T> &a, 
         }
     }
     switch (kind) {
+    case J7_CONST:
+    case J7_VAR:
+        if constexpr (sizeof(T) == 8) {   // FP64 7-point sweeps (FP32 rows of nx + 2 floats are not 16-byte aligned)
+            if (kind == J7_CONST)
+                return big ? launch_plainv<T, J7_CONST, 16, false, TMA>(a, st, num_sms) : launch_plainv<T, J7_CONST, 8, false, TMA>(a, st, num_sms);
+            return big ? launch_plainv<T, J7_VAR, 16, false, TMA>(a, st, num_sms) : launch_plainv<T, J7_VAR, 8, false, TMA>(a, st, num_sms);
+        }
+        return cudaErrorNotSupported;
     case W25_CONST: return big ? launch_plainv<T, W25_CONST, 16, false, TMA>(a, st, num_sms) : launch_plainv<T, W25_CONST, 8, false, TMA>(a, st, num_sms);
     // the 13-array kinds hold 13 coefficient vectors per thread: their second
     // tile is 4 rows (more CTAs per SM) instead of 16
