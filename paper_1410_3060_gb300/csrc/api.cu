@@ -298,7 +298,7 @@ cudaError_t plain_step(stencil_plan_s *p, bool adjoint, const Scalars &s, const 
                        const void *in_p, const void *in_c, void *out, T *trace, const T *inject, int64_t rcv_z,
                        cudaStream_t st) {
     const int variant = plan_variant(p);
-    if (!adjoint && variant >= 10 && wavefront_supported(p->kind, p->dtype, 1, p->g)) {
+    if (!adjoint && variant >= 10 && variant <= 12 && wavefront_supported(p->kind, p->dtype, 1, p->g)) {
         BlockedArgs<T> w;
         memset(&w, 0, sizeof(w));
         w.u = (const T *)in_c;
@@ -394,7 +394,7 @@ int run_program(stencil_plan_s *p, void *pair_p, void *pair_c, const stencil_coe
             cudaError_t e;
             const int scheme = plan_scheme(p), variant = plan_variant(p);
             if (scheme == 3) {
-                e = launch_wavefront<T>(p->kind, a, variant >= 10 ? variant - 9 : 0, st, p->num_sms);
+                e = launch_wavefront<T>(p->kind, a, (variant >= 10 && variant <= 12) ? variant - 9 : 0, st, p->num_sms);
             } else {
                 if (blocked_scratch_levels(o.levels) > p->nbands) return STENCIL_EUNSUPPORTED;
                 for (int k = 1; k < o.levels; ++k) a.bands[k] = (T *)p->bands[k - 1];
