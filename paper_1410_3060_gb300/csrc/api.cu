@@ -249,7 +249,7 @@ int default_time_block(const stencil_plan_s *p) {
 }
 
 // The register wavefront serves a blocked pass of scheme 3 (and a plain
-// pass of tile variant >= 10) when it supports the kind, dtype, depth and
+// pass of tile variant 10-12) when it supports the kind, dtype, depth and
 // geometry; the shared-memory blocked kernels serve schemes 1 and 2.
 bool pass_supported(const stencil_plan_s *p, int levels) {
     if (plan_scheme(p) == 3) return wavefront_supported(p->kind, p->dtype, levels, p->g);
