@@ -446,7 +446,9 @@ def run_ours(args):
     if tr is not None:
         roofline["traffic"] = tr[0] * float(n) ** 3
         roofline["traffic_source"] = tr[1] + " (bytes per update x updates per launch)"
-    if main["scheme"] == 3 or main["variant"] >= 10:
+    if main["time_block"] == 1 and 13 <= main["variant"] <= 16:
+        kname = "plainv_kernel (vectorised, " + ("TMA" if main["variant"] >= 15 else "cp.async") + " staging)"
+    elif main["scheme"] == 3 or 10 <= main["variant"] <= 12:
         kname = f"wavefront_kernel (register wavefront, {main['time_block']} levels per pass)"
     elif main["time_block"] == 1:
         kname = "plain_stream_kernel" if main["variant"] != 5 else "plain_sweep_kernel"
@@ -456,6 +458,10 @@ def run_ours(args):
     roofline["peak_source"] = ("2 FP64 FMA/clk/SM x %d SMs x %.0f MHz (measured clock); FMA-chain probe %.3f TFLOP/s"
                                % (num_sms, clk / 1e6, probe_f64 / 1e12)) if dtype == st.F64 else \
         "MEASURED_PEAKS.json hbm_gbs (copy, measured)"
+    if "fp64_pipe_view" in roofline:
+        # against the FMA-chain probe: the FP64 rate a kernel of dependent FMAs reaches here
+        pv_ = roofline["fp64_pipe_view"]
+        pv_["frac_of_fma_probe"] = pv_["achieved_ginstr_s"] / (probe_f64 / 2 / 1e9)
 
     variants = []
     if not args.no_variants:
