@@ -63,7 +63,7 @@ __device__ __forceinline__ void st16(T *p, const T (&s)[V16<T>::n]) {
     *reinterpret_cast<typename V16<T>::type *>(p) = v;
 }
 
-template <typename T, int KIND, int WY, bool ADJ = false>
+template <typename T, int KIND, int WY, bool ADJ = false, bool TMA = false>
 struct Tile {
     static constexpr int R = KindTraits<KIND>::R;
     static constexpr int V = V16<T>::n;
@@ -72,13 +72,15 @@ struct Tile {
     static constexpr int OS = R - R % V;             // own columns of tile bx start at bx TX + OS (aligned)
     static constexpr int SW = TX + 2 * RH, SH = TY + 2 * R, SP0 = SW * SH;
     static constexpr int SP = (int)((SP0 * sizeof(T) + 127) / 128 * 128 / sizeof(T));   // slot stride
-    static constexpr int PD = 2;                 // planes in flight
-    static constexpr int NS = R + 1 + PD;        // shared plane slots
     // per-point inputs staged with the field plane: u^{t-1} (second-order
     // kinds) and a single coefficient array (alpha); 13-array kinds load
     // their coefficients directly
     static constexpr int NPS = (KindTraits<KIND>::WAVE ? 1 : 0) + ((KindTraits<KIND>::NARR == 1 && !ADJ) ? 1 : 0);
     static constexpr int PP = TX * TY;           // one per-point plane
+    // planes in flight: one more with TMA (its copies take no registers)
+    // where the slots fit shared memory
+    static constexpr int PD = (TMA && NPS < 2) ? 3 : 2;
+    static constexpr int NS = R + 1 + PD;        // shared plane slots
     static constexpr size_t smem = sizeof(T) * ((size_t)NS * SP + (size_t)NS * NPS * PP) + 8 * NS + 128;
     static_assert((sizeof(T) * SP) % 128 == 0 && (sizeof(T) * PP) % 128 == 0, "128-byte aligned slots");
     static constexpr int MINB = 1;
@@ -134,10 +136,10 @@ static __device__ unsigned int g_wait_timeouts;
 // (A^T y)(q) = sum_k A_k(q - o_k) y(q - o_k); x-shifted coefficients come
 // from the three (FP32) or five (FP64) aligned vectors around the own one.
 template <typename T, int KIND, int WY, bool ADJ = false, bool TMA = false>
-__global__ void __launch_bounds__(32 * WY, pv::Tile<T, KIND, WY, ADJ>::MINB)
+__global__ void __launch_bounds__(32 * WY, pv::Tile<T, KIND, WY, ADJ, TMA>::MINB)
 plainv_kernel(const SweepArgs<T> a, const __grid_constant__ CUtensorMap tm_u,
               const __grid_constant__ CUtensorMap tm_p, const __grid_constant__ CUtensorMap tm_a) {
-    using TL = pv::Tile<T, KIND, WY, ADJ>;
+    using TL = pv::Tile<T, KIND, WY, ADJ, TMA>;
     constexpr int R = TL::R, V = TL::V;
     constexpr bool WAVE = KindTraits<KIND>::WAVE;
     constexpr int NA = KindTraits<KIND>::NARR;
@@ -546,7 +548,7 @@ inline cudaError_t make_tmap(CUtensorMap *m, const void *base, int elem_bytes, c
 
 template <typename T, int KIND, int WY, bool ADJ = false, bool TMA = false>
 cudaError_t launch_plainv(const SweepArgs<T> &a, cudaStream_t st, int num_sms) {
-    using TL = pv::Tile<T, KIND, WY, ADJ>;
+    using TL = pv::Tile<T, KIND, WY, ADJ, TMA>;
     constexpr int R = TL::R;
     auto kern = plainv_kernel<T, KIND, WY, ADJ, TMA>;
     CUtensorMap tm_u, tm_p, tm_a;
