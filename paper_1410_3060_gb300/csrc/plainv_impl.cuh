@@ -77,9 +77,10 @@ struct Tile {
     // their coefficients directly
     static constexpr int NPS = (KindTraits<KIND>::WAVE ? 1 : 0) + ((KindTraits<KIND>::NARR == 1 && !ADJ) ? 1 : 0);
     static constexpr int PP = TX * TY;           // one per-point plane
-    // planes in flight: one more with TMA (its copies take no registers)
-    // where the slots fit shared memory
-    static constexpr int PD = (TMA && NPS < 2) ? 3 : 2;
+    // planes in flight: one more with TMA (its copies take no registers) for
+    // the constant wave (measured: 423 vs 402 GLUP/s at 512^3; the 13-array
+    // kinds run slower with the larger ring)
+    static constexpr int PD = (TMA && NPS == 1 && KindTraits<KIND>::NARR == 0) ? 3 : 2;
     static constexpr int NS = R + 1 + PD;        // shared plane slots
     static constexpr size_t smem = sizeof(T) * ((size_t)NS * SP + (size_t)NS * NPS * PP) + 8 * NS + 128;
     static_assert((sizeof(T) * SP) % 128 == 0 && (sizeof(T) * PP) % 128 == 0, "128-byte aligned slots");
@@ -188,14 +189,27 @@ plainv_kernel(const SweepArgs<T> a, const __grid_constant__ CUtensorMap tm_u,
     }
     // this thread's points: padded row y0 + R + w, columns xo + lane V ..
     const int px = xo + lane * V, py = y0 + R + w;
+    // radius 4 (nx % V == 0): a vector is wholly in or out of the interior;
+    // radius 1: the vectors at the interior's x edges hold one halo point
+    constexpr bool PARTIAL = (R % V) != 0;
     bool cin[V];
-    bool call = py < g.ny + R, own = false;   // own: any point of the vector is interior
+    bool call, own;   // own: any point of the vector is interior
+    if constexpr (PARTIAL) {
+        call = py < g.ny + R;
+        own = false;
 #pragma unroll
-    for (int i = 0; i < V; ++i) {
-        cin[i] = py < g.ny + R && px + i >= R && px + i < g.nx + R;
-        call = call && cin[i];
-        own = own || cin[i];
+        for (int i = 0; i < V; ++i) {
+            cin[i] = py < g.ny + R && px + i >= R && px + i < g.nx + R;
+            call = call && cin[i];
+            own = own || cin[i];
+        }
+    } else {
+        own = px < g.nx + R && py < g.ny + R;
+        call = own;
+#pragma unroll
+        for (int i = 0; i < V; ++i) cin[i] = own;
     }
+    (void)call;
     const int poff = py * sy + px;
     const int scen = (R + w) * SW + RH + lane * V;     // shared offset of the own vector
     const int pown = w * TX + lane * V;                // offset in a per-point plane
@@ -496,13 +510,17 @@ plainv_kernel(const SweepArgs<T> a, const __grid_constant__ CUtensorMap tm_u,
                         if (a.trace) a.trace[pl + i] = res[i];
                     }
                 }
-                if (call) {
-                    pv::st16<T>(a.out + zo, res);
-                } else {
-                    // a vector that straddles the edge of the interior (radius 1)
+                if constexpr (PARTIAL) {
+                    if (call) {
+                        pv::st16<T>(a.out + zo, res);
+                    } else {
+                        // a vector that straddles the edge of the interior
 #pragma unroll
-                    for (int i = 0; i < V; ++i)
-                        if (cin[i]) a.out[zo + i] = res[i];
+                        for (int i = 0; i < V; ++i)
+                            if (cin[i]) a.out[zo + i] = res[i];
+                    }
+                } else {
+                    pv::st16<T>(a.out + zo, res);
                 }
             }
         });
