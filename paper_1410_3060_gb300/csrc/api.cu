@@ -227,7 +227,7 @@ int plan_scheme(const stencil_plan_s *p) {
 
 // Default tile variant: the register wavefront tiles for FP32 7-point plans,
 // the TMA-staged vectorised 25-point sweep where the geometry allows it
-// (measured at 512^3: FP32 W25_CONST 402 vs 274 GLUP/s for the best
+// (measured at 512^3: FP32 W25_CONST 448 vs 274 GLUP/s for the best
 // streaming tile, W25_VAR 105 vs 76; FP64 W25_VAR 20.6 vs 18.6; FP64
 // W25_CONST is FP64-bound either way and keeps the streaming kernel), else
 // the streaming-kernel default.

@@ -78,7 +78,7 @@ struct Tile {
     static constexpr int NPS = (KindTraits<KIND>::WAVE ? 1 : 0) + ((KindTraits<KIND>::NARR == 1 && !ADJ) ? 1 : 0);
     static constexpr int PP = TX * TY;           // one per-point plane
     // planes in flight: one more with TMA (its copies take no registers) for
-    // the constant wave (measured: 423 vs 402 GLUP/s at 512^3; the 13-array
+    // the constant wave (measured: 448 vs 402 GLUP/s at 512^3; the 13-array
     // kinds run slower with the larger ring)
     static constexpr int PD = (TMA && NPS == 1 && KindTraits<KIND>::NARR == 0) ? 3 : 2;
     static constexpr int NS = R + 1 + PD;        // shared plane slots
