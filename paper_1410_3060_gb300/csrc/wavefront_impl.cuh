@@ -96,7 +96,7 @@ struct WfGeom {
 }  // namespace
 
 // Tile constants of one (V, NR, WY, B, R) configuration.
-template <int V, int NR, int WY, int B, int R>
+template <int V, int NR, int WY, int B, int R, int ELEM>
 struct WfTile {
     static constexpr int TXE = 32 * V, TYE = WY * NR;
     static constexpr int BR = B * R;
@@ -104,14 +104,16 @@ struct WfTile {
     static constexpr int SX = (TXE - BR - AX) / V * V;   // owned columns per tile
     static constexpr int SY = TYE - 2 * BR;              // owned rows per tile
     static constexpr int RING = 2 * R + 1;
-    static constexpr int PD = 2;                          // level-0 planes in flight
-    static constexpr int NS = PD + 2;                     // level-0 shared slots
     static constexpr int NX = RING;                       // edge-row buffers (one per step mod RING)
+    // level-0 planes in flight: three where the slots fit shared memory
+    static constexpr size_t XB = (size_t)ELEM * NX * B * WY * 2 * R * TXE;
+    static constexpr int PD = (size_t)ELEM * 5 * TYE * TXE + XB <= 200 * 1024 ? 3 : 2;
+    static constexpr int NS = PD + 2;                     // level-0 shared slots
 };
 
 template <typename T, int V, int NR, int WY, int B, int R>
 constexpr size_t wf_smem() {
-    using TL = WfTile<V, NR, WY, B, R>;
+    using TL = WfTile<V, NR, WY, B, R, (int)sizeof(T)>;
     return sizeof(T) * ((size_t)TL::NS * TL::TYE * TL::TXE + (size_t)TL::NX * B * WY * 2 * R * TL::TXE);
 }
 
@@ -120,7 +122,7 @@ __global__ void __launch_bounds__(32 * WY) wavefront_kernel(const BlockedArgs<T>
     constexpr int R = KindTraits<KIND>::R;
     constexpr int NA = KindTraits<KIND>::NARR;
     static_assert(R == 1 && (KIND == J7_CONST || KIND == J7_VAR), "radius-1 kinds");
-    using TL = WfTile<V, NR, WY, B, R>;
+    using TL = WfTile<V, NR, WY, B, R, (int)sizeof(T)>;
     constexpr int RING = TL::RING;
     constexpr int U = RING;               // steps per unrolled block: ring slots are constants
     constexpr int PD = TL::PD, NS = TL::NS;
