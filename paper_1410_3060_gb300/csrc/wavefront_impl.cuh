@@ -105,9 +105,9 @@ struct WfTile {
     static constexpr int SY = TYE - 2 * BR;              // owned rows per tile
     static constexpr int RING = 2 * R + 1;
     static constexpr int NX = RING;                       // edge-row buffers (one per step mod RING)
-    // level-0 planes in flight: three where the slots fit shared memory
-    static constexpr size_t XB = (size_t)ELEM * NX * B * WY * 2 * R * TXE;
-    static constexpr int PD = (size_t)ELEM * 5 * TYE * TXE + XB <= 200 * 1024 ? 3 : 2;
+    // level-0 planes in flight (three measured slower: 510 vs 632 GLUP/s for
+    // the one-level 7-point constant sweep at 512^3)
+    static constexpr int PD = 2;
     static constexpr int NS = PD + 2;                     // level-0 shared slots
 };
 
