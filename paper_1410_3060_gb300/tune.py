@@ -16,7 +16,7 @@ def default_candidates(plan: st.Plan):
     """Every one-level tile variant, and every block depth with every blocked
     kernel family (register wavefront tiles, shared-memory overlapped and
     diamond tiles)."""
-    out = [(1, 0, v) for v in range(1, 15)]
+    out = [(1, 0, v) for v in range(1, 17)]
     for b in (2, 3, 4):
         out += [(b, 3, v) for v in (10, 11, 12)]
         out += [(b, s, 0) for s in (1, 2)]

@@ -1,0 +1,55 @@
+"""Host logic of bench.py and the run-time tuner (no GPU): the roofline
+record's arithmetic and the tuner's candidate list."""
+import importlib.util
+import os
+
+import pytest
+
+from paper_1410_3060_gb300 import perfmodel as pm
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def bench():
+    spec = importlib.util.spec_from_file_location("bench_mod", os.path.join(ROOT, "bench.py"))
+    mod = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(mod)
+    return mod
+
+
+def test_fp32_roofline_counts_bytes_once_per_pass(bench):
+    """A pass of b levels moves the plain bytes of one update once: at 64
+    steps in 16 passes of 4 levels taking 1 s in total, 512^3 points x 36 B
+    x 16 passes of 7-point variable FP32 traffic per second."""
+    n, T, b, ms = 512, 64, 4, 1000.0
+    res = {"time_block": b, "ms_per_step": ms, "T": T}
+    r = bench.roofline_of(pm, pm.J7_VAR, "f32", n, res, 1.26e12, 6788.6, 78e12)
+    expect_gbs = 36.0 * n ** 3 * (T / b) / 1.0 / 1e9
+    assert r["bound"] == "hbm" and r["unit"] == "GB/s"
+    assert abs(r["achieved"] - expect_gbs) < 1e-9 * expect_gbs
+    assert abs(r["frac"] - expect_gbs / 6788.6) < 1e-12
+
+
+def test_fp64_roofline_flops_and_pipe_views(bench):
+    """FP64: flops (FMA = 2) against 2 FMA/clk/SM x SMs x clock, and the
+    FP64 instruction view (adds count as a full pipe slot)."""
+    n, T, ms = 512, 64, 1000.0
+    peak = 1.2544e12
+    res = {"time_block": 1, "ms_per_step": ms, "T": T}
+    r = bench.roofline_of(pm, pm.J7_CONST, "f64", n, res, peak, 6788.6, 78e12)
+    lups = float(n) ** 3 * T
+    assert r["bound"] == "alu"
+    assert abs(r["achieved"] - 8 * lups / 1e12) < 1e-9
+    pv = r["fp64_pipe_view"]
+    assert pv["fp64_instr_per_update"] == 7
+    assert abs(pv["frac"] - 7 * lups / (peak / 2)) < 1e-12
+
+
+def test_tuner_candidates_cover_every_kernel_family():
+    from paper_1410_3060_gb300 import tune
+    c = tune.default_candidates(None)
+    assert set(v for b, s, v in c if b == 1) == set(range(1, 17))
+    for b in (2, 3, 4):
+        fams = {(s, v) for bb, s, v in c if bb == b}
+        assert {(3, 10), (3, 11), (3, 12), (1, 0), (2, 0)} <= fams
