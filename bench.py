@@ -266,7 +266,7 @@ def forward_case(torch, st, wl, kind, n, T, dtype, steps, warmup, ws, stream, ti
         copied = [torch.cuda.Event(), torch.cuda.Event()]
         done = [None, None]
 
-        def h2d(k):
+        def copy_inputs(k):
             with torch.cuda.stream(cs):
                 if done[k] is not None:
                     cs.wait_event(done[k])          # the sweeps that last read this set are finished
@@ -280,11 +280,11 @@ def forward_case(torch, st, wl, kind, n, T, dtype, steps, warmup, ws, stream, ti
         barrier(torch, ws)
         with Timer(torch, stream) as te:
             cs.wait_stream(stream)
-            h2d(0)
+            copy_inputs(0)
             for i in range(steps):
                 k = i % 2
                 if i + 1 < steps:
-                    h2d(1 - k)
+                    copy_inputs(1 - k)
                 stream.wait_event(copied[k])
                 p_, u_, W_ = sets[k]
                 plan.forward(p_, u_, wk.w, W_, T, stream=stream)
