@@ -53,3 +53,23 @@ def test_tuner_candidates_cover_every_kernel_family():
     for b in (2, 3, 4):
         fams = {(s, v) for bb, s, v in c if bb == b}
         assert {(3, 10), (3, 11), (3, 12), (1, 0), (2, 0)} <= fams
+
+
+def test_reference_arm_prints_one_contract_line():
+    """bench.py --impl reference runs on the host cores (the FP64 oracle) and
+    prints one JSON line with the contract's keys."""
+    import json
+    import subprocess
+    import sys
+    out = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--n", "24",
+                          "--T", "2", "--steps", "1", "--warmup", "1"], capture_output=True, text=True, timeout=600,
+                         cwd=ROOT)
+    assert out.returncode == 0, out.stderr[-2000:]
+    lines = [l for l in out.stdout.splitlines() if l.startswith("{")]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    for k in ("metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step", "higher_is_better", "scaling",
+              "dtype", "config", "e2e", "cpu_baseline", "impl"):
+        assert k in d, k
+    assert d["impl"] == "reference" and d["value"] > 0
+    assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["cores"] >= 1
