@@ -311,6 +311,24 @@ def forward_case(torch, st, wl, kind, n, T, dtype, steps, warmup, ws, stream, ti
 # configurations summarised under profiles/; the roofline record reports them
 # scaled to one launch of the benchmarked size, null for any other kernel.
 MEASURED_TRAFFIC = {("j7_var", "f64", 1, 8): (72.5, "profiles/plain_stream_j7_var_256_fp64.md")}
+# thread instructions per update of the on-chip-bound FP32 kernels (ncu
+# warp instructions x 32 / updates of the profiled launch): the issue view of
+# their roofline, ceiling = 4 warp instructions per clock per SM
+MEASURED_INSTR = {
+    ("j7_const", "f32", 3, 10): (28.5, "profiles/wavefront_j7_const_512_fp32_b3.md"),
+    ("j7_var", "f32", 4, 11): (70.4, "profiles/wavefront_j7_var_384_fp32_b4.md"),
+    ("w25_const", "f32", 1, 15): (47.3, "profiles/plainv_tma_w25_const_512_fp32.md"),
+}
+
+
+def issue_view(kind_name, dtype_name, res, num_sms, clk_hz):
+    """Instruction-issue ceiling of a profiled kernel configuration, or None."""
+    m = MEASURED_INSTR.get((kind_name, dtype_name, res["time_block"], res["variant"]))
+    if m is None:
+        return None
+    ceiling = num_sms * 4 * 32 * clk_hz / m[0] / 1e9
+    return {"thread_instr_per_update": m[0], "ceiling_glups": ceiling, "frac": res["glups"] / ceiling,
+            "source": m[1]}
 
 KIND_BY_NAME = {"j7_const": 1, "j7_var": 2, "w25_const": 3, "w25_var": 4, "j25_var": 5, "w25_alpha": 6}
 KIND_TEXT = {1: "7-point constant coefficients (Fig. 1b)", 2: "7-point variable coefficients (Fig. 1c)",
@@ -488,6 +506,9 @@ def run_ours(args):
     roofline["peak_source"] = ("2 FP64 FMA/clk/SM x %d SMs x %.0f MHz (measured clock); FMA-chain probe %.3f TFLOP/s"
                                % (num_sms, clk / 1e6, probe_f64 / 1e12)) if dtype == st.F64 else \
         "MEASURED_PEAKS.json hbm_gbs (copy, measured)"
+    iv = issue_view(args.kind, args.dtype, main, num_sms, clk)
+    if iv:
+        roofline["issue_view"] = iv
     if "fp64_pipe_view" in roofline:
         # against the FMA-chain probe: the FP64 rate a kernel of dependent FMAs reaches here
         pv_ = roofline["fp64_pipe_view"]
@@ -507,6 +528,9 @@ def run_ours(args):
             r, _ = forward_case(torch, st, wl, vk, n, vT, vd, max(1, args.steps // 2), 1, ws, stream,
                                 time_block=vb, wk=cache[vk])
             r["roofline"] = roofline_of(pm, vk, r["dtype"], n, r, peak_f64, hbm_peak, peak_f32)
+            iv = issue_view(wl.KIND_NAMES[vk], r["dtype"], r, num_sms, clk)
+            if iv:
+                r["roofline"]["issue_view"] = iv
             variants.append(r)
         cache.clear()
         # forward + adjoint of the differentiable wave workload (256^3, T = 200, K = 20)
