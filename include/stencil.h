@@ -113,7 +113,7 @@ enum stencil_option {
        (4 rows for the 13-array kinds; needs nx a multiple of 4 in FP32, of
        2 in FP64), 15 and 16 = the same tiles staged by TMA (one tensor copy
        per plane tile, mbarrier completion).  A variant a kind or geometry
-       cannot use runs the default streaming tile.  The default is the measured best: 10 / 11 for FP32
+       cannot use runs the default streaming tile.  The default is the measured best: 12 / 11 for FP32
        J7_CONST / J7_VAR, 15 for FP32 W25_CONST and W25_ALPHA, 16 for
        W25_VAR and J25_VAR, else a streaming tile. */
     STENCIL_OPT_VARIANT = 5,

@@ -212,9 +212,10 @@ struct stencil_plan_s {
 namespace {
 
 // FP32 7-point plans whose geometry the register wavefront serves default
-// to it (measured fastest on GB300 at 512^3: depth 3 with 64x32 tiles of
-// 4 rows per thread for the constant kind, depth 4 with 2 rows per thread
-// for the variable kind); all other plans to the shared-memory kernels.
+// to it (measured fastest on GB300 at 512^3, T = 64: depth 3 with 64x64
+// tiles for the constant kind, 898 GLUP/s; depth 4 with 64x32 tiles of 2
+// rows per thread for the variable kind, 238); all other plans to the
+// shared-memory kernels.
 bool wavefront_default(const stencil_plan_s *p) {
     return p->dtype == 1 && (p->kind == J7_CONST || p->kind == J7_VAR) &&
            wavefront_supported(p->kind, p->dtype, 1, p->g);
@@ -233,7 +234,7 @@ int plan_scheme(const stencil_plan_s *p) {
 // the streaming-kernel default.
 int plan_variant(const stencil_plan_s *p) {
     if (p->variant) return p->variant;
-    if (wavefront_default(p)) return p->kind == J7_CONST ? 10 : 11;
+    if (wavefront_default(p)) return p->kind == J7_CONST ? 12 : 11;
     const bool vec = p->dtype == 1 ? plainv_supported_f32(p->kind, p->g) : plainv_supported_f64(p->kind, p->g);
     if (vec) {
         const bool arrays13 = p->kind == W25_VAR || p->kind == J25_VAR;
