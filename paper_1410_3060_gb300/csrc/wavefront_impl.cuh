@@ -112,9 +112,23 @@ struct WfTile {
 };
 
 template <typename T, int V, int NR, int WY, int B, int R>
-constexpr size_t wf_smem() {
+constexpr size_t wf_smem_base() {
     using TL = WfTile<V, NR, WY, B, R, (int)sizeof(T)>;
     return sizeof(T) * ((size_t)TL::NS * TL::TYE * TL::TXE + (size_t)TL::NX * B * WY * 2 * R * TL::TXE);
+}
+// Variable kind: levels 2..B read their coefficients from a shared ring of
+// B-1 planes that level 1 fills (each thread its own points) where it fits
+// next to the other buffers; otherwise they re-read them from L2.
+template <typename T, int V, int NR, int WY, int B, int R, int NA>
+constexpr int wf_coef_slots() {
+    if (NA == 0 || B < 2) return 0;
+    const size_t ring = sizeof(T) * (size_t)(B - 1) * NA * NR * 32 * WY * V;
+    return wf_smem_base<T, V, NR, WY, B, R>() + ring <= 227 * 1024 ? B - 1 : 0;
+}
+template <typename T, int V, int NR, int WY, int B, int R, int NA = 0>
+constexpr size_t wf_smem() {
+    return wf_smem_base<T, V, NR, WY, B, R>() +
+           sizeof(T) * (size_t)wf_coef_slots<T, V, NR, WY, B, R, NA>() * NA * NR * 32 * WY * V;
 }
 
 template <typename T, int KIND, int B, int V, int NR, int WY>
@@ -139,6 +153,12 @@ __global__ void __launch_bounds__(32 * WY) wavefront_kernel(const BlockedArgs<T>
     extern __shared__ __align__(16) unsigned char smem_raw[];
     T *const s0b = reinterpret_cast<T *>(smem_raw);
     T *const xb = s0b + NS * S0;
+    // coefficient ring [slot][array][row][thread][V] (variable kind)
+    constexpr int CR = wf_coef_slots<T, V, NR, WY, B, R, NA>();
+    T *const cring = xb + TL::NX * XP;
+    const int tidv = (threadIdx.y * 32 + threadIdx.x) * V;
+    constexpr int CRN = 32 * WY * V;   // one (array, row) of a ring slot
+    (void)cring; (void)tidv;
 
     const Geom &g = a.g;
     const int lane = threadIdx.x, w = threadIdx.y;
@@ -349,6 +369,12 @@ __global__ void __launch_bounds__(32 * WY) wavefront_kernel(const BlockedArgs<T>
                             for (int t = 0; t < NA; ++t)
 #pragma unroll
                                 for (int i = 0; i < V; ++i) cf[t][i] = cf1[jr][t][i];
+                        } else if constexpr (NA > 0 && CR > 0) {
+                            // plane zk, stored by level 1 at the end of step zk + 1
+                            const int cs = ((zk % CR) + CR) % CR;
+#pragma unroll
+                            for (int t = 0; t < NA; ++t)
+                                vld<T, V>(cf[t], cring + ((cs * NA + t) * NR + jr) * CRN + tidv);
                         } else if constexpr (NA > 0) {
                             if ((lmask >> jr) & 1u) {
                                 const int o = off0 + jr * sy;
@@ -394,6 +420,15 @@ __global__ void __launch_bounds__(32 * WY) wavefront_kernel(const BlockedArgs<T>
                     if (a.out_prev) store_plane(a.out_prev + (int64_t)(zk + R) * sz, lev(IC<B - 1>{}, IC<pc>{}));
                 }
             });
+            if constexpr (NA > 0 && CR > 0) {
+                // level 1's coefficients (plane q - R) for levels 2..B of the
+                // next B-1 steps (each thread its own points: no barrier)
+                const int cs = (((q - R) % CR) + CR) % CR;
+#pragma unroll
+                for (int jr = 0; jr < NR; ++jr)
+#pragma unroll
+                    for (int t = 0; t < NA; ++t) vst<T, V>(cring + ((cs * NA + t) * NR + jr) * CRN + tidv, cf1[jr][t]);
+            }
         });
     }
     cp_async_wait<0>();
@@ -411,7 +446,7 @@ cudaError_t launch_wf(const BlockedArgs<T> &a, cudaStream_t st, int num_sms) {
     constexpr int SX = (TXE - BR - AX) / V * V;
     constexpr int SY = TYE - 2 * BR;
     auto kern = wavefront_kernel<T, KIND, B, V, NR, WY>;
-    constexpr size_t smem = wf_smem<T, V, NR, WY, B, R>();
+    constexpr size_t smem = wf_smem<T, V, NR, WY, B, R, KindTraits<KIND>::NARR>();
     static_assert(smem <= 227 * 1024, "shared memory per CTA");
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
