@@ -79,7 +79,7 @@ enum stencil_status {
 enum stencil_option {
     /* Time levels applied per pass over the lattice (the temporal block
        depth b).  0 = library default for the kind, dtype and scheme (3 for
-       FP32 J7_CONST and 4 for FP32 J7_VAR on the register wavefront, 1 =
+       FP32 J7_CONST and 2 for FP32 J7_VAR on the register wavefront, 1 =
        plain sweeps otherwise), 1 = plain one-step-per-sweep kernel. */
     STENCIL_OPT_TIME_BLOCK = 1,
     /* Kernel family of a blocked pass: 0 = default (3 for FP32 7-point

@@ -213,9 +213,9 @@ namespace {
 
 // FP32 7-point plans whose geometry the register wavefront serves default
 // to it (measured fastest on GB300 at 512^3, T = 64: depth 3 with 64x64
-// tiles for the constant kind, 898 GLUP/s; depth 4 with 64x32 tiles of 2
-// rows per thread for the variable kind, 238); all other plans to the
-// shared-memory kernels.
+// tiles for the constant kind, 898 GLUP/s; depth 2 with 64x32 tiles of 2
+// rows per thread and the shared coefficient ring for the variable kind,
+// 265); all other plans to the shared-memory kernels.
 bool wavefront_default(const stencil_plan_s *p) {
     return p->dtype == 1 && (p->kind == J7_CONST || p->kind == J7_VAR) &&
            wavefront_supported(p->kind, p->dtype, 1, p->g);
@@ -245,7 +245,7 @@ int plan_variant(const stencil_plan_s *p) {
 }
 
 int default_time_block(const stencil_plan_s *p) {
-    if (plan_scheme(p) == 3 && wavefront_default(p)) return p->kind == J7_CONST ? 3 : 4;
+    if (plan_scheme(p) == 3 && wavefront_default(p)) return p->kind == J7_CONST ? 3 : 2;
     return blocked_default_levels(p->kind, p->dtype);
 }
 

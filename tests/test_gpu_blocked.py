@@ -86,7 +86,7 @@ def test_time_block_option_roundtrip(st):
     p = st.Plan(1, 32, 32, 32, F32)
     assert p.get(2) == 3 and p.get(1) == 3 and p.get(5) == 12   # FP32 7-point defaults
     q = st.Plan(2, 32, 32, 32, F32)
-    assert q.get(2) == 3 and q.get(1) == 4 and q.get(5) == 11
+    assert q.get(2) == 3 and q.get(1) == 2 and q.get(5) == 11
     q.close()
     p.set(2, 2)                                                  # shared-memory diamond tiles
     p.set(1, 4)
