@@ -317,6 +317,7 @@ MEASURED_TRAFFIC = {("j7_var", "f64", 1, 8): (72.5, "profiles/plain_stream_j7_va
 MEASURED_INSTR = {
     ("j7_const", "f32", 3, 10): (28.5, "profiles/wavefront_j7_const_512_fp32_b3.md"),
     ("j7_const", "f32", 3, 12): (26.6, "profiles/wavefront_j7_const_512_fp32_b3_64x64.md"),
+    ("j7_var", "f32", 2, 11): (63.6, "profiles/wavefront_j7_var_384_fp32_b2_ring.md"),
     ("j7_var", "f32", 4, 11): (70.4, "profiles/wavefront_j7_var_384_fp32_b4.md"),
     ("w25_const", "f32", 1, 15): (47.3, "profiles/plainv_tma_w25_const_512_fp32.md"),
 }
