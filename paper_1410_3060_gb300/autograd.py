@@ -7,10 +7,11 @@ the initial field and the coefficient arrays.
 Forward: stencil_forward in segments of K steps (temporally blocked where
 the library blocks the kind), keeping the state pair at every checkpoint
 (every K steps) and the receiver trace; stencil_misfit gives the FP64 loss
-and the residual.
+and the residual.  The last segment runs through stencil_forward_states,
+so that its states are kept for the backward pass.
 
 Backward, segment by segment from the last: stencil_forward_states
-recomputes the K states of the segment from its checkpoint (on a second
+recomputes the K states of every earlier segment from its checkpoint (on a second
 stream, one segment ahead, into the other of two state-buffer sets, so that
 the recompute of segment i-1 overlaps the adjoint of segment i), then
 stencil_adjoint runs the transposed sweep backward over the segment,
@@ -85,6 +86,7 @@ class MisfitRunner:
             for b in bs:
                 st.fill_zero(b)   # zero halos (only interiors are ever written)
         self._side = torch.cuda.Stream(device=device) if self.overlap else None
+        self._kept = None
 
     def close(self):
         self.plan.close()
@@ -103,18 +105,27 @@ class MisfitRunner:
         trace = self._trace
         ckpts = []
         t = 0
-        for i in range(len(self._ckpt)):
+        nck = len(self._ckpt)
+        for i in range(nck):
             cp, cu = self._ckpt[i]
             cp.copy_(up)
             cu.copy_(u)
             ckpts.append((t, cp, cu))
             k = min(K, T - t)
-            self.plan.forward(up, u, self.w, W, k, trace=trace[t:t + k], rcv_z=self.rcv_z)
+            if i == nck - 1:
+                # the last segment's states are the first ones the backward
+                # pass reads: they are kept (in the buffer set of the
+                # backward's first segment) instead of being recomputed
+                self.plan.forward_states(up, u, self.w, W, self._sets[0][:k], trace=trace[t:t + k],
+                                         rcv_z=self.rcv_z)
+            else:
+                self.plan.forward(up, u, self.w, W, k, trace=trace[t:t + k], rcv_z=self.rcv_z)
             t += k
         res = self._res                      # res[i] = r^i, r^0 = 0
         st.fill_zero(res[0])
         self.plan.misfit(trace, d, res[1:], self._loss)
-        return self._loss[0].clone(), {"ckpts": ckpts, "res": res, "last": u}
+        self._kept = {"valid": True}
+        return self._loss[0].clone(), {"ckpts": ckpts, "res": res, "kept": self._kept}
 
     # -- backward: recompute + adjoint per segment
     def backward_pass(self, state, W, gloss):
@@ -135,6 +146,12 @@ class MisfitRunner:
         main = torch.cuda.current_stream()
         nsets = len(self._sets)
         rec_ev, adj_ev = [None] * nsets, [None] * nsets
+        # the forward pass left the last segment's states in buffer set 0,
+        # valid until a backward pass (or a later forward pass) reuses the set
+        kept = state.get("kept")
+        have_last = kept is not None and kept["valid"] and kept is self._kept
+        if kept is not None:
+            kept["valid"] = False
 
         def recompute(i, stream):
             # u^{c+1} .. u^{c+k} of segment i into buffer set i mod nsets
@@ -144,9 +161,10 @@ class MisfitRunner:
 
         if self.overlap:
             self._side.wait_stream(main)          # checkpoints, residual and cleared buffers are ready
-            with torch.cuda.stream(self._side):
-                recompute(0, self._side)
-                rec_ev[0] = self._side.record_event()
+            if not have_last:
+                with torch.cuda.stream(self._side):
+                    recompute(0, self._side)
+                    rec_ev[0] = self._side.record_event()
         top = True
         for i, (c, cp, cu) in enumerate(segs):
             k = min(K, T - c)
@@ -161,8 +179,9 @@ class MisfitRunner:
                             self._side.wait_event(adj_ev[j])
                         recompute(i + 1, self._side)
                         rec_ev[j] = self._side.record_event()
-                main.wait_event(rec_ev[i % nsets])
-            else:
+                if rec_ev[i % nsets] is not None:
+                    main.wait_event(rec_ev[i % nsets])
+            elif not (i == 0 and have_last):
                 recompute(i, main)
             bufs = self._sets[i % nsets]
             states = [cu] + bufs[:k - 1]

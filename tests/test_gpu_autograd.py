@@ -159,3 +159,27 @@ def test_autograd_finite_differences_gpu(st, fwi48):
         an = float((W.grad * dw).sum())
         assert abs(fd - an) <= 1e-5 * max(abs(an), abs(fd)), (k, fd, an)
     run.close()
+
+
+@pytest.mark.parametrize("overlap", [True, False])
+def test_backward_pass_repeated(st, fwi48, overlap):
+    """The forward pass keeps the last segment's states for the backward
+    pass; a second backward pass on the same forward state recomputes them
+    and gives the same gradients (both runner modes), which match the
+    oracle's."""
+    import torch
+    from paper_1410_3060_gb300.autograd import MisfitRunner
+    fw, d, _, odu0, odW = fwi48
+    run = MisfitRunner(wl.W25_VAR, fw.n, fw.T, fw.K, fw.rcv_z, dtype=F64, overlap=overlap)
+    u0, W, dd = to_dev(fw.u0, F64), to_dev(fw.W, F64), to_dev(d, F64)
+    one = torch.ones((), dtype=torch.float64)
+    _, state = run.forward_pass(u0, W, dd)
+    du0a, dWa = run.backward_pass(state, W, one)
+    du0a, dWa = du0a.clone(), dWa.clone()
+    du0b, dWb = run.backward_pass(state, W, one)
+    torch.cuda.synchronize()
+    assert torch.equal(du0a, du0b) and torch.equal(dWa, dWb)
+    assert normwise_err(to_np(du0a), odu0) <= 1e-10
+    for k in range(13):
+        assert normwise_err(to_np(dWa[k]), odW[k]) <= 1e-10, k
+    run.close()
