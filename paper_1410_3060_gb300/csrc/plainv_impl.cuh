@@ -543,7 +543,10 @@ namespace pv {
 // elements; the tensor unit fills zeros outside the array.  The encoder is
 // the driver's, looked up through the runtime (no link against the driver
 // library).
-inline cudaError_t make_tmap(CUtensorMap *m, const void *base, int elem_bytes, const Geom &g, int bx, int by) {
+// `arrays` > 1: that many padded fields stored one after another, mapped as
+// one volume of arrays x pz planes.
+inline cudaError_t make_tmap(CUtensorMap *m, const void *base, int elem_bytes, const Geom &g, int bx, int by,
+                             int arrays = 1) {
     static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
     if (!fn) {
         void *f = nullptr;
@@ -552,7 +555,7 @@ inline cudaError_t make_tmap(CUtensorMap *m, const void *base, int elem_bytes, c
         if (e != cudaSuccess || q != cudaDriverEntryPointSuccess || !f) return e != cudaSuccess ? e : cudaErrorNotSupported;
         fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(f);
     }
-    const cuuint64_t dims[3] = {(cuuint64_t)g.px, (cuuint64_t)g.py, (cuuint64_t)g.pz};
+    const cuuint64_t dims[3] = {(cuuint64_t)g.px, (cuuint64_t)g.py, (cuuint64_t)g.pz * (cuuint64_t)arrays};
     const cuuint64_t strides[2] = {(cuuint64_t)g.px * elem_bytes, (cuuint64_t)g.px * g.py * elem_bytes};
     const cuuint32_t box[3] = {(cuuint32_t)bx, (cuuint32_t)by, 1};
     const cuuint32_t es[3] = {1, 1, 1};
@@ -561,6 +564,21 @@ inline cudaError_t make_tmap(CUtensorMap *m, const void *base, int elem_bytes, c
                           CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
                           CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
+
+// Interior planes per z chunk: minimise (waves of resident CTAs) x (planes
+// per chunk including the 2R planes a chunk re-reads).
+inline int pick_zchunk(int nz, int R, int64_t tiles, int64_t resident) {
+    int best = 1;
+    double best_cost = 1e300;
+    for (int nzc = 1; nzc <= nz; ++nzc) {
+        const int chunk = (nz + nzc - 1) / nzc;
+        if (nzc > 1 && chunk < 4 * R) break;
+        const int64_t ctas = tiles * ((nz + chunk - 1) / chunk);
+        const double cost = (double)((ctas + resident - 1) / resident) * (chunk + 2 * R);
+        if (cost < best_cost * 0.999) { best_cost = cost; best = nzc; }
+    }
+    return (nz + best - 1) / best;
 }
 }  // namespace pv
 
@@ -586,23 +604,18 @@ cudaError_t launch_plainv(const SweepArgs<T> &a, cudaStream_t st, int num_sms) {
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, 32 * WY, TL::smem);
     if (per_sm < 1) per_sm = 1;
     const int gx = (a.g.nx + R - TL::OS + TL::TX - 1) / TL::TX, gy = (a.g.ny + TL::TY - 1) / TL::TY;
-    // z chunks: minimise (waves of resident CTAs) x (planes per chunk incl. the 2R re-read)
-    const int64_t resident = (int64_t)num_sms * per_sm, tiles = (int64_t)gx * gy;
-    int best = 1;
-    double best_cost = 1e300;
-    for (int nzc = 1; nzc <= a.g.nz; ++nzc) {
-        const int chunk = (a.g.nz + nzc - 1) / nzc;
-        if (nzc > 1 && chunk < 4 * R) break;
-        const int64_t ctas = tiles * ((a.g.nz + chunk - 1) / chunk);
-        const double cost = (double)((ctas + resident - 1) / resident) * (chunk + 2 * R);
-        if (cost < best_cost * 0.999) { best_cost = cost; best = nzc; }
-    }
     SweepArgs<T> b = a;
-    b.zchunk = (a.g.nz + best - 1) / best;
+    b.zchunk = pv::pick_zchunk(a.g.nz, R, (int64_t)gx * gy, (int64_t)num_sms * per_sm);
     dim3 grid(gx, gy, (a.g.nz + b.zchunk - 1) / b.zchunk), block(32, WY, 1);
     kern<<<grid, block, TL::smem, st>>>(b, tm_u, tm_p, tm_a);
     return cudaGetLastError();
 }
+
+}  // namespace stc
+
+#include "adjt_impl.cuh"
+
+namespace stc {
 
 template <typename T, bool TMA>
 cudaError_t launch_plainv_kind_t(int kind, bool adjoint, const SweepArgs<T> &a, bool big, cudaStream_t st,
@@ -612,9 +625,11 @@ cudaError_t launch_plainv_kind_t(int kind, bool adjoint, const SweepArgs<T> &a, 
         // source-point coefficients reach 4 rows up and down, which 8-row
         // tiles keep in L1 more often (measured: 142.7 vs 150.2 ms for the
         // 256^3 forward+adjoint backward pass)
+        // with TMA staging the 13-array kinds run the staged-coefficient
+        // adjoint (adjt_impl.cuh)
         switch (kind) {
-        case W25_VAR: return launch_plainv<T, W25_VAR, 8, true, TMA>(a, st, num_sms);
-        case J25_VAR: return launch_plainv<T, J25_VAR, 8, true, TMA>(a, st, num_sms);
+        case W25_VAR: return TMA ? launch_adjt<T, W25_VAR, 8>(a, st, num_sms) : launch_plainv<T, W25_VAR, 8, true, false>(a, st, num_sms);
+        case J25_VAR: return TMA ? launch_adjt<T, J25_VAR, 8>(a, st, num_sms) : launch_plainv<T, J25_VAR, 8, true, false>(a, st, num_sms);
         case W25_ALPHA: return big ? launch_plainv<T, W25_ALPHA, 4, true, TMA>(a, st, num_sms) : launch_plainv<T, W25_ALPHA, 8, true, TMA>(a, st, num_sms);
         case W25_CONST: break;
         default: return cudaErrorNotSupported;
