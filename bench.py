@@ -369,7 +369,21 @@ def roofline_of(pm, kind, dtype_name, n, res, peak_f64, hbm_peak, fp32_peak):
             "alu_view": {"achieved_tflops": flops_pass / t_pass / 1e12, "peak_tflops": fp32_peak / 1e12}}
 
 
-def fwd_adj_case(torch, st, wl, n, T, K, dtype, steps, warmup, ws, stream, fw=None, variant=None):
+def fwd_adj_bytes_per_lup(elem, T, K, grad_batch):
+    """Algorithmic HBM bytes per lattice update of one forward + backward of
+    the 25-point variable wave: the forward sweep, the recompute of every
+    segment but the last (whose states the forward pass keeps) and the
+    adjoint sweep each read two fields and the 13 coefficient arrays and
+    write one field; the gradient reads the adjoint level and the state of
+    every step and reads and writes the 13 FP64 gradient arrays once per
+    batch of grad_batch steps."""
+    sweep = 16 * elem
+    nseg = (T + K - 1) // K
+    recomputed = (T - (T - (nseg - 1) * K)) / T
+    return sweep * (2 + recomputed) + 2 * elem + 13 * 16 / grad_batch
+
+
+def fwd_adj_case(torch, st, wl, n, T, K, dtype, steps, warmup, ws, stream, fw=None, variant=None, hbm_peak=None):
     """Differentiable 25-point variable wave workload: one step = the
     checkpointed forward (T steps, state pair kept every K steps, receiver
     trace, FP64 misfit) plus the backward (recompute of every segment and the
@@ -417,6 +431,13 @@ def fwd_adj_case(torch, st, wl, n, T, K, dtype, steps, warmup, ws, stream, fw=No
            "forward_ms": t_f / steps, "backward_ms": t_b / steps,
            "forward_glups": lups / (t_f / steps * 1e-3) / 1e9, "loss": float(loss.item()),
            "time_block": run.plan.get(st.OPT_TIME_BLOCK), "variant": run.plan.get(st.OPT_VARIANT)}
+    if hbm_peak:
+        bpl = fwd_adj_bytes_per_lup(4 if dtype == st.F32 else 8, T, K, run.plan.get(st.OPT_GRAD_BATCH))
+        ach = res["glups"] / ws * bpl
+        res["roofline"] = {"bound": "hbm", "bytes_per_lup": bpl, "achieved": ach, "peak": hbm_peak, "unit": "GB/s",
+                           "frac": ach / hbm_peak,
+                           "note": "algorithmic bytes of forward + recompute + adjoint + gradient"
+                                   + ("" if dtype == st.F32 else "; FP64 is bound by the FP64 pipe")}
     run.close()
     del u0, W, d
     torch.cuda.empty_cache()
@@ -480,7 +501,7 @@ def run_ours(args):
         return
     if args.fwd_adj:
         r, _ = fwd_adj_case(torch, st, wl, n, T, 20, dtype, args.steps, args.warmup, ws, stream,
-                            variant=args.variant)
+                            variant=args.variant, hbm_peak=hbm_peak)
         print(json.dumps({"fwd_adj": r}), flush=True)
         return
     dev_index = torch.cuda.current_device()
@@ -538,7 +559,7 @@ def run_ours(args):
         # forward + adjoint of the differentiable wave workload (256^3, T = 200, K = 20)
         fw = None
         for vd in (st.F32, st.F64):
-            r, fw = fwd_adj_case(torch, st, wl, 256, 200, 20, vd, 1, 1, ws, stream, fw=fw)
+            r, fw = fwd_adj_case(torch, st, wl, 256, 200, 20, vd, 1, 1, ws, stream, fw=fw, hbm_peak=hbm_peak)
             variants.append(r)
 
     cpu = None

@@ -10,15 +10,16 @@
 // brings, into one shared slot and by one thread's bulk tensor copies:
 //   the y tile of plane p with its x and y halos,
 //   the 4 x-axis coefficient tiles of plane p with x halos (own rows),
-//   the 4 y-axis coefficient tiles of plane p with y halos (own columns),
-//   the centre and the 4 z-axis coefficient tiles of plane p (own points),
-//   y_prev of plane p (own points; second-order kind).
+//   the 4 y-axis coefficient tiles of plane p with y halos (own columns);
+// the inputs of the thread's own points -- the centre and the 4 z-axis
+// coefficients of plane p and y_prev (second-order kind) -- are 16-byte
+// loads into registers issued while the thread waits for plane p.
 // Every term of output plane p that reads plane p only -- the centre, the x
 // and y terms, 2 y(p) - y_prev(p) -- is summed when plane p arrives.  The z
 // terms are pushed: A_{z,r}(p) y(p) is added to the partial sums of output
 // planes p - r and p + r (a register ring of 2R+1 partial sums), so output
-// plane p - R is complete once plane p has arrived.  Two slots: the copies
-// of plane p + 1 run while plane p is summed.
+// plane p - R is complete once plane p has arrived.  Three slots: the copies
+// of planes p + 1 and p + 2 run while plane p is summed.
 #pragma once
 
 namespace stc {
@@ -35,19 +36,15 @@ struct AdjTile {
     static constexpr int SW = TX + 2 * RH, SH = TY + 2 * R;
     // region sizes rounded to 128 bytes (TMA destinations)
     static constexpr int al(int n) { return (int)((n * sizeof(T) + 127) / 128 * 128 / sizeof(T)); }
-    static constexpr int CXS = al(SW * TY), CYS = al(TX * SH), PPS = al(TX * TY);
+    static constexpr int CXS = al(SW * TY), CYS = al(TX * SH);
     // element offsets of the regions of a slot
     static constexpr int LAM = 0;                    // [SH][SW]
     static constexpr int CX = LAM + al(SW * SH);     // 4 x [TY][SW]
     static constexpr int CY = CX + 4 * CXS;          // 4 x [SH][TX]
-    static constexpr int C0 = CY + 4 * CYS;          // [TY][TX]
-    static constexpr int CZ = C0 + PPS;              // 4 x [TY][TX]
-    static constexpr int LP = CZ + 4 * PPS;          // [TY][TX]
-    static constexpr int SLOT = LP + PPS;
-    static constexpr int NSLOT = 2;
+    static constexpr int SLOT = CY + 4 * CYS;
+    static constexpr int NSLOT = 3;
     // bytes one plane's copies deliver (the boxes, zero fill included)
-    static constexpr uint32_t BYTES = (uint32_t)sizeof(T) * (SW * SH + 4 * SW * TY + 4 * TX * SH + 5 * TX * TY);
-    static constexpr uint32_t BYTES_LP = (uint32_t)sizeof(T) * TX * TY;
+    static constexpr uint32_t BYTES = (uint32_t)sizeof(T) * (SW * SH + 4 * SW * TY + 4 * TX * SH);
     static constexpr size_t smem = sizeof(T) * (size_t)NSLOT * SLOT + 8 * NSLOT + 128;
     static_assert((sizeof(T) * SLOT) % 128 == 0, "128-byte aligned slots");
 };
@@ -57,8 +54,7 @@ struct AdjTile {
 template <typename T, int KIND, int WY>
 __global__ void __launch_bounds__(32 * WY, 1)
 adjt_kernel(const SweepArgs<T> a, const __grid_constant__ CUtensorMap tm_lam, const __grid_constant__ CUtensorMap tm_cx,
-            const __grid_constant__ CUtensorMap tm_cy, const __grid_constant__ CUtensorMap tm_cp,
-            const __grid_constant__ CUtensorMap tm_lp) {
+            const __grid_constant__ CUtensorMap tm_cy) {
     using TL = pv::AdjTile<T, WY>;
     constexpr int R = TL::R, V = TL::V, TX = TL::TX, SW = TL::SW, RH = TL::RH, OS = TL::OS;
     constexpr int NH = RH / V;                   // halo vectors on each side
@@ -67,7 +63,6 @@ adjt_kernel(const SweepArgs<T> a, const __grid_constant__ CUtensorMap tm_lam, co
     extern __shared__ __align__(128) unsigned char smem_raw[];
     T *const sb = reinterpret_cast<T *>((reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
     uint64_t *const bars = reinterpret_cast<uint64_t *>(sb + TL::NSLOT * TL::SLOT);
-    (void)tm_lp;
 
     const Geom &g = a.g;
     const int lane = threadIdx.x, w = threadIdx.y, tid = w * 32 + lane;
@@ -84,24 +79,46 @@ adjt_kernel(const SweepArgs<T> a, const __grid_constant__ CUtensorMap tm_lam, co
     const int olam = (R + w) * SW + RH + lane * V;   // own vector in the y tile
     const int ocx = w * SW + RH + lane * V;          // ... in an x-axis tile
     const int ocy = (R + w) * TX + lane * V;         // ... in a y-axis tile
-    const int opp = w * TX + lane * V;               // ... in a per-point tile
 
     // all copies of plane p (interior index) into slot s
     auto issue = [&](int p, int s) {
         T *d = sb + s * TL::SLOT;
         uint64_t *bar = &bars[s];
         const int zp = p + R;   // padded plane
-        pv::mbar_expect_tx(bar, WAVE ? TL::BYTES + TL::BYTES_LP : TL::BYTES);
+        pv::mbar_expect_tx(bar, TL::BYTES);
         pv::tma_load_3d(d + TL::LAM, &tm_lam, x0, y0, zp, bar);
-        pv::tma_load_3d(d + TL::C0, &tm_cp, xo, y0 + R, zp, bar);
 #pragma unroll
         for (int r = 1; r <= 4; ++r) {
-            // array 3(r-1)+1: x axis, 3(r-1)+2: y axis, 3r: z axis
+            // array 3(r-1)+1: x axis, 3(r-1)+2: y axis
             pv::tma_load_3d(d + TL::CX + (r - 1) * TL::CXS, &tm_cx, x0, y0 + R, (3 * r - 2) * pz + zp, bar);
             pv::tma_load_3d(d + TL::CY + (r - 1) * TL::CYS, &tm_cy, xo, y0, (3 * r - 1) * pz + zp, bar);
-            pv::tma_load_3d(d + TL::CZ + (r - 1) * TL::PPS, &tm_cp, xo, y0 + R, 3 * r * pz + zp, bar);
         }
-        if constexpr (WAVE) pv::tma_load_3d(d + TL::LP, &tm_lp, xo, y0 + R, zp, bar);
+    };
+    // own-point inputs of plane p: z-axis coefficients (array 3r) where p is
+    // interior, the centre coefficient and y_prev where p is an output plane
+    // of this chunk (y_prev may be the output array: only the chunk's own
+    // planes are read, each before it is written)
+    T pc0[V], pcz[4][V], plp[V];
+    auto load_own = [&](int p) {
+        const bool inz = own && p >= 0 && p < g.nz;
+        const bool inc = own && p >= z0 && p < z1;
+        const int64_t zo = (int64_t)(p + R) * g.sz + poff;
+#pragma unroll
+        for (int r = 1; r <= 4; ++r) {
+            if (inz) {
+                pv::ldg16<T>(pcz[r - 1], a.W + 3 * r * g.nfield + zo);
+            } else {
+#pragma unroll
+                for (int i = 0; i < V; ++i) pcz[r - 1][i] = T(0);
+            }
+        }
+        if (inc) {
+            pv::ldg16<T>(pc0, a.W + zo);
+            if constexpr (WAVE) pv::ld16<T>(plp, a.u_prev + zo);
+        } else {
+#pragma unroll
+            for (int i = 0; i < V; ++i) pc0[i] = plp[i] = T(0);
+        }
     };
 
     T acc[RING][V];   // partial sums of output planes p - R .. p + R (slot of plane p: its ring index)
@@ -113,21 +130,26 @@ adjt_kernel(const SweepArgs<T> a, const __grid_constant__ CUtensorMap tm_lam, co
     if (tid < TL::NSLOT) pv::mbar_init(&bars[tid], 1);
     pv::mbar_init_fence();
     __syncthreads();
-    if (tid == 0) issue(qs, 0);
+    if (tid == 0) {
+        issue(qs, 0);
+        if (qs + 1 < qe) issue(qs + 1, 1);
+    }
+    load_own(qs);
+    static_assert(RING % TL::NSLOT == 0, "slot of plane p: j mod NSLOT");
 
     for (int pb = qs; pb < qe; pb += RING) {
         static_for<RING>([&](auto jj) {
             constexpr int j = decltype(jj)::value;
+            constexpr int s = j % TL::NSLOT;
             const int p = pb + j;
             if (p >= qe) return;
-            const int s = (p - qs) & 1;
             // k-th use of a slot completes phase k (parity k & 1)
-            if (!pv::mbar_wait(&bars[s], (uint32_t)(((p - qs) >> 1) & 1))) {
+            if (!pv::mbar_wait(&bars[s], (uint32_t)(((p - qs) / TL::NSLOT) & 1))) {
                 atomicAdd(&g_wait_timeouts, 1u);
                 return;
             }
-            __syncthreads();   // every thread is done with the other slot (plane p - 1)
-            if (tid == 0 && p + 1 < qe) issue(p + 1, s ^ 1);
+            __syncthreads();   // every thread is done with plane p - 1's slot
+            if (tid == 0 && p + 2 < qe) issue(p + 2, (j + 2) % TL::NSLOT);
             const T *sl = sb + s * TL::SLOT;
             if (own && p >= 0 && p < g.nz) {
                 T lc[V];
@@ -135,11 +157,9 @@ adjt_kernel(const SweepArgs<T> a, const __grid_constant__ CUtensorMap tm_lam, co
                 // z terms with source plane p
 #pragma unroll
                 for (int r = 1; r <= 4; ++r) {
-                    T cz[V];
-                    pv::ld16<T>(cz, sl + TL::CZ + (r - 1) * TL::PPS + opp);
 #pragma unroll
                     for (int i = 0; i < V; ++i) {
-                        const T v = cz[i] * lc[i];
+                        const T v = pcz[r - 1][i] * lc[i];
                         acc[cmod(j - r, RING)][i] += v;
                         acc[cmod(j + r, RING)][i] += v;
                     }
@@ -147,17 +167,11 @@ adjt_kernel(const SweepArgs<T> a, const __grid_constant__ CUtensorMap tm_lam, co
                 if (p >= z0 && p < z1) {
                     // terms of output plane p that read plane p only
                     T t[V];
-                    {
-                        T c0[V];
-                        pv::ld16<T>(c0, sl + TL::C0 + opp);
 #pragma unroll
-                        for (int i = 0; i < V; ++i) t[i] = c0[i] * lc[i];
-                        if constexpr (WAVE) {
-                            T lp[V];
-                            pv::ld16<T>(lp, sl + TL::LP + opp);
+                    for (int i = 0; i < V; ++i) t[i] = pc0[i] * lc[i];
+                    if constexpr (WAVE) {
 #pragma unroll
-                            for (int i = 0; i < V; ++i) t[i] = fma(T(2), lc[i], t[i]) - lp[i];
-                        }
+                        for (int i = 0; i < V; ++i) t[i] = fma(T(2), lc[i], t[i]) - plp[i];
                     }
                     // y vectors left and right of the own one (RH columns each side)
                     T ll[NH][V], lr[NH][V];
@@ -221,6 +235,7 @@ adjt_kernel(const SweepArgs<T> a, const __grid_constant__ CUtensorMap tm_lam, co
             }
 #pragma unroll
             for (int i = 0; i < V; ++i) acc[jz][i] = T(0);   // now the slot of plane p + R + 1
+            if (p + 1 < qe) load_own(p + 1);
         });
     }
 }
@@ -231,17 +246,13 @@ cudaError_t launch_adjt(const SweepArgs<T> &a, cudaStream_t st, int num_sms) {
     constexpr int R = TL::R, NA = KindTraits<KIND>::NARR;
     static_assert(NA == 13, "13-array kinds");
     auto kern = adjt_kernel<T, KIND, WY>;
-    CUtensorMap m_lam, m_cx, m_cy, m_cp, m_lp;
+    CUtensorMap m_lam, m_cx, m_cy;
     memset(&m_lam, 0, sizeof(m_lam));
     memset(&m_cx, 0, sizeof(m_cx));
     memset(&m_cy, 0, sizeof(m_cy));
-    memset(&m_cp, 0, sizeof(m_cp));
-    memset(&m_lp, 0, sizeof(m_lp));
     cudaError_t e = pv::make_tmap(&m_lam, a.u, sizeof(T), a.g, TL::SW, TL::SH);
     if (e == cudaSuccess) e = pv::make_tmap(&m_cx, a.W, sizeof(T), a.g, TL::SW, TL::TY, NA);
     if (e == cudaSuccess) e = pv::make_tmap(&m_cy, a.W, sizeof(T), a.g, TL::TX, TL::SH, NA);
-    if (e == cudaSuccess) e = pv::make_tmap(&m_cp, a.W, sizeof(T), a.g, TL::TX, TL::TY, NA);
-    if (e == cudaSuccess && KindTraits<KIND>::WAVE) e = pv::make_tmap(&m_lp, a.u_prev, sizeof(T), a.g, TL::TX, TL::TY);
     if (e != cudaSuccess) return e;
     static_assert(TL::smem <= 227 * 1024, "shared memory per CTA");
     e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TL::smem);
@@ -251,9 +262,13 @@ cudaError_t launch_adjt(const SweepArgs<T> &a, cudaStream_t st, int num_sms) {
     if (per_sm < 1) per_sm = 1;
     const int gx = (a.g.nx + R - TL::OS + TL::TX - 1) / TL::TX, gy = (a.g.ny + TL::TY - 1) / TL::TY;
     SweepArgs<T> b = a;
-    b.zchunk = pv::pick_zchunk(a.g.nz, R, (int64_t)gx * gy, (int64_t)num_sms * per_sm);
+    // FP32: HBM-bound, fewest chunks (measured at 256^3: 2 chunks of 128
+    // planes 121.8 ms for the backward pass against 123.7 with the 7 chunks
+    // of the wave-count choice); FP64: bound by the FP64 pipe, every SM busy
+    b.zchunk = sizeof(T) == 4 ? pv::pick_zchunk_traffic(a.g.nz, R, (int64_t)gx * gy, (int64_t)num_sms * per_sm)
+                              : pv::pick_zchunk(a.g.nz, R, (int64_t)gx * gy, (int64_t)num_sms * per_sm);
     dim3 grid(gx, gy, (a.g.nz + b.zchunk - 1) / b.zchunk), block(32, WY, 1);
-    kern<<<grid, block, TL::smem, st>>>(b, m_lam, m_cx, m_cy, m_cp, m_lp);
+    kern<<<grid, block, TL::smem, st>>>(b, m_lam, m_cx, m_cy);
     return cudaGetLastError();
 }
 

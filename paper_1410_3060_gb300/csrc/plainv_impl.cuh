@@ -580,6 +580,20 @@ inline int pick_zchunk(int nz, int R, int64_t tiles, int64_t resident) {
     }
     return (nz + best - 1) / best;
 }
+
+// Interior planes per z chunk for an HBM-bound kernel: the fewest chunks
+// (the least re-read of 2R planes per chunk) that still give 80% of the
+// resident CTA slots a CTA.
+inline int pick_zchunk_traffic(int nz, int R, int64_t tiles, int64_t resident) {
+    int chunk = nz;
+    for (int nzc = 1; nzc <= nz; ++nzc) {
+        const int c = (nz + nzc - 1) / nzc;
+        if (nzc > 1 && c < 4 * R) break;
+        chunk = c;
+        if (tiles * ((nz + c - 1) / c) * 5 >= resident * 4) break;
+    }
+    return chunk;
+}
 }  // namespace pv
 
 template <typename T, int KIND, int WY, bool ADJ = false, bool TMA = false>

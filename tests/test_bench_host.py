@@ -31,6 +31,16 @@ def test_fp32_roofline_counts_bytes_once_per_pass(bench):
     assert abs(r["frac"] - expect_gbs / 6788.6) < 1e-12
 
 
+def test_fwd_adj_bytes_per_update(bench):
+    """Forward + backward of the 25-point variable wave, FP32, T = 200 in
+    segments of 20 (the last kept, 180 steps recomputed), gradient batches of
+    16: 64 B forward + 0.9 x 64 B recompute + 64 B adjoint + 8 B gradient
+    reads + 13 x 16 / 16 B of FP64 read-modify-write per update."""
+    assert abs(bench.fwd_adj_bytes_per_lup(4, 200, 20, 16) - (64 + 57.6 + 64 + 8 + 13)) < 1e-12
+    # one segment: nothing is recomputed
+    assert abs(bench.fwd_adj_bytes_per_lup(8, 20, 20, 1) - (128 + 128 + 16 + 208)) < 1e-12
+
+
 def test_fp64_roofline_flops_and_pipe_views(bench):
     """FP64: flops (FMA = 2) against 2 FMA/clk/SM x SMs x clock, and the
     FP64 instruction view (adds count as a full pipe slot)."""
