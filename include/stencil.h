@@ -112,10 +112,12 @@ enum stencil_option {
        25-point kinds with 16-byte vectors along x, 8 and 16 rows per CTA
        (4 rows for the 13-array kinds; needs nx a multiple of 4 in FP32, of
        2 in FP64), 15 and 16 = the same tiles staged by TMA (one tensor copy
-       per plane tile, mbarrier completion).  A variant a kind or geometry
-       cannot use runs the default streaming tile.  The default is the measured best: 12 / 11 for FP32
-       J7_CONST / J7_VAR, 15 for FP32 W25_CONST and W25_ALPHA, 16 for
-       W25_VAR and J25_VAR, else a streaming tile. */
+       per plane tile, mbarrier completion; the adjoint of W25_VAR and
+       J25_VAR then stages every coefficient tile by TMA as well).  A variant
+       a kind or geometry cannot use runs the default streaming tile.  The
+       default is the measured best: 12 / 11 for FP32 J7_CONST / J7_VAR, 15
+       for FP32 W25_CONST, 16 for FP32 W25_ALPHA and for W25_VAR and
+       J25_VAR, else a streaming tile. */
     STENCIL_OPT_VARIANT = 5,
     /* 1: stencil_forward captures its pass program (every launch and copy of
        the T steps) into a CUDA graph the first time it sees an argument set

@@ -239,7 +239,9 @@ int plan_variant(const stencil_plan_s *p) {
     if (vec) {
         const bool arrays13 = p->kind == W25_VAR || p->kind == J25_VAR;
         if (arrays13) return 16;
-        if (p->dtype == 1) return 15;
+        // FP32 at 512^3: constant wave 449 (15) vs 414 (16) GLUP/s; alpha-array
+        // wave 332 (16) vs 292 (15)
+        if (p->dtype == 1) return p->kind == W25_ALPHA ? 16 : 15;
     }
     return default_variant(p->kind, p->dtype);
 }

@@ -77,12 +77,17 @@ struct Tile {
     // their coefficients directly
     static constexpr int NPS = (KindTraits<KIND>::WAVE ? 1 : 0) + ((KindTraits<KIND>::NARR == 1 && !ADJ) ? 1 : 0);
     static constexpr int PP = TX * TY;           // one per-point plane
+    static constexpr size_t smem_of(int pd) {
+        return sizeof(T) * ((size_t)(R + 1 + pd) * SP + (size_t)(R + 1 + pd) * NPS * PP) + 8 * (R + 1 + pd) + 128;
+    }
     // planes in flight: one more with TMA (its copies take no registers) for
-    // the constant wave (measured: 448 vs 402 GLUP/s at 512^3; the 13-array
-    // kinds run slower with the larger ring)
-    static constexpr int PD = (TMA && NPS == 1 && KindTraits<KIND>::NARR == 0) ? 3 : 2;
+    // the constant wave (measured: 448 vs 402 GLUP/s at 512^3) and the
+    // forward of the alpha-array wave, where the larger ring fits; the
+    // 13-array kinds run slower with it
+    static constexpr bool DEEP = TMA && !ADJ && KindTraits<KIND>::NARR <= 1 && KindTraits<KIND>::WAVE;
+    static constexpr int PD = (DEEP && smem_of(3) <= 227 * 1024) ? 3 : 2;
     static constexpr int NS = R + 1 + PD;        // shared plane slots
-    static constexpr size_t smem = sizeof(T) * ((size_t)NS * SP + (size_t)NS * NPS * PP) + 8 * NS + 128;
+    static constexpr size_t smem = smem_of(PD);
     static_assert((sizeof(T) * SP) % 128 == 0 && (sizeof(T) * PP) % 128 == 0, "128-byte aligned slots");
     static constexpr int MINB = 1;
 };
