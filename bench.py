@@ -257,19 +257,23 @@ def forward_case(torch, st, wl, kind, n, T, dtype, steps, warmup, ws, stream, ti
         hout = torch.empty_like(hu).pin_memory()
         h2d = hp.numel() * hp.element_size() * 2 + (hW.numel() * hW.element_size() if hW is not None else 0)
         d2h = hout.numel() * hout.element_size()
-        # two device input sets: the host->device copy of step i+1's inputs and
-        # the device->host read of step i-1's result run on a copy stream while
-        # step i's sweeps run (every step still copies its own inputs and reads
-        # its own result inside the timed region)
+        # two device input sets: the host->device copy of step i+1's inputs
+        # (on one copy stream) and the device->host read of step i-1's result
+        # (on another: the link carries both directions at once) run while
+        # step i's sweeps run (every step still copies its own inputs and
+        # reads its own result inside the timed region)
         sets = [(up, u, W), (torch.empty_like(up), torch.empty_like(u), torch.empty_like(W) if W is not None else None)]
-        cs = torch.cuda.Stream()
+        cs, rs = torch.cuda.Stream(), torch.cuda.Stream()
         copied = [torch.cuda.Event(), torch.cuda.Event()]
         done = [None, None]
+        read = [None, None]
 
         def copy_inputs(k):
             with torch.cuda.stream(cs):
                 if done[k] is not None:
                     cs.wait_event(done[k])          # the sweeps that last read this set are finished
+                if read[k] is not None:
+                    cs.wait_event(read[k])          # and so is the read of their result
                 p_, u_, W_ = sets[k]
                 p_.copy_(hp, non_blocking=True)
                 u_.copy_(hu, non_blocking=True)
@@ -291,10 +295,12 @@ def forward_case(torch, st, wl, kind, n, T, dtype, steps, warmup, ws, stream, ti
                 ev = torch.cuda.Event()
                 ev.record(stream)
                 done[k] = ev
-                with torch.cuda.stream(cs):
-                    cs.wait_event(ev)
+                with torch.cuda.stream(rs):
+                    rs.wait_event(ev)
                     hout.copy_(u_, non_blocking=True)
+                    read[k] = rs.record_event()
             stream.wait_stream(cs)
+            stream.wait_stream(rs)
         barrier(torch, ws)
         del sets
         ms_e = max_over_ranks(torch, ws, te.ms)

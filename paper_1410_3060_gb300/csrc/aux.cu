@@ -111,7 +111,7 @@ __global__ void __launch_bounds__(256) grad_kernel(const GradArgs<T> a) {
 // sums instead of 13, so that an SM keeps about three times as many warps,
 // and loads, in flight.
 template <typename T, int TY>
-__global__ void __launch_bounds__(96 * TY, sizeof(T) == 4 ? 4 : 3) grad_axis_kernel(const GradArgs<T> a) {
+__global__ void __launch_bounds__(96 * TY, TY == 8 ? 2 : 3) grad_axis_kernel(const GradArgs<T> a) {
     constexpr int R = 4;
     const Geom g = a.g;
     const int x = blockIdx.x * 32 + threadIdx.x;
@@ -173,7 +173,9 @@ __global__ void __launch_bounds__(96 * TY, sizeof(T) == 4 ? 4 : 3) grad_axis_ker
 template <typename T>
 cudaError_t launch_grad(int kind, const GradArgs<T> &a, cudaStream_t st) {
     if (kind == W25_VAR || kind == J25_VAR) {
-        constexpr int TY = 4;
+        // FP32: 8 rows per CTA (the y neighbours of more rows stay in the
+        // CTA); FP64: 4 rows (its 56 registers a thread allow three CTAs)
+        constexpr int TY = sizeof(T) == 4 ? 8 : 4;
         dim3 block(32, TY, 3), grid((a.g.nx + 31) / 32, (a.g.ny + TY - 1) / TY, a.g.nz);
         grad_axis_kernel<T, TY><<<grid, block, 0, st>>>(a);
         return cudaGetLastError();
