@@ -120,6 +120,41 @@ def test_adjoint_with_residual_and_gradient(st, kind, dtype, variant):
     plan.close()
 
 
+@pytest.mark.parametrize("kind", [4, 5])
+@pytest.mark.parametrize("dtype", [F64, F32])
+def test_adjoint_tiles_and_chunks(st, kind, dtype):
+    """The default adjoint of the 13-array kinds (TMA-staged coefficients)
+    over several x tiles (the last one ragged), ragged y tiles and several z
+    chunks (the last one shorter), with the gradient; against the oracle."""
+    import torch
+    rng = np.random.default_rng(40 + kind)
+    n = (264, 40, 70)
+    T = 3
+    wk = wl.make(kind, n, T, seed=5)
+    R = wk.R
+    l2, l1 = rand_interior(n, R, rng), rand_interior(n, R, rng)
+    states = np.stack([rand_interior(n, R, rng) for _ in range(T)])
+    res = rng.uniform(-1, 1, size=(T, n[1], n[0]))
+    rz = 33
+    cast = (lambda a: a.astype(np.float32).astype(np.float64)) if dtype == F32 else (lambda a: a)
+    og = np.zeros((13,) + l1.shape)
+    ol2, ol1 = oracle.adjoint(kind, cast(l2), cast(l1), wk.w, cast(wk.W), T, states=cast(states),
+                              residual=cast(res), rcv_z=rz, grad=og, threads=8)
+    plan = st.Plan(kind, *n, dtype)
+    assert plan.get(st.OPT_VARIANT) == 16
+    gl2, gl1 = to_dev(l2, dtype), to_dev(l1, dtype)
+    gg = torch.zeros((13,) + l1.shape, device="cuda", dtype=torch.float64)
+    plan.adjoint(gl2, gl1, wk.w, to_dev(wk.W, dtype), T, fwd_states=[to_dev(s_, dtype) for s_ in states],
+                 residual=to_dev(res, dtype), rcv_z=rz, grad=gg)
+    torch.cuda.synchronize()
+    tol = 1e-12 if dtype == F64 else 2e-5
+    assert normwise_err(to_np(gl1), ol1) <= tol
+    assert normwise_err(to_np(gl2), ol2) <= tol
+    assert normwise_err(to_np(gg), og) <= tol
+    assert st.wait_timeouts() == 0
+    plan.close()
+
+
 @pytest.mark.parametrize("dtype", [F64, F32])
 def test_misfit(st, dtype):
     import torch
