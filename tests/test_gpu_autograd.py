@@ -50,10 +50,14 @@ def test_forward_states(st, kind, dtype):
 
 @pytest.mark.parametrize("kind", [2, 4, 5, 6])
 @pytest.mark.parametrize("batch", [3, 8])
-def test_batched_gradient_matches_oracle(st, kind, batch):
+@pytest.mark.parametrize("nx", [37, 40])
+def test_batched_gradient_matches_oracle(st, kind, batch, nx):
+    """Gradient batches of 3 and 8 steps over 9 steps; nx = 40 gives the
+    13-array kinds the shared-memory tiled gradient kernel for batches of 8
+    steps (the rest: one thread per point and axis)."""
     import torch
     rng = np.random.default_rng(20 + kind)
-    n, T, rz = (37, 29, 21), 7, 6
+    n, T, rz = (nx, 29, 21), 9, 6
     wk = wl.make(kind, n, T, seed=5)
     R = wk.R
     l2, l1 = rand_interior(n, R, rng), rand_interior(n, R, rng)

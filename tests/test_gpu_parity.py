@@ -125,11 +125,12 @@ def test_adjoint_with_residual_and_gradient(st, kind, dtype, variant):
 def test_adjoint_tiles_and_chunks(st, kind, dtype):
     """The default adjoint of the 13-array kinds (TMA-staged coefficients)
     over several x tiles (the last one ragged), ragged y tiles and several z
-    chunks (the last one shorter), with the gradient; against the oracle."""
+    chunks (the last one shorter), with the gradient in a batch of 8 steps
+    (the shared-memory tiled kernel) and one of 1; against the oracle."""
     import torch
     rng = np.random.default_rng(40 + kind)
     n = (264, 40, 70)
-    T = 3
+    T = 9
     wk = wl.make(kind, n, T, seed=5)
     R = wk.R
     l2, l1 = rand_interior(n, R, rng), rand_interior(n, R, rng)
@@ -142,6 +143,7 @@ def test_adjoint_tiles_and_chunks(st, kind, dtype):
                               residual=cast(res), rcv_z=rz, grad=og, threads=8)
     plan = st.Plan(kind, *n, dtype)
     assert plan.get(st.OPT_VARIANT) == 16
+    plan.set(st.OPT_GRAD_BATCH, 8)
     gl2, gl1 = to_dev(l2, dtype), to_dev(l1, dtype)
     gg = torch.zeros((13,) + l1.shape, device="cuda", dtype=torch.float64)
     plan.adjoint(gl2, gl1, wk.w, to_dev(wk.W, dtype), T, fwd_states=[to_dev(s_, dtype) for s_ in states],
