@@ -52,7 +52,10 @@ __device__ __forceinline__ void grad_terms(const T *u, const T l, const Geom &g,
 // (the fields are FP32) and sum the terms of the batch with compensated
 // (Kahan) FP32 summation -- error of a few FP32 roundings of the batch sum,
 // the order of the rounding of the FP32 terms themselves -- then add the
-// batch sum to the FP64 gradient: the sum over time is carried in FP64.
+// batch sum, rounded once to FP32 (sum - compensation: one more rounding of
+// the batch sum), to the FP64 gradient: the sum over time is carried in
+// FP64.  GB300 runs FP64 at 2 operations per clock per SM, so the epilogue
+// takes one conversion and one FP64 add per array.
 template <typename T, int KIND>
 __global__ void __launch_bounds__(256) grad_kernel(const GradArgs<T> a) {
     constexpr int R = KindTraits<KIND>::R;
@@ -100,7 +103,7 @@ __global__ void __launch_bounds__(256) grad_kernel(const GradArgs<T> a) {
         }
 #pragma unroll
         for (int k = 0; k < NA; ++k)
-            a.grad[(int64_t)k * g.nfield + idx] += (double)sum[k] - (double)cmp[k];
+            a.grad[(int64_t)k * g.nfield + idx] += (double)__fsub_rn(sum[k], cmp[k]);
     }
 }
 
@@ -163,7 +166,7 @@ __global__ void __launch_bounds__(96 * TY, TY == 8 ? 2 : 3) grad_axis_kernel(con
             for (int k = 0; k < 5; ++k) d[k] = dn[k];
         }
 #pragma unroll
-        for (int k = 0; k < 5; ++k) out[k] = (double)sum[k] - (double)cmp[k];
+        for (int k = 0; k < 5; ++k) out[k] = (double)__fsub_rn(sum[k], cmp[k]);
     }
 #pragma unroll
     for (int r = 1; r <= 4; ++r) a.grad[(int64_t)(3 * (r - 1) + ax + 1) * g.nfield + idx] += out[r - 1];
@@ -299,7 +302,7 @@ __global__ void __launch_bounds__(GT_X * GT_Y) grad_tile_kernel(const GradArgs<T
     const int64_t idx = zc + (int64_t)(y0 + R + ly) * g.sy + (x0 + R + lx);
 #pragma unroll
     for (int k = 0; k < 13; ++k)
-        a.grad[(int64_t)k * g.nfield + idx] += sizeof(T) == 8 ? acc[k] : (double)sum[k] - (double)cmp[k];
+        a.grad[(int64_t)k * g.nfield + idx] += sizeof(T) == 8 ? acc[k] : (double)__fsub_rn(sum[k], cmp[k]);
 }
 
 template <typename T>
