@@ -262,11 +262,18 @@ cudaError_t launch_adjt(const SweepArgs<T> &a, cudaStream_t st, int num_sms) {
     if (per_sm < 1) per_sm = 1;
     const int gx = (a.g.nx + R - TL::OS + TL::TX - 1) / TL::TX, gy = (a.g.ny + TL::TY - 1) / TL::TY;
     SweepArgs<T> b = a;
-    // FP32: HBM-bound, fewest chunks (measured at 256^3: 2 chunks of 128
-    // planes 121.8 ms for the backward pass against 123.7 with the 7 chunks
-    // of the wave-count choice); FP64: bound by the FP64 pipe, every SM busy
-    b.zchunk = sizeof(T) == 4 ? pv::pick_zchunk_traffic(a.g.nz, R, (int64_t)gx * gy, (int64_t)num_sms * per_sm)
-                              : pv::pick_zchunk(a.g.nz, R, (int64_t)gx * gy, (int64_t)num_sms * per_sm);
+    // FP32: HBM-bound, the fewest chunks when they fit in one wave of
+    // resident CTAs (measured at 256^3: 2 chunks of 128 planes, 121.8 ms for
+    // the backward pass against 123.7 with the 7 chunks of the wave-count
+    // choice); otherwise, and for FP64 (bound by the FP64 pipe), the
+    // wave-count choice: a partial last wave of one-CTA-per-SM tiles costs
+    // more than the re-read it saves
+    const int64_t tiles = (int64_t)gx * gy, resident = (int64_t)num_sms * per_sm;
+    b.zchunk = pv::pick_zchunk(a.g.nz, R, tiles, resident);
+    if (sizeof(T) == 4) {
+        const int c = pv::pick_zchunk_traffic(a.g.nz, R, tiles, resident);
+        if (tiles * ((a.g.nz + c - 1) / c) <= resident) b.zchunk = c;
+    }
     dim3 grid(gx, gy, (a.g.nz + b.zchunk - 1) / b.zchunk), block(32, WY, 1);
     kern<<<grid, block, TL::smem, st>>>(b, m_lam, m_cx, m_cy);
     return cudaGetLastError();
