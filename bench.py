@@ -100,6 +100,8 @@ def run_reference(args):
         cpu_oracle_rate(kind, wk, T_sample, threads)
     rates = [cpu_oracle_rate(kind, wk, T_sample, threads)[0] for _ in range(args.steps)]
     v = statistics.median(rates)
+    # the same loops on one core, once (context for the all-core figure)
+    v1, dt1 = cpu_oracle_rate(kind, wk, T_sample, 1)
     n3 = args.n ** 3
     sample = f"{T_sample} time step of the {args.n}^3 {args.kind} sweep per step (FP64 plain C loops, {threads} threads)"
     line = {
@@ -111,6 +113,8 @@ def run_reference(args):
                    "n": args.n, "T": args.T, "sample": sample},
         "cpu_baseline": {"value": v, "unit": METRIC, "cores": threads, "kind": "oracle", "sample": sample},
         "e2e": {"value": v, "unit": METRIC, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        "cpu_single_thread": {"value": v1, "unit": METRIC, "cores": 1, "kind": "oracle",
+                              "sample": f"{T_sample} time step of the {args.n}^3 {args.kind} sweep, once ({dt1:.1f} s)"},
     }
     print(json.dumps(line), flush=True)
 
