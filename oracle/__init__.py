@@ -8,5 +8,5 @@ input generators in ``paper_1410_3060_gb300.workloads``.
 from .oracle import (  # noqa: F401
     J7_CONST, J7_VAR, W25_CONST, W25_VAR, J25_VAR, W25_ALPHA,
     RADIUS, NUM_ARRAYS, NUM_WEIGHTS, SECOND_ORDER,
-    build, forward, adjoint, receiver_loss, loss_and_gradient, lib_path,
+    build, forward, forward_f32, adjoint, receiver_loss, loss_and_gradient, lib_path,
 )

@@ -3,7 +3,8 @@
 TEST INFRASTRUCTURE ONLY: used by ``tests/``, ``__graft_entry__.smoke()``
 and the CPU-baseline leg of ``bench.py``.  Never imported by the library.
 
-Everything here is FP64.  Arrays are halo-padded C-order numpy arrays of
+Everything here is FP64 except ``forward_f32``, the same sweep evaluated
+in FP32 (``oracle_f32.c``).  Arrays are halo-padded C-order numpy arrays of
 shape (nz+2R, ny+2R, nx+2R); coefficient stacks have shape (k, nz+2R,
 ny+2R, nx+2R).  The update definitions, kind numbers and the time-state
 convention are documented in ``oracle.c`` (paper Sect. 3.1, Fig. 1).
@@ -28,6 +29,7 @@ SECOND_ORDER = {J7_CONST: False, J7_VAR: False, W25_CONST: True, W25_VAR: True,
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _BUILD = os.path.join(_HERE, "_build")
 _SRC = os.path.join(_HERE, "oracle.c")
+_SRC32 = os.path.join(_HERE, "oracle_f32.c")
 _lock = threading.Lock()
 _lib = None
 
@@ -37,18 +39,19 @@ def lib_path() -> str:
 
 
 def build(force: bool = False) -> str:
-    """Compile ``oracle.c`` into ``_build/liboracle.so`` with gcc.
+    """Compile ``oracle.c`` and ``oracle_f32.c`` into ``_build/liboracle.so`` with gcc.
 
     -ffp-contract=off keeps every multiply and add separately rounded so the
     oracle gives identical bits on x86_64 and aarch64 hosts.
     """
     out = lib_path()
-    if not force and os.path.exists(out) and os.path.getmtime(out) >= os.path.getmtime(_SRC):
+    newest = max(os.path.getmtime(_SRC), os.path.getmtime(_SRC32))
+    if not force and os.path.exists(out) and os.path.getmtime(out) >= newest:
         return out
     os.makedirs(_BUILD, exist_ok=True)
     tmp = out + f".tmp{os.getpid()}"
     cmd = ["gcc", "-std=c11", "-O2", "-ffp-contract=off", "-fno-fast-math", "-fopenmp",
-           "-fPIC", "-shared", "-o", tmp, _SRC]
+           "-fPIC", "-shared", "-o", tmp, _SRC, _SRC32]
     subprocess.run(cmd, check=True)
     os.replace(tmp, out)
     return out
@@ -62,6 +65,9 @@ def _open(path):
     lib.oracle_adjoint.argtypes = [i32, i64, i64, i64, i32, dp, dp, dp, dp, i64, dp, dp, i64,
                                    dp, i32]
     lib.oracle_adjoint.restype = i32
+    if hasattr(lib, "oracle_forward_f32"):   # absent from the planted-mistake copies of oracle.c
+        lib.oracle_forward_f32.argtypes = [i32, i64, i64, i64, i32, dp, dp, dp, i32, dp, i64, dp, i64, i32]
+        lib.oracle_forward_f32.restype = i32
     return lib
 
 
@@ -97,8 +103,23 @@ def compile_variant(source_text: str, out_path: str) -> str:
     return out_path
 
 
+def compile_variant_f32(f32_text: str, out_path: str) -> str:
+    """Compile ``oracle.c`` with a (modified) copy of ``oracle_f32.c``."""
+    src = out_path + "_f32.c"
+    with open(src, "w") as f:
+        f.write(f32_text)
+    subprocess.run(["gcc", "-std=c11", "-O2", "-ffp-contract=off", "-fno-fast-math", "-fopenmp",
+                    "-fPIC", "-shared", "-o", out_path, _SRC, src], check=True)
+    return out_path
+
+
 def source_text() -> str:
     with open(_SRC) as f:
+        return f.read()
+
+
+def source_text_f32() -> str:
+    with open(_SRC32) as f:
         return f.read()
 
 
@@ -155,6 +176,31 @@ def forward(kind, u_prev, u, w=None, W=None, T=1, rcv_z=None, threads=1):
     if st != 0:
         raise ValueError(f"oracle_forward failed with status {st}")
     return a, b, trace
+
+
+def forward_f32(kind, u_prev, u, w=None, W=None, T=1, rcv_z=None, threads=1):
+    """The FP32 evaluation of ``forward`` (oracle_f32.c): the inputs are
+    rounded to float32 once, every update is evaluated in float32 in the
+    FP64 oracle's order of terms.  Returns float64 arrays holding the float32
+    results (u^{T-1}, u^T, trace)."""
+    R = RADIUS[kind]
+    a = np.array(u_prev, dtype=np.float32, order="C", copy=True)
+    b = np.array(u, dtype=np.float32, order="C", copy=True)
+    nx, ny, nz = _dims(b, R)
+    wv = _weights(kind, w)
+    Wv = None
+    if NUM_ARRAYS[kind]:
+        Wv = np.ascontiguousarray(W, dtype=np.float32)
+        assert Wv.shape == (NUM_ARRAYS[kind],) + b.shape
+    trace = np.zeros((T, ny, nx), dtype=np.float32) if rcv_z is not None else None
+    p32 = (lambda x: None if x is None else x.ctypes.data_as(ctypes.c_void_p))
+    st = _load().oracle_forward_f32(kind, nx, ny, nz, R, p32(a), p32(b), _ptr(wv),
+                                    0 if wv is None else len(wv), p32(Wv), int(T), p32(trace),
+                                    int(rcv_z or 0), int(threads))
+    if st != 0:
+        raise ValueError(f"oracle_forward_f32 failed with status {st}")
+    return (a.astype(np.float64), b.astype(np.float64),
+            trace.astype(np.float64) if trace is not None else None)
 
 
 def adjoint(kind, lam_next, lam, w=None, W=None, T=1, states=None, residual=None, rcv_z=None,

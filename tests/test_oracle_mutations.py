@@ -58,3 +58,34 @@ def test_pin_catches_mutation(name, tmp_path):
     with ora.swapped_library(path):
         with pytest.raises(AssertionError):
             run_pin(name)
+
+
+# ---- the FP32 evaluation (oracle_f32.c): mistakes planted there must break
+# its bit-for-bit agreement with the FP64 oracle on dyadic inputs
+MUTATIONS_F32 = {
+    # z pair dropped from the 7-point constant stencil
+    "f32_j7_drop_z": ("+ lam[1] * (u[i - g->sz] + u[i + g->sz]);", ";"),
+    # sign of the previous level in the wave update
+    "f32_wave_prev_sign": ("return 2.0f * u[i] - up[i] + al * acc;", "return 2.0f * u[i] + up[i] + al * acc;"),
+    # y-1 neighbour of the 7-point variable stencil read at y+1
+    "f32_j7var_offset": ("+ A[3 * n + i] * u[i - g->sy]", "+ A[3 * n + i] * u[i + g->sy]"),
+    # coefficient of the radius-r pair taken from radius r - 1's arrays
+    "f32_w25var_radius": ("acc += A[(int64_t)(3 * (r - 1) + a + 1) * n + i] * (u[i - d] + u[i + d]);",
+                          "acc += A[(int64_t)(3 * (r > 1 ? r - 2 : 0) + a + 1) * n + i] * (u[i - d] + u[i + d]);"),
+}
+F32_PIN_KIND = {"f32_j7_drop_z": oracle.J7_CONST, "f32_wave_prev_sign": oracle.W25_CONST,
+                "f32_j7var_offset": oracle.J7_VAR, "f32_w25var_radius": oracle.W25_VAR}
+
+
+@pytest.mark.parametrize("name", sorted(MUTATIONS_F32))
+def test_f32_pin_catches_mutation(name, tmp_path):
+    import test_oracle_f32 as pins32
+    old, new = MUTATIONS_F32[name]
+    src = ora.source_text_f32()
+    assert src.count(old) == 1, f"mutation anchor not unique: {old}"
+    kind = F32_PIN_KIND[name]
+    pins32.test_f32_equals_fp64_oracle_on_dyadic_inputs(kind)   # the real FP32 evaluation passes
+    path = ora.compile_variant_f32(src.replace(old, new), str(tmp_path / f"lib_{name}.so"))
+    with ora.swapped_library(path):
+        with pytest.raises(AssertionError):
+            pins32.test_f32_equals_fp64_oracle_on_dyadic_inputs(kind)
