@@ -73,13 +73,35 @@ def dist_env():
 
 
 # --------------------------------------------------------------- reference arm
-def cpu_oracle_rate(kind, wk, T_sample, threads):
+def cpu_oracle_rate(kind, wk, T_sample, threads, keep=False):
+    """GLUP/s and seconds of the FP64 oracle on T_sample steps of the
+    workload (and, with keep, its u^T)."""
     import oracle
     t0 = time.perf_counter()
-    oracle.forward(kind, wk.u_prev, wk.u, wk.w, wk.W, T_sample, threads=threads)
+    _, uT, _ = oracle.forward(kind, wk.u_prev, wk.u, wk.w, wk.W, T_sample, threads=threads)
     dt = time.perf_counter() - t0
     n = wk.n[0] * wk.n[1] * wk.n[2]
-    return n * T_sample / dt / 1e9, dt
+    return (n * T_sample / dt / 1e9, dt) + ((uT,) if keep else ())
+
+
+def gpu_one_step_error(torch, st, kind, wk, dtype, oracle_u1):
+    """Normwise error (max |g - o| / max |o|) of one GPU step of the plan's
+    default program against the oracle's step from the same input."""
+    tdt = torch.float64 if dtype == st.F64 else torch.float32
+    nx, ny, nz = wk.n
+    plan = st.Plan(kind, nx, ny, nz, dtype)
+    up = torch.from_numpy(wk.u_prev).to("cuda", tdt)
+    u = torch.from_numpy(wk.u).to("cuda", tdt)
+    W = torch.from_numpy(wk.W).to("cuda", tdt) if wk.W is not None else None
+    plan.forward(up, u, wk.w, W, 1)
+    plan.check()
+    plan.close()
+    o = torch.from_numpy(oracle_u1)
+    g = u.to("cpu", torch.float64)
+    err = float((g - o).abs().max() / o.abs().max().clamp_min(1e-300))
+    del up, u, W
+    torch.cuda.empty_cache()
+    return err
 
 
 def run_reference(args):
@@ -240,14 +262,28 @@ def forward_case(torch, st, wl, kind, n, T, dtype, steps, warmup, ws, stream, ti
     up = torch.from_numpy(wk.u_prev).to("cuda", tdt)
     u = torch.from_numpy(wk.u).to("cuda", tdt)
     W = torch.from_numpy(wk.W).to("cuda", tdt) if wk.W is not None else None
+    # every step starts from the workload's initial state (a device copy,
+    # restored between steps outside the step's events): the decaying
+    # 7-point variable field would otherwise reach zero after a few hundred
+    # sweeps, and every step then sweeps the same data
+    up0, u0 = up.clone(), u.clone()
     for _ in range(warmup):
+        up.copy_(up0)
+        u.copy_(u0)
         plan.forward(up, u, wk.w, W, T)
     barrier(torch, ws)
-    with Timer(torch, stream) as tm:
-        for _ in range(steps):
-            plan.forward(up, u, wk.w, W, T)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    for i in range(steps):
+        up.copy_(up0)
+        u.copy_(u0)
+        ev[i][0].record(stream)
+        plan.forward(up, u, wk.w, W, T)
+        ev[i][1].record(stream)
+    ev[-1][1].synchronize()
+    step_ms = sum(a.elapsed_time(b) for a, b in ev)
     barrier(torch, ws)
-    ms = max_over_ranks(torch, ws, tm.ms)
+    ms = max_over_ranks(torch, ws, step_ms)
+    del up0, u0
     lups = float(n) ** 3 * T
     passes = [o for o in st.schedule(kind, T, b, dtype) if o[0] == 0]
     res = {"kind": wl.KIND_NAMES[kind], "n": n, "T": T, "dtype": "f64" if dtype == st.F64 else "f32",
@@ -318,9 +354,18 @@ def forward_case(torch, st, wl, kind, n, T, dtype, steps, warmup, ws, stream, ti
 
 # DRAM bytes per update measured by ncu (dram__bytes_read.sum +
 # dram__bytes_write.sum of one launch / updates of that launch) for the kernel
-# configurations summarised under profiles/; the roofline record reports them
-# scaled to one launch of the benchmarked size, null for any other kernel.
+# configurations summarised under profiles/, keyed by (kind, dtype, levels per
+# pass, tile variant); the roofline record reports them scaled to one launch
+# of the benchmarked size, null for any configuration without a profile of
+# its current kernel.
 MEASURED_TRAFFIC = {("j7_var", "f64", 1, 8): (72.5, "profiles/plain_stream_j7_var_256_fp64.md")}
+
+
+def add_traffic(rec, kind_name, dtype_name, res, n):
+    tr = MEASURED_TRAFFIC.get((kind_name, dtype_name, res["time_block"], res["variant"]))
+    if tr is not None:
+        rec["traffic"] = tr[0] * float(n) ** 3
+        rec["traffic_source"] = tr[1] + " (DRAM bytes per update x updates per launch)"
 # thread instructions per update of the on-chip-bound FP32 kernels (ncu
 # warp instructions x 32 / updates of the profiled launch): the issue view of
 # their roofline, ceiling = 4 warp instructions per clock per SM
@@ -350,33 +395,42 @@ KIND_TEXT = {1: "7-point constant coefficients (Fig. 1b)", 2: "7-point variable 
              6: "25-point wave with alpha array (Fig. 1e)"}
 
 
-def roofline_of(pm, kind, dtype_name, n, res, peak_f64, hbm_peak, fp32_peak):
-    """Roofline record of one case: FP64 sweeps are bound by the FP64 pipe
-    (peak = 2 FP64 FMA per clock per SM x SMs x SM clock), FP32 sweeps by
-    HBM (peak = measured copy bandwidth).  Units processed per pass: n^3
-    updates of `time_block` levels; algorithmic bytes = one read of every
-    input stream and one write of the state per pass."""
+def roofline_of(pm, kind, dtype_name, n, res, fp_peaks, hbm_peak):
+    """Roofline record of one case (min of ceilings): the HBM ceiling (measured
+    copy bandwidth / algorithmic bytes per update) against the FP ceiling
+    (the measured FMA-chain rate of the dtype, fp_peaks[dtype]["probe"] in
+    flop/s, / flops per update); the lower one is the bound and the record's
+    achieved / peak are in its units.  Units processed per pass: n^3 updates
+    of `time_block` levels; algorithmic bytes = one read of every input
+    stream and one write of the state per pass; flops of every level.  The
+    datasheet FP rate (FMA units x SMs x measured clock) is a side view."""
     word = 8 if dtype_name == "f64" else 4
     b = res["time_block"]
     t_pass = res["ms_per_step"] / (res["T"] / b) * 1e-3
     pts = float(n) ** 3
     bytes_pass = pm.gpu_bytes_per_lup(kind, word) * pts
     flops_pass = pm.FLOPS_PER_LUP[kind] * pts * b
+    probe, sheet = fp_peaks[dtype_name]["probe"], fp_peaks[dtype_name]["datasheet"]
+    hbm_ceiling = hbm_peak * 1e9 / (pm.gpu_bytes_per_lup(kind, word) / b) / 1e9   # GLUP/s
+    fp_ceiling = probe / pm.FLOPS_PER_LUP[kind] / 1e9
     hbm = {"achieved_gbs": bytes_pass / t_pass / 1e9, "peak_gbs": hbm_peak,
-           "frac": bytes_pass / t_pass / 1e9 / hbm_peak}
-    if dtype_name == "f64":
-        ach = flops_pass / t_pass / 1e12
-        # the FP64 pipe executes one add, multiply or FMA per lane-slot: the
-        # instruction view counts adds as full pipe slots (flops count them
-        # as half an FMA)
-        instr = pm.FP_INSTR_PER_LUP[kind] * pts * b / t_pass
-        pipe = {"fp64_instr_per_update": pm.FP_INSTR_PER_LUP[kind], "achieved_ginstr_s": instr / 1e9,
-                "peak_ginstr_s": peak_f64 / 2 / 1e9, "frac": instr / (peak_f64 / 2)}
-        return {"bound": "alu", "achieved": ach, "peak": peak_f64 / 1e12, "unit": "TFLOP/s",
-                "frac": ach / (peak_f64 / 1e12), "traffic": None, "hbm_view": hbm, "fp64_pipe_view": pipe}
-    return {"bound": "hbm", "achieved": hbm["achieved_gbs"], "peak": hbm_peak, "unit": "GB/s",
-            "frac": hbm["frac"], "traffic": None,
-            "alu_view": {"achieved_tflops": flops_pass / t_pass / 1e12, "peak_tflops": fp32_peak / 1e12}}
+           "frac": bytes_pass / t_pass / 1e9 / hbm_peak, "ceiling_glups": hbm_ceiling}
+    ach_tf = flops_pass / t_pass / 1e12
+    fp = {"achieved_tflops": ach_tf, "peak_tflops": probe / 1e12, "frac": ach_tf / (probe / 1e12),
+          "ceiling_glups": fp_ceiling, "peak_source": f"measured {dtype_name.upper()} FMA-chain rate",
+          "datasheet_peak_tflops": sheet / 1e12, "frac_of_datasheet": ach_tf / (sheet / 1e12),
+          # an add occupies a pipe slot like an FMA: the instruction view
+          "fp_instr_per_update": pm.FP_INSTR_PER_LUP[kind],
+          "instr_frac": pm.FP_INSTR_PER_LUP[kind] * pts * b / t_pass / (probe / 2)}
+    if fp_ceiling < hbm_ceiling:
+        rec = {"bound": "alu", "achieved": ach_tf, "peak": probe / 1e12, "unit": "TFLOP/s",
+               "frac": fp["frac"], "peak_source": fp["peak_source"] + " (stencil_fma_peak)"}
+    else:
+        rec = {"bound": "hbm", "achieved": hbm["achieved_gbs"], "peak": hbm_peak, "unit": "GB/s",
+               "frac": hbm["frac"], "peak_source": "MEASURED_PEAKS.json hbm_gbs (copy, measured)"}
+    rec.update({"traffic": None, "ceilings_glups": {"hbm": hbm_ceiling, "fp": fp_ceiling},
+                "hbm_view": hbm, "fp_view": fp})
+    return rec
 
 
 def fwd_adj_bytes_per_lup(elem, T, K, grad_batch):
@@ -454,7 +508,7 @@ def fwd_adj_case(torch, st, wl, n, T, K, dtype, steps, warmup, ws, stream, fw=No
     return res, fw
 
 
-def run_sweep(args, torch, st, wl, pm, stream, ws, peak_f64, hbm_peak, peak_f32):
+def run_sweep(args, torch, st, wl, pm, stream, ws, fp_peaks, hbm_peak):
     """Tuning sweep (the auto-tuning of tile parameters): every forward tile
     variant and block depth of every kind and dtype at the given size; one
     JSON line per case."""
@@ -468,7 +522,7 @@ def run_sweep(args, torch, st, wl, pm, stream, ws, peak_f64, hbm_peak, peak_f32)
             for v in (1, 2, 3, 4, 5, 6, 7, 8, 9) + ((10, 11, 12, 13, 14, 15, 16) if r1 else (13, 14, 15, 16)):
                 r, _ = forward_case(torch, st, wl, kind, n, T, dtype, args.steps, 1, ws, stream, time_block=1,
                                     wk=wk, variant=v)
-                r["roofline"] = roofline_of(pm, kind, r["dtype"], n, r, peak_f64, hbm_peak, peak_f32)
+                r["roofline"] = roofline_of(pm, kind, r["dtype"], n, r, fp_peaks, hbm_peak)
                 print(json.dumps({"sweep": r}), flush=True)
             blocked = ((2, 3, 4) if r1 else (2,)) if dtype == st.F32 else ((2,) if r1 else ())
             for b in blocked:
@@ -476,7 +530,7 @@ def run_sweep(args, torch, st, wl, pm, stream, ws, peak_f64, hbm_peak, peak_f32)
                 for sch, v in cases:
                     r, _ = forward_case(torch, st, wl, kind, n, T, dtype, args.steps, 1, ws, stream,
                                         time_block=b, wk=wk, scheme=sch, variant=v)
-                    r["roofline"] = roofline_of(pm, kind, r["dtype"], n, r, peak_f64, hbm_peak, peak_f32)
+                    r["roofline"] = roofline_of(pm, kind, r["dtype"], n, r, fp_peaks, hbm_peak)
                     print(json.dumps({"sweep": r}), flush=True)
         del wk
 
@@ -500,14 +554,16 @@ def run_ours(args):
     probe_f64, clk = st.fma_peak(st.F64)
     probe_f32, _ = st.fma_peak(st.F32)
     num_sms = torch.cuda.get_device_properties(0).multi_processor_count
-    peak_f64 = 2 * 2 * num_sms * clk      # 2 FP64 FMA per clock per SM (GB300 nominal FP64 rate)
-    peak_f32 = 2 * 128 * num_sms * clk    # 128 FP32 FMA per clock per SM
+    sheet_f64 = 2 * 2 * num_sms * clk      # datasheet: 2 FP64 FMA per clock per SM (GB300)
+    sheet_f32 = 2 * 128 * num_sms * clk    # datasheet: 128 FP32 FMA per clock per SM
+    fp_peaks = {"f64": {"probe": probe_f64, "datasheet": sheet_f64},
+                "f32": {"probe": probe_f32, "datasheet": sheet_f32}}
     peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
         os.path.join(ROOT, "MEASURED_PEAKS.json")) else {}
     hbm_peak = peaks.get("hbm_gbs", 6800.0)
 
     if args.sweep:
-        run_sweep(args, torch, st, wl, pm, stream, ws, peak_f64, hbm_peak, peak_f32)
+        run_sweep(args, torch, st, wl, pm, stream, ws, fp_peaks, hbm_peak)
         return
     if args.fwd_adj:
         r, _ = fwd_adj_case(torch, st, wl, n, T, 20, dtype, args.steps, args.warmup, ws, stream,
@@ -522,11 +578,8 @@ def run_ours(args):
                                time_block=args.time_block, e2e=not args.no_e2e, wk=wk, scheme=args.scheme,
                                variant=args.variant, graph=args.graph)
     clocks = sampler.summary()
-    roofline = roofline_of(pm, kind, args.dtype, n, main, peak_f64, hbm_peak, peak_f32)
-    tr = MEASURED_TRAFFIC.get((args.kind, args.dtype, main["time_block"], main["variant"]))
-    if tr is not None:
-        roofline["traffic"] = tr[0] * float(n) ** 3
-        roofline["traffic_source"] = tr[1] + " (bytes per update x updates per launch)"
+    roofline = roofline_of(pm, kind, args.dtype, n, main, fp_peaks, hbm_peak)
+    add_traffic(roofline, args.kind, args.dtype, main, n)
     if main["time_block"] == 1 and 13 <= main["variant"] <= 16:
         kname = "plainv_kernel (vectorised, " + ("TMA" if main["variant"] >= 15 else "cp.async") + " staging)"
     elif main["scheme"] == 3 or 10 <= main["variant"] <= 12:
@@ -536,16 +589,9 @@ def run_ours(args):
     else:
         kname = "blocked_kernel (phase A + B)" if main["scheme"] == 2 else "blocked_kernel (overlapped)"
     roofline["kernel"] = kname + f"<{'double' if dtype == st.F64 else 'float'}, {args.kind}>"
-    roofline["peak_source"] = ("2 FP64 FMA/clk/SM x %d SMs x %.0f MHz (measured clock); FMA-chain probe %.3f TFLOP/s"
-                               % (num_sms, clk / 1e6, probe_f64 / 1e12)) if dtype == st.F64 else \
-        "MEASURED_PEAKS.json hbm_gbs (copy, measured)"
     iv = issue_view(args.kind, args.dtype, main, num_sms, clk)
     if iv:
         roofline["issue_view"] = iv
-    if "fp64_pipe_view" in roofline:
-        # against the FMA-chain probe: the FP64 rate a kernel of dependent FMAs reaches here
-        pv_ = roofline["fp64_pipe_view"]
-        pv_["frac_of_fma_probe"] = pv_["achieved_ginstr_s"] / (probe_f64 / 2 / 1e9)
 
     variants = []
     if not args.no_variants:
@@ -560,7 +606,8 @@ def run_ours(args):
                 cache[vk] = wl.make(vk, n, vT, seed=0) if vk != wl.J7_VAR else wl.j7_var(n, vT, seed=0)
             r, _ = forward_case(torch, st, wl, vk, n, vT, vd, max(1, args.steps // 2), 1, ws, stream,
                                 time_block=vb, wk=cache[vk])
-            r["roofline"] = roofline_of(pm, vk, r["dtype"], n, r, peak_f64, hbm_peak, peak_f32)
+            r["roofline"] = roofline_of(pm, vk, r["dtype"], n, r, fp_peaks, hbm_peak)
+            add_traffic(r["roofline"], wl.KIND_NAMES[vk], r["dtype"], r, n)
             iv = issue_view(wl.KIND_NAMES[vk], r["dtype"], r, num_sms, clk)
             if iv:
                 r["roofline"]["issue_view"] = iv
@@ -573,13 +620,20 @@ def run_ours(args):
             variants.append(r)
 
     cpu = None
+    max_rel_err = None
     if rank == 0 and not args.no_cpu:
         import oracle
         oracle.build()
         threads = oracle.oracle.default_threads()
-        rate, dt = cpu_oracle_rate(kind, wk, 1, threads)
+        rate, dt, o1 = cpu_oracle_rate(kind, wk, 1, threads, keep=True)
         cpu = {"value": rate, "unit": METRIC, "cores": threads, "kind": "oracle",
                "sample": f"1 time step of the {n}^3 {args.kind} FP64 sweep ({dt:.1f} s)"}
+        # the GPU's first step against this oracle step (the full-T errors
+        # are measured by tests/test_gpu_errors.py)
+        max_rel_err = {"value": gpu_one_step_error(torch, st, kind, wk, dtype, o1), "T": 1,
+                       "metric": "max |gpu - oracle| / max |oracle| of u^1, whole 512^3 lattice",
+                       "vs": "FP64 oracle step of the cpu_baseline sample"}
+        del o1
 
     if rank == 0:
         line = {
@@ -588,16 +642,17 @@ def run_ours(args):
             "scaling": "weak", "vs_baseline": None, "dtype": args.dtype, "data": "synthetic",
             "config": {"workload": f"{args.kind}_{n}^3_T{T}_{args.dtype}", "kind": KIND_TEXT[kind],
                        "n": n, "T": T, "time_block": main["time_block"], "parallelism": f"replicas{ws}",
-                       "l2": "inputs larger than L2 (no flush needed)" if n >= 256 else "small case"},
+                       "l2": "inputs larger than L2 (no flush needed)" if n >= 256 else "small case",
+                       "state": "reset to u0 from a device copy before every step, outside the step's events"},
             "e2e": main.get("e2e"), "gpu_launches": main["launches_per_step"] * args.steps,
-            "roofline": roofline, "clocks": clocks, "cpu_baseline": cpu,
+            "roofline": roofline, "clocks": clocks, "cpu_baseline": cpu, "max_rel_err": max_rel_err,
             "energy": ({"joules_per_step": clocks["power_w_under_load"] * main["ms_per_step"] * 1e-3,
                         "nJ_per_lup": clocks["power_w_under_load"] * main["ms_per_step"] * 1e-3
                         / (float(n) ** 3 * T) * 1e9,
                         "method": "mean nvidia-smi board power of the loaded half of the samples x time per step"}
                        if clocks.get("power_w_under_load") else None),
             "peaks_measured": {"fp64_fma_probe_tflops": probe_f64 / 1e12, "fp32_fma_probe_tflops": probe_f32 / 1e12,
-                               "fp64_peak_tflops": peak_f64 / 1e12, "fp32_peak_tflops": peak_f32 / 1e12,
+                               "fp64_datasheet_tflops": sheet_f64 / 1e12, "fp32_datasheet_tflops": sheet_f32 / 1e12,
                                "sm_clock_mhz": clk / 1e6, "hbm_gbs": hbm_peak},
             "variants": variants,
         }

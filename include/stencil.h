@@ -72,7 +72,8 @@ enum stencil_status {
     STENCIL_EINVAL = -1,       /* bad argument: see stencil_strerror        */
     STENCIL_EUNSUPPORTED = -2, /* valid request this build does not serve   */
     STENCIL_ENOMEM = -3,       /* device scratch allocation failed          */
-    STENCIL_ECUDA = -4         /* a CUDA call failed (stencil_last_cuda_error) */
+    STENCIL_ECUDA = -4,        /* a CUDA call failed (stencil_last_cuda_error) */
+    STENCIL_ETIMEOUT = -5      /* a bounded device wait gave up (stencil_check) */
 };
 
 /* Plan options (stencil_plan_set / stencil_plan_get). */
@@ -126,7 +127,21 @@ enum stencil_option {
        the same; a new argument set or any stencil_plan_set replaces the
        graph.  Capture runs on a plan-owned stream, so the caller's stream
        may be the legacy default stream.  0 (default): direct launches. */
-    STENCIL_OPT_GRAPH = 6
+    STENCIL_OPT_GRAPH = 6,
+    /* Polls of the bounded mbarrier waits of the TMA-staged sweeps (tile
+       variants 15 and 16) before a wait gives up: 0 = default (2^22, far
+       longer than any copy takes; each poll may suspend the thread for a
+       hardware-defined time).  A CTA whose wait gives up stops sweeping,
+       waits (bounded) for its copies in flight and returns; its part of the
+       result is then wrong and stencil_check reports STENCIL_ETIMEOUT. */
+    STENCIL_OPT_WAIT_LIMIT = 7,
+    /* Test hook for the give-up path of the bounded waits: v >= 0 makes the
+       first CTA (block 0, 0, 0) of every TMA-staged sweep of this plan skip
+       issuing the copies of interior plane v (the first CTA's first z chunk
+       then waits for a copy that never comes, gives up and returns; no copy
+       is left in flight).  -1 = off (default).  Only for tests of the
+       ETIMEOUT path, together with a small STENCIL_OPT_WAIT_LIMIT. */
+    STENCIL_OPT_TEST_SKIP_COPY = 8
 };
 
 typedef struct stencil_plan_s *stencil_plan_t;
@@ -238,9 +253,12 @@ int stencil_misfit(stencil_plan_t plan, const void *trace, const void *d, int64_
  *  work is enqueued).
  * Scratch: the FP64 partial sums live in a static device array of the
  * library (64 KiB, one partial per 2048 elements, at most 8192), which every
- * GPU that loads the library holds until the process exits.  The first call
- * on a device looks up that array's device address (cudaGetSymbolAddress,
- * with the device current); make that first call before any stream capture.
+ * GPU that loads the library holds until the process exits.  A call looks up
+ * that array's device address (cudaGetSymbolAddress, with the device
+ * current) unless its stream is being captured; inside a capture it uses the
+ * address found by an earlier call on that device, so make one call on each
+ * device before any stream capture (a capture without one fails with
+ * STENCIL_ECUDA).
  * All calls share the array: calls that may overlap on the GPU (different
  * streams, or other threads) race and must be serialised by the caller.
  * Every entry a call reads is written by the same call, so nothing carries
@@ -278,11 +296,23 @@ const char *stencil_strerror(int status);
  * in this thread (cudaError_t as int), or 0. */
 int stencil_last_cuda_error(void);
 
-/* Number of bounded device waits (the TMA-staged sweeps' waits for their
- * plane copies) that gave up since the library was loaded, on the current
- * device, into *count; such a wait ends its thread instead of hanging.  0
- * on a healthy run.  Synchronises the device. */
+/* Number of CTAs of the TMA-staged sweeps whose bounded wait for a plane
+ * copy gave up since the library was loaded, on the current device, into
+ * *count (0 on a healthy run).  Such a CTA leaves its sweep with every
+ * other thread of the CTA at the barrier after the wait, waits (bounded)
+ * for the copies it still has in flight and returns, so the kernel ends
+ * instead of hanging; its part of the result is wrong.  Synchronises the
+ * device. */
 int stencil_wait_timeouts(int64_t *count);
+
+/* Wait for the work enqueued on `stream` (and on the plan's own gradient
+ * stream) to finish and report its status: STENCIL_ETIMEOUT if any bounded
+ * device wait of the library gave up since the plan's previous
+ * stencil_check (or its creation) -- the results of the calls in between
+ * are then invalid --, STENCIL_ECUDA if a CUDA error was reported, else
+ * STENCIL_OK.  The device counters are shared by all plans of the process:
+ * a timeout in another plan's work in that interval is reported too. */
+int stencil_check(stencil_plan_t plan, void *stream);
 
 #ifdef __cplusplus
 }

@@ -21,6 +21,13 @@ one level above T with a zero adjoint pair, so that lam^T = g^T is formed by
 the library.  Finally dL/du0 = lam^0 - lam^1 (second-order kinds; the tied
 u^{-1} contributes -lam^1) or lam^0 (first-order kinds), by stencil_axpby.
 
+Every forward pass gets its own set of checkpoint, trace, residual and loss
+buffers from a pool of the runner (a new set is allocated only while more
+forward passes are pending than the pool holds); the set returns to the
+pool when the forward pass's state is dropped.  So several losses of one
+runner may be built before a single backward() (their sum differentiates
+correctly), and a forward pass under no_grad releases its set at once.
+
 Every step of the computation runs in libstencil.so; torch provides memory
 and the autograd plumbing.
 """
@@ -45,7 +52,24 @@ class _MisfitFn(torch.autograd.Function):
         (W,) = ctx.saved_tensors
         du0, dW = ctx.runner.backward_pass(ctx.state, W, gloss)
         ctx.state = None
-        return du0.clone(), dW.to(W.dtype), None, None
+        # the runner's gradient buffers are reused by its next backward pass
+        return du0.clone(), dW.to(W.dtype, copy=True), None, None
+
+
+class _ForwardState:
+    """What one forward pass leaves for its backward pass: the checkpoints,
+    the residual, and whether the last segment's states are still held.
+    Owns one buffer set of the runner's pool and gives it back when dropped."""
+
+    def __init__(self, runner, bufs):
+        self._runner, self.bufs = runner, bufs
+        self.ckpts, self.res, self.kept = [], bufs["res"], None
+
+    def __del__(self):
+        try:
+            self._runner._pool.append(self.bufs)
+        except Exception:
+            pass
 
 
 class MisfitRunner:
@@ -70,12 +94,9 @@ class MisfitRunner:
         nx, ny, nz = self.n
         shape = self.plan.padded_shape
         new = lambda *s_, dt=None: torch.empty(s_, device=device, dtype=dt or self.dtype)  # noqa: E731
-        nck = (self.T + self.K - 1) // self.K
-        self._ckpt = [(new(*shape), new(*shape)) for _ in range(nck)]
+        self._new = new
+        self._pool = [self._new_forward_set()]
         self._state = (new(*shape), new(*shape))
-        self._trace = new(self.T, ny, nx)
-        self._res = new(self.T + 1, ny, nx)
-        self._loss = new(1, dt=torch.float64)
         self._lam = (new(*shape), new(*shape))
         self._grad = new(st.NUM_ARRAYS[kind], *shape, dt=torch.float64)
         self.overlap = bool(overlap)
@@ -87,6 +108,17 @@ class MisfitRunner:
                 st.fill_zero(b)   # zero halos (only interiors are ever written)
         self._side = torch.cuda.Stream(device=device) if self.overlap else None
         self._kept = None
+        self._res_scaled = None
+
+    def _new_forward_set(self):
+        """Checkpoints (state pair every K steps), trace, residual and loss of
+        one forward pass."""
+        nx, ny, nz = self.n
+        shape = self.plan.padded_shape
+        nck = (self.T + self.K - 1) // self.K
+        return {"ckpt": [(self._new(*shape), self._new(*shape)) for _ in range(nck)],
+                "trace": self._new(self.T, ny, nx), "res": self._new(self.T + 1, ny, nx),
+                "loss": self._new(1, dt=torch.float64)}
 
     def close(self):
         self.plan.close()
@@ -98,16 +130,18 @@ class MisfitRunner:
     # -- forward: checkpoints, trace, loss
     def forward_pass(self, u0, W, d):
         T, K = self.T, self.K
+        bufs = self._pool.pop() if self._pool else self._new_forward_set()
+        state = _ForwardState(self, bufs)
         up, u = self._state
         u0d = u0.detach()
         up.copy_(u0d)
         u.copy_(u0d)
-        trace = self._trace
-        ckpts = []
+        trace = bufs["trace"]
+        ckpts = state.ckpts
         t = 0
-        nck = len(self._ckpt)
+        nck = len(bufs["ckpt"])
         for i in range(nck):
-            cp, cu = self._ckpt[i]
+            cp, cu = bufs["ckpt"][i]
             cp.copy_(up)
             cu.copy_(u)
             ckpts.append((t, cp, cu))
@@ -121,37 +155,46 @@ class MisfitRunner:
             else:
                 self.plan.forward(up, u, self.w, W, k, trace=trace[t:t + k], rcv_z=self.rcv_z)
             t += k
-        res = self._res                      # res[i] = r^i, r^0 = 0
+        res = bufs["res"]                    # res[i] = r^i, r^0 = 0
         st.fill_zero(res[0])
-        self.plan.misfit(trace, d, res[1:], self._loss)
+        self.plan.misfit(trace, d, res[1:], bufs["loss"])
+        # the last segment's states sit in buffer set 0 until a backward
+        # pass or a later forward pass reuses it
         self._kept = {"valid": True}
-        return self._loss[0].clone(), {"ckpts": ckpts, "res": res, "kept": self._kept}
+        state.kept = self._kept
+        return bufs["loss"][0].clone(), state
 
     # -- backward: recompute + adjoint per segment
     def backward_pass(self, state, W, gloss):
         T, K, (nx, ny, nz) = self.T, self.K, self.n
         plan = self.plan
-        res = state["res"]
-        dev = res.device
+        res = state.res
         if not (isinstance(gloss, torch.Tensor) and gloss.numel() == 1):
             raise ValueError("scalar loss gradient expected")
         g = float(gloss.item())
         if g != 1.0:
-            plan.axpby(g, res, 0.0, res, res)
+            # scaled into the runner's scratch: the state's residual stays as
+            # the forward pass left it (a later backward pass may reuse it)
+            if self._res_scaled is None:
+                self._res_scaled = torch.empty_like(res)
+            plan.axpby(g, res, 0.0, res, self._res_scaled)
+            res = self._res_scaled
         lam_next, lam = self._lam
         grad = self._grad
         for t_ in (lam_next, lam, grad):
             st.fill_zero(t_)
-        segs = list(reversed(state["ckpts"]))
+        segs = list(reversed(state.ckpts))
         main = torch.cuda.current_stream()
         nsets = len(self._sets)
         rec_ev, adj_ev = [None] * nsets, [None] * nsets
         # the forward pass left the last segment's states in buffer set 0,
         # valid until a backward pass (or a later forward pass) reuses the set
-        kept = state.get("kept")
+        kept = state.kept
         have_last = kept is not None and kept["valid"] and kept is self._kept
-        if kept is not None:
-            kept["valid"] = False
+        # this pass rewrites the state-buffer sets: no forward pass's kept
+        # states survive it
+        if self._kept is not None:
+            self._kept["valid"] = False
 
         def recompute(i, stream):
             # u^{c+1} .. u^{c+k} of segment i into buffer set i mod nsets

@@ -19,7 +19,10 @@
 // terms are pushed: A_{z,r}(p) y(p) is added to the partial sums of output
 // planes p - r and p + r (a register ring of 2R+1 partial sums), so output
 // plane p - R is complete once plane p has arrived.  Three slots: the copies
-// of planes p + 1 and p + 2 run while plane p is summed.
+// of planes p + 1 and p + 2 run while plane p is summed.  The plane waits are
+// bounded and give up as in the forward sweep: the CTA leaves together after
+// the barrier that follows the wait, the issuing thread waits (bounded) for
+// its copies in flight and counts one timeout.
 #pragma once
 
 namespace stc {
@@ -82,6 +85,7 @@ adjt_kernel(const SweepArgs<T> a, const __grid_constant__ CUtensorMap tm_lam, co
 
     // all copies of plane p (interior index) into slot s
     auto issue = [&](int p, int s) {
+        if (pv::skip_copy(a.skip_plane, p)) return;   // test hook: this copy never arrives
         T *d = sb + s * TL::SLOT;
         uint64_t *bar = &bars[s];
         const int zp = p + R;   // padded plane
@@ -137,18 +141,21 @@ adjt_kernel(const SweepArgs<T> a, const __grid_constant__ CUtensorMap tm_lam, co
     load_own(qs);
     static_assert(RING % TL::NSLOT == 0, "slot of plane p: j mod NSLOT");
 
-    for (int pb = qs; pb < qe; pb += RING) {
+    const int wlim = pv::wait_limit_of(a.wait_limit);
+    int failed_p = qe;   // CTA-uniform: plane whose wait gave up (qe = none)
+    for (int pb = qs; pb < qe && failed_p == qe; pb += RING) {
         static_for<RING>([&](auto jj) {
             constexpr int j = decltype(jj)::value;
             constexpr int s = j % TL::NSLOT;
             const int p = pb + j;
-            if (p >= qe) return;
-            // k-th use of a slot completes phase k (parity k & 1)
-            if (!pv::mbar_wait(&bars[s], (uint32_t)(((p - qs) / TL::NSLOT) & 1))) {
-                atomicAdd(&g_wait_timeouts, 1u);
+            if (p >= qe || failed_p != qe) return;
+            // k-th use of a slot completes phase k (parity k & 1); the
+            // barrier also makes every thread done with plane p - 1's slot
+            const bool ok = pv::mbar_wait(&bars[s], (uint32_t)(((p - qs) / TL::NSLOT) & 1), wlim);
+            if (__syncthreads_or(!ok)) {
+                failed_p = p;
                 return;
             }
-            __syncthreads();   // every thread is done with plane p - 1's slot
             if (tid == 0 && p + 2 < qe) issue(p + 2, (j + 2) % TL::NSLOT);
             const T *sl = sb + s * TL::SLOT;
             if (own && p >= 0 && p < g.nz) {
@@ -237,6 +244,16 @@ adjt_kernel(const SweepArgs<T> a, const __grid_constant__ CUtensorMap tm_lam, co
             for (int i = 0; i < V; ++i) acc[jz][i] = T(0);   // now the slot of plane p + R + 1
             if (p + 1 < qe) load_own(p + 1);
         });
+    }
+    if (failed_p != qe && tid == 0) {
+        // planes failed_p and failed_p + 1 were issued (or skipped) before
+        // the barrier that stopped the loop: wait, bounded, for those in
+        // flight, then count the timeout
+        for (int k = 0; k < 2 && failed_p + k < qe; ++k) {
+            const int pp = failed_p + k;
+            pv::mbar_wait(&bars[(pp - qs) % TL::NSLOT], (uint32_t)(((pp - qs) / TL::NSLOT) & 1), wlim);
+        }
+        atomicAdd(&g_wait_timeouts, 1u);
     }
 }
 

@@ -186,6 +186,9 @@ struct stencil_plan_s {
     int ngring;
     double *partials;
     int npartials;
+    int wait_limit;        // polls of a bounded mbarrier wait (0 = default)
+    int skip_plane;        // test hook of the bounded waits (SKIP_NONE = off)
+    uint64_t timeouts_seen;   // device timeout counters at the last stencil_check
     // CUDA graph of the forward pass program (STENCIL_OPT_GRAPH)
     int graph;
     cudaStream_t cap_stream;
@@ -325,6 +328,8 @@ cudaError_t plain_step(stencil_plan_s *p, bool adjoint, const Scalars &s, const 
     a.rcv_z = (int)rcv_z;
     a.trace = trace;
     a.inject = inject;
+    a.wait_limit = p->wait_limit;
+    a.skip_plane = p->skip_plane;
     // the vectorised 25-point sweep (forward and adjoint)
     if (variant >= 13 && variant <= 16 && (!adjoint || kind_radius(p->kind) == 4) &&
         (p->dtype == 1 ? plainv_supported_f32(p->kind, p->g) : plainv_supported_f64(p->kind, p->g)))
@@ -429,12 +434,15 @@ int run_forward_states(stencil_plan_s *p, const void *u_prev, const void *u, con
 }
 
 // Adjoint with gradient batches: every adjoint level is written to a ring of
-// G + 2 plan fields, and after every G steps one gradient launch sums the G
+// 2G + 2 plan fields, and after every G steps one gradient launch sums the G
 // terms lam^{n+1} * d(A u^n)/dA in FP64 registers and updates the gradient
 // arrays once.  Step j (j = 1..T) produces lam^{m-j} into ring slot
-// (j-1) mod (G+2); its inputs lam^{m-j+1}, lam^{m-j+2} sit in the two
-// previous slots (or the caller's pair), which are not rewritten before
-// the batch that reads them has run.
+// (j-1) mod (2G+2); its inputs lam^{m-j+1}, lam^{m-j+2} sit in the two
+// previous slots (or the caller's pair).  2G + 2 slots are enough: batch b's
+// gradient reads its G levels and the level before them while batch b+1's
+// sweeps write the next G (G + 1 + G slots, plus one so that batch b+1's
+// first sweep still sees both inputs), and the first sweep of batch b+2
+// waits for batch b's gradient (ev_grad[b % 2]) before it overwrites them.
 template <typename T>
 int run_adjoint_ring(stencil_plan_s *p, void *lam_next, void *lam, const stencil_coeffs_t *coeffs, int64_t nsteps,
                      cudaStream_t st, const void *inject, int64_t rcv_z, const void *const *fwd_states,
@@ -597,6 +605,8 @@ int stencil_plan(stencil_plan_t *plan, int kind, int64_t nx, int64_t ny, int64_t
     p->g.nfield = px * py * pz;
     p->elem = dtype == STENCIL_F64 ? 8 : 4;
     p->grad_batch = 1;
+    p->skip_plane = SKIP_NONE;
+    p->timeouts_seen = (uint64_t)plainv_timeouts_f32() + plainv_timeouts_f64();
     p->field_bytes = (size_t)p->g.nfield * p->elem;
     cudaError_t e = cudaGetDevice(&p->device);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&p->num_sms, cudaDevAttrMultiProcessorCount, p->device);
@@ -646,6 +656,14 @@ int stencil_plan_set(stencil_plan_t p, int option, int64_t value) {
         if (value < 0 || value > 1) return STENCIL_EINVAL;
         p->graph = (int)value;
         return STENCIL_OK;
+    case STENCIL_OPT_WAIT_LIMIT:
+        if (value < 0 || value > (1 << 30)) return STENCIL_EINVAL;
+        p->wait_limit = (int)value;
+        return STENCIL_OK;
+    case STENCIL_OPT_TEST_SKIP_COPY:
+        if (value < -1 || value >= p->g.nz) return STENCIL_EINVAL;
+        p->skip_plane = value < 0 ? SKIP_NONE : (int)value;
+        return STENCIL_OK;
     default:
         return STENCIL_EINVAL;
     }
@@ -659,6 +677,8 @@ int stencil_plan_get(stencil_plan_t p, int option, int64_t *value) {
     case STENCIL_OPT_GRAD_BATCH: *value = p->grad_batch; return STENCIL_OK;
     case STENCIL_OPT_VARIANT: *value = plan_variant(p); return STENCIL_OK;
     case STENCIL_OPT_GRAPH: *value = p->graph; return STENCIL_OK;
+    case STENCIL_OPT_WAIT_LIMIT: *value = p->wait_limit > 0 ? p->wait_limit : WAIT_LIMIT_DEFAULT; return STENCIL_OK;
+    case STENCIL_OPT_TEST_SKIP_COPY: *value = p->skip_plane == SKIP_NONE ? -1 : p->skip_plane; return STENCIL_OK;
     case STENCIL_OPT_SCRATCH_BYTES:
         *value = (int64_t)((p->scratch[0] ? 2 * p->field_bytes : 0) + (p->nbands + p->ngring) * p->field_bytes +
                            p->npartials * sizeof(double));
@@ -877,6 +897,7 @@ const char *stencil_strerror(int status) {
     case STENCIL_EUNSUPPORTED: return "unsupported by this build";
     case STENCIL_ENOMEM: return "device allocation failed";
     case STENCIL_ECUDA: return "CUDA error";
+    case STENCIL_ETIMEOUT: return "a bounded device wait gave up";
     default: return "unknown status";
     }
 }
@@ -889,6 +910,19 @@ int stencil_wait_timeouts(int64_t *count) {
     if (e != cudaSuccess) return cuda_fail(e);
     *count = (int64_t)plainv_timeouts_f32() + (int64_t)plainv_timeouts_f64();
     return STENCIL_OK;
+}
+
+int stencil_check(stencil_plan_t p, void *stream) {
+    if (!p) return STENCIL_EINVAL;
+    cudaError_t e = cudaStreamSynchronize((cudaStream_t)stream);
+    if (e == cudaSuccess && p->grad_stream) e = cudaStreamSynchronize(p->grad_stream);
+    if (e != cudaSuccess) return cuda_fail(e);
+    const uint64_t now = (uint64_t)plainv_timeouts_f32() + plainv_timeouts_f64();
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_fail(e);
+    const bool grew = now != p->timeouts_seen;
+    p->timeouts_seen = now;
+    return grew ? STENCIL_ETIMEOUT : STENCIL_OK;
 }
 
 }  // extern "C"

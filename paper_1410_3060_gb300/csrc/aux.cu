@@ -401,8 +401,11 @@ template cudaError_t launch_axpby<double>(double, const double *, double, const 
                                           cudaStream_t);
 // ---- allocation-free misfit: the partial sums live in a library-owned
 // static device array instead of plan scratch.  The array's name is only a
-// host-side stand-in; its device address is looked up once per device
-// (with that device current) and cached.
+// host-side stand-in; its device address is looked up with the device
+// current.  A call outside stream capture looks it up again (so the address
+// stays right after a device reset reloads the module); a call inside a
+// capture uses the address cached by an earlier call on that device and
+// fails if there is none.
 static __device__ __align__(256) double g_misfit_partials[MISFIT_STATIC_MAX_PARTIALS];
 
 namespace {
@@ -417,14 +420,19 @@ cudaError_t misfit_static(int dtype, const void *trace, const void *d, int64_t n
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
     if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    e = cudaStreamIsCapturing(st, &cap);
+    if (e != cudaSuccess) return e;
     double *partials = nullptr;
     {
         std::lock_guard<std::mutex> lock(g_static_mtx);
-        if (!g_static_addr[dev]) {
+        if (cap == cudaStreamCaptureStatusNone) {
             void *ptr = nullptr;
             e = cudaGetSymbolAddress(&ptr, g_misfit_partials);
             if (e != cudaSuccess) return e;
             g_static_addr[dev] = static_cast<double *>(ptr);
+        } else if (!g_static_addr[dev]) {
+            return cudaErrorStreamCaptureUnsupported;
         }
         partials = g_static_addr[dev];
     }

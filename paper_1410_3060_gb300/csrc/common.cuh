@@ -69,7 +69,14 @@ struct SweepArgs {
     int rcv_z;           // interior z of the receiver plane (trace / inject)
     int zchunk;          // interior planes per CTA along z
     int variant;         // forward tile variant (0 = default of the kind / dtype)
+    int wait_limit;      // polls of a bounded mbarrier wait before it gives up (TMA-staged kernels)
+    int skip_plane;      // test hook: the first CTA does not issue the copy of this plane (SKIP_NONE = off)
 };
+
+// Polls of a bounded mbarrier wait when a plan sets no limit.
+constexpr int WAIT_LIMIT_DEFAULT = 1 << 22;
+// skip_plane value that matches no plane.
+constexpr int SKIP_NONE = -(1 << 30);
 
 // ---- cp.async (LDGSTS) helpers: 4- or 8-byte element copies into shared
 // memory; any element-aligned global address works.

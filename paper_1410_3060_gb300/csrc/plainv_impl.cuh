@@ -15,10 +15,15 @@
 //
 // TMA staging (template flag TMA): one thread issues each plane tile (and the
 // per-point planes) as a single cp.async.bulk.tensor copy described by a
-// tensor map, completing on a per-slot mbarrier that every thread waits on
-// (bounded: a wait that gives up counts a timeout and ends the thread); the
-// tensor unit zero-fills everything outside the padded array.  The copy then
-// costs no per-thread instructions.
+// tensor map, completing on a per-slot mbarrier that every thread waits on;
+// the tensor unit zero-fills everything outside the padded array.  The copy
+// then costs no per-thread instructions.  The wait is bounded: a thread
+// whose wait runs out reports it at the CTA barrier that follows every wait
+// (__syncthreads_or), and then the whole CTA leaves the plane loop together
+// -- no thread skips a barrier, nothing more is issued -- the issuing
+// thread waits (bounded again) for the copies it still has in flight, counts
+// one timeout in a device counter and the CTA returns.  stencil_check turns
+// the counter into STENCIL_ETIMEOUT.
 #pragma once
 #include <cuda.h>
 #include <cudaTypedefs.h>
@@ -116,10 +121,10 @@ __device__ __forceinline__ void tma_load_3d(void *dst, const CUtensorMap *map, i
         "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(z), "r"(smem_u32(bar))
         : "memory");
 }
-// wait for phase `parity` of `bar`; false when the bounded wait gives up
-__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity) {
+// wait for phase `parity` of `bar`; false when `limit` polls gave up
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, int limit) {
     const uint32_t b = smem_u32(bar);
-    for (int it = 0; it < (1 << 22); ++it) {
+    for (int it = 0; it < limit; ++it) {
         uint32_t ok;
         asm volatile(
             "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
@@ -133,9 +138,18 @@ __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity) {
 
 }  // namespace pv
 
-// Waits that gave up (a counter per translation unit; read through
-// plainv_timeouts_f32 / _f64).
+// CTAs whose bounded wait gave up (a counter per translation unit; read
+// through plainv_timeouts_f32 / _f64).
 static __device__ unsigned int g_wait_timeouts;
+
+namespace pv {
+// Polls of a bounded wait for this launch.
+__device__ __forceinline__ int wait_limit_of(int v) { return v > 0 ? v : WAIT_LIMIT_DEFAULT; }
+// Test hook: whether this CTA skips issuing the copies of plane q.
+__device__ __forceinline__ bool skip_copy(int skip_plane, int q) {
+    return q == skip_plane && blockIdx.x == 0 && blockIdx.y == 0 && blockIdx.z == 0;
+}
+}  // namespace pv
 
 // ADJ: the adjoint (transposed) sweep of a variable-coefficient kind: every
 // term's coefficient is read at its source point,
@@ -224,7 +238,7 @@ plainv_kernel(const SweepArgs<T> a, const __grid_constant__ CUtensorMap tm_u,
         if constexpr (TMA) {
             // thread 0: the tile with its halo, and the per-point planes of
             // output plane q - R (outside the padded array: zero fill)
-            if (tid == 0) {
+            if (tid == 0 && !pv::skip_copy(a.skip_plane, q)) {
                 pv::mbar_expect_tx(&bars[slot], (uint32_t)(sizeof(T) * (SP0 + NPS * PP)));
                 pv::tma_load_3d(sb + slot * SP, &tm_u, x0, y0, q + R, &bars[slot]);
                 if constexpr (KindTraits<KIND>::WAVE)
@@ -278,11 +292,14 @@ plainv_kernel(const SweepArgs<T> a, const __grid_constant__ CUtensorMap tm_u,
     (void)s0; (void)s1; (void)s2; (void)s3; (void)s4;
 
     int slot = 0;   // shared slot of plane q
-    for (int qb = qs; qb < qe; qb += RING) {
+    const int wlim = pv::wait_limit_of(a.wait_limit);
+    (void)wlim;
+    int failed_q = qe;  // CTA-uniform: plane whose wait gave up (qe = none)
+    for (int qb = qs; qb < qe && failed_q == qe; qb += RING) {
         static_for<RING>([&](auto jj) {
             constexpr int j = decltype(jj)::value;
             const int q = qb + j;
-            if (q >= qe) return;
+            if (q >= qe || failed_q != qe) return;
             const int z = q - R;
             const int64_t zo = (int64_t)(z + R) * sz + poff;
             // 13-array kinds: the coefficients of output plane z, issued before
@@ -301,15 +318,17 @@ plainv_kernel(const SweepArgs<T> a, const __grid_constant__ CUtensorMap tm_u,
                 }
             }
             if constexpr (TMA) {
-                // k-th use of a slot completes phase k (parity k & 1)
-                if (!pv::mbar_wait(&bars[slot], (uint32_t)(((q - qs) / NS) & 1))) {
-                    atomicAdd(&g_wait_timeouts, 1u);
+                // k-th use of a slot completes phase k (parity k & 1); every
+                // thread learns at the barrier whether any wait gave up
+                const bool ok = pv::mbar_wait(&bars[slot], (uint32_t)(((q - qs) / NS) & 1), wlim);
+                if (__syncthreads_or(!ok)) {
+                    failed_q = q;
                     return;
                 }
             } else {
                 cp_async_wait<PD - 1>();
+                __syncthreads();
             }
-            __syncthreads();
             pv::ld16<T>(ring[j], sb + slot * SP + scen);
             // staged per-point inputs of output plane z
             T pvv[V], al[V];
@@ -530,7 +549,21 @@ plainv_kernel(const SweepArgs<T> a, const __grid_constant__ CUtensorMap tm_u,
             }
         });
     }
-    if constexpr (!TMA) cp_async_wait<0>();
+    if constexpr (TMA) {
+        if (failed_q != qe && tid == 0) {
+            // the copies of planes failed_q .. failed_q + PD - 1 were issued
+            // (or skipped) before the barrier that stopped the loop: wait,
+            // bounded, for those in flight before the CTA's shared memory is
+            // released, then count the timeout
+            for (int k = 0; k < PD && failed_q + k < qe; ++k) {
+                const int qq = failed_q + k;
+                pv::mbar_wait(&bars[(qq - qs) % NS], (uint32_t)(((qq - qs) / NS) & 1), wlim);
+            }
+            atomicAdd(&g_wait_timeouts, 1u);
+        }
+    } else {
+        cp_async_wait<0>();
+    }
 }
 
 // Whether the vectorised sweep serves this kind and geometry.
@@ -685,7 +718,7 @@ cudaError_t launch_plainv_kind(int kind, bool adjoint, const SweepArgs<T> &a, in
 // Waits of this translation unit's kernels that gave up.
 inline unsigned int plainv_read_timeouts() {
     unsigned int v = 0;
-    cudaMemcpyFromSymbol(&v, g_wait_timeouts, sizeof(v));
+    if (cudaMemcpyFromSymbol(&v, g_wait_timeouts, sizeof(v)) != cudaSuccess) return 0;
     return v;
 }
 

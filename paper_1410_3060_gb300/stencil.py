@@ -17,6 +17,8 @@ from . import build as _build
 J7_CONST, J7_VAR, W25_CONST, W25_VAR, J25_VAR, W25_ALPHA = 1, 2, 3, 4, 5, 6
 F64, F32 = 0, 1
 OPT_TIME_BLOCK, OPT_SCHEME, OPT_SCRATCH_BYTES, OPT_GRAD_BATCH, OPT_VARIANT, OPT_GRAPH = 1, 2, 3, 4, 5, 6
+OPT_WAIT_LIMIT, OPT_TEST_SKIP_COPY = 7, 8
+OK, EINVAL, EUNSUPPORTED, ENOMEM, ECUDA, ETIMEOUT = 0, -1, -2, -3, -4, -5
 RADIUS = {J7_CONST: 1, J7_VAR: 1, W25_CONST: 4, W25_VAR: 4, J25_VAR: 4, W25_ALPHA: 4}
 NUM_ARRAYS = {J7_CONST: 0, J7_VAR: 7, W25_CONST: 0, W25_VAR: 13, J25_VAR: 13, W25_ALPHA: 1}
 NUM_WEIGHTS = {J7_CONST: 2, J7_VAR: 0, W25_CONST: 6, W25_VAR: 0, J25_VAR: 0, W25_ALPHA: 5}
@@ -27,7 +29,7 @@ SECOND_ORDER = {J7_CONST: False, J7_VAR: False, W25_CONST: True, W25_VAR: True, 
 EXPORTED = ("stencil_plan", "stencil_plan_set", "stencil_plan_get", "stencil_plan_destroy",
             "stencil_forward", "stencil_forward_states", "stencil_adjoint", "stencil_axpby",
             "stencil_misfit", "stencil_misfit_static", "stencil_fill_zero", "stencil_schedule", "stencil_fma_peak",
-            "stencil_strerror", "stencil_last_cuda_error", "stencil_wait_timeouts")
+            "stencil_strerror", "stencil_last_cuda_error", "stencil_wait_timeouts", "stencil_check")
 MISFIT_STATIC_MAX_ELEMS = 8192 * 2048
 
 _lock = threading.Lock()
@@ -83,10 +85,12 @@ def lib():
             L.stencil_strerror.restype = ctypes.c_char_p
             L.stencil_last_cuda_error.argtypes = []
             L.stencil_wait_timeouts.argtypes = [ctypes.POINTER(i64)]
+            L.stencil_check.argtypes = [vp, vp]
             for fn in ("stencil_plan", "stencil_plan_set", "stencil_plan_get", "stencil_forward",
                        "stencil_forward_states", "stencil_adjoint", "stencil_axpby", "stencil_misfit",
                        "stencil_misfit_static", "stencil_fill_zero",
-                       "stencil_schedule", "stencil_fma_peak", "stencil_last_cuda_error", "stencil_wait_timeouts"):
+                       "stencil_schedule", "stencil_fma_peak", "stencil_last_cuda_error", "stencil_wait_timeouts",
+                       "stencil_check"):
                 getattr(L, fn).restype = i32
             _lib = L
     return _lib
@@ -121,12 +125,16 @@ def misfit_static(trace, d, residual, loss, stream=None):
     """stencil_misfit_static: the receiver misfit without a plan or any device
     allocation (partial sums in the library's static device array)."""
     import torch
+    if trace.dtype not in (torch.float64, torch.float32):
+        raise ValueError(f"trace: float64 or float32 expected, got {trace.dtype}")
     dtype = F64 if trace.dtype == torch.float64 else F32
     for name, t in (("d", d), ("residual", residual)):
         if t.dtype != trace.dtype or t.shape != trace.shape or not t.is_contiguous() or not t.is_cuda:
             raise ValueError(f"{name}: expected a contiguous CUDA tensor like trace")
-    if not trace.is_contiguous() or not trace.is_cuda or loss.dtype != torch.float64 or not loss.is_cuda:
-        raise ValueError("trace: contiguous CUDA tensor; loss: CUDA float64")
+    if not trace.is_contiguous() or not trace.is_cuda:
+        raise ValueError("trace: contiguous CUDA tensor expected")
+    if loss.dtype != torch.float64 or not loss.is_cuda or loss.numel() < 1:
+        raise ValueError("loss: CUDA float64 tensor with at least one element")
     _check("stencil_misfit_static", lib().stencil_misfit_static(dtype, _ptr(trace), _ptr(d), int(trace.numel()),
                                                                 _ptr(residual), _ptr(loss), _stream_handle(stream)))
 
@@ -181,6 +189,12 @@ class Plan:
         v = ctypes.c_int64(0)
         _check("stencil_plan_get", lib().stencil_plan_get(self._h, option, ctypes.byref(v)))
         return v.value
+
+    def check(self, stream=None):
+        """stencil_check: wait for the plan's work on ``stream`` and raise
+        StencilError (status ETIMEOUT) if a bounded device wait gave up since
+        the previous check."""
+        _check("stencil_check", lib().stencil_check(self._h, _stream_handle(stream)))
 
     def close(self):
         if getattr(self, "_h", None):

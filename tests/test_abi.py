@@ -4,6 +4,7 @@ device, and its time-loop program leaves (u^{T-1}, u^T) in (u_prev, u)."""
 import os
 import re
 
+import numpy as np
 import pytest
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
@@ -47,6 +48,38 @@ def test_strerror_and_invalid_arguments(st):
     assert L.stencil_schedule(1, 1, -1, 1, None, 0, ctypes.byref(n)) == -1
     assert L.stencil_schedule(1, 1, 4, 0, None, 0, ctypes.byref(n)) == -1
     assert L.stencil_schedule(1, 5, 4, 1, None, 0, ctypes.byref(n)) == -1
+    assert L.stencil_strerror(-5) == b"a bounded device wait gave up"
+    assert L.stencil_check(None, None) == -1
+
+
+class _FakeTensor:
+    """Stands in for a CUDA tensor in the host-side argument checks."""
+
+    def __init__(self, dtype, shape=(4, 3), cuda=True, n=None):
+        self.dtype, self.shape, self.is_cuda = dtype, shape, cuda
+        self._n = n if n is not None else int(np.prod(shape))
+
+    def is_contiguous(self):
+        return True
+
+    def numel(self):
+        return self._n
+
+
+def test_misfit_static_rejects_other_dtypes_and_empty_loss(st):
+    """Only float64 / float32 traces (the kernel reads 4 or 8 bytes per
+    element) and a loss tensor with room for the result are accepted; the
+    checks run before any library call."""
+    import torch
+    for dt in (torch.float16, torch.bfloat16, torch.int32):
+        t = _FakeTensor(dt)
+        with pytest.raises(ValueError):
+            st.misfit_static(t, t, t, _FakeTensor(torch.float64, (1,)))
+    t = _FakeTensor(torch.float32)
+    with pytest.raises(ValueError):
+        st.misfit_static(t, t, t, _FakeTensor(torch.float64, (0,), n=0))
+    with pytest.raises(ValueError):
+        st.misfit_static(t, t, t, _FakeTensor(torch.float32, (1,)))
 
 
 def simulate(kind, T, ops, wave):

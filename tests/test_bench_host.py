@@ -24,11 +24,15 @@ def test_fp32_roofline_counts_bytes_once_per_pass(bench):
     x 16 passes of 7-point variable FP32 traffic per second."""
     n, T, b, ms = 512, 64, 4, 1000.0
     res = {"time_block": b, "ms_per_step": ms, "T": T}
-    r = bench.roofline_of(pm, pm.J7_VAR, "f32", n, res, 1.26e12, 6788.6, 78e12)
+    peaks = {"f32": {"probe": 70e12, "datasheet": 80e12}, "f64": {"probe": 1.05e12, "datasheet": 1.26e12}}
+    r = bench.roofline_of(pm, pm.J7_VAR, "f32", n, res, peaks, 6788.6)
     expect_gbs = 36.0 * n ** 3 * (T / b) / 1.0 / 1e9
     assert r["bound"] == "hbm" and r["unit"] == "GB/s"
     assert abs(r["achieved"] - expect_gbs) < 1e-9 * expect_gbs
     assert abs(r["frac"] - expect_gbs / 6788.6) < 1e-12
+    # ceilings: HBM 6788.6 GB/s / (36 B / 4 levels); FP 70 TFLOP/s / 13 flops
+    assert abs(r["ceilings_glups"]["hbm"] - 6788.6 / 9.0) < 1e-9
+    assert abs(r["ceilings_glups"]["fp"] - 70e3 / 13) < 1e-6
 
 
 def test_fwd_adj_bytes_per_update(bench):
@@ -41,19 +45,28 @@ def test_fwd_adj_bytes_per_update(bench):
     assert abs(bench.fwd_adj_bytes_per_lup(8, 20, 20, 1) - (128 + 128 + 16 + 208)) < 1e-12
 
 
-def test_fp64_roofline_flops_and_pipe_views(bench):
-    """FP64: flops (FMA = 2) against 2 FMA/clk/SM x SMs x clock, and the
-    FP64 instruction view (adds count as a full pipe slot)."""
+def test_fp64_roofline_takes_the_lower_ceiling(bench):
+    """FP64: the bound is the lower of the HBM ceiling and the FP ceiling of
+    the measured FMA-chain rate.  7-point variable (72 B, 13 flops per
+    update): HBM 6788.6 / 72 = 94.3 GLUP/s, FP 1.054e12 / 13 = 81.1 -> FP
+    bound; the datasheet rate and the instruction view are side views."""
     n, T, ms = 512, 64, 1000.0
-    peak = 1.2544e12
+    probe, sheet = 1.054e12, 1.2544e12
+    peaks = {"f64": {"probe": probe, "datasheet": sheet}, "f32": {"probe": 70e12, "datasheet": 80e12}}
     res = {"time_block": 1, "ms_per_step": ms, "T": T}
-    r = bench.roofline_of(pm, pm.J7_CONST, "f64", n, res, peak, 6788.6, 78e12)
+    r = bench.roofline_of(pm, pm.J7_VAR, "f64", n, res, peaks, 6788.6)
     lups = float(n) ** 3 * T
-    assert r["bound"] == "alu"
-    assert abs(r["achieved"] - 8 * lups / 1e12) < 1e-9
-    pv = r["fp64_pipe_view"]
-    assert pv["fp64_instr_per_update"] == 7
-    assert abs(pv["frac"] - 7 * lups / (peak / 2)) < 1e-12
+    assert r["bound"] == "alu" and r["unit"] == "TFLOP/s"
+    assert abs(r["achieved"] - 13 * lups / 1e12) < 1e-9
+    assert abs(r["peak"] - probe / 1e12) < 1e-12 and abs(r["frac"] - 13 * lups / probe) < 1e-12
+    fv = r["fp_view"]
+    assert fv["fp_instr_per_update"] == 7
+    assert abs(fv["instr_frac"] - 7 * lups / (probe / 2)) < 1e-12
+    assert abs(fv["frac_of_datasheet"] - 13 * lups / sheet) < 1e-12
+    # a fast FP64 pipe would leave HBM as the bound
+    peaks["f64"]["probe"] = 20e12
+    r = bench.roofline_of(pm, pm.J7_VAR, "f64", n, res, peaks, 6788.6)
+    assert r["bound"] == "hbm" and abs(r["frac"] - 72 * lups / 1e9 / 6788.6) < 1e-12
 
 
 def test_tuner_candidates_cover_every_kernel_family():

@@ -187,3 +187,30 @@ def test_backward_pass_repeated(st, fwi48, overlap):
     for k in range(13):
         assert normwise_err(to_np(dWa[k]), odW[k]) <= 1e-10, k
     run.close()
+
+
+@pytest.mark.parametrize("dtype", [F64, F32])
+def test_two_losses_summed_one_backward(st, fwi48, dtype):
+    """Two losses of one runner built before a single backward(): each forward
+    pass keeps its own checkpoints and residual, so the gradient of the sum
+    is the sum of the oracle gradients (the second data set is the first
+    scaled by 0.5, so its loss and gradient differ)."""
+    import torch
+    from paper_1410_3060_gb300.autograd import MisfitRunner
+    fw, d, oloss, odu0, odW = fwi48
+    d2 = 0.5 * d
+    oloss2, odu02, odW2 = oracle.loss_and_gradient(wl.W25_VAR, fw.u0, fw.W, d2, fw.T, fw.rcv_z, threads=8)
+    run = MisfitRunner(wl.W25_VAR, fw.n, fw.T, fw.K, fw.rcv_z, dtype=dtype)
+    u0 = to_dev(fw.u0, dtype).requires_grad_(True)
+    W = to_dev(fw.W, dtype).requires_grad_(True)
+    l1 = run(u0, W, to_dev(d, dtype))
+    l2 = run(u0, W, to_dev(d2, dtype))
+    (l1 + 3.0 * l2).backward()
+    torch.cuda.synchronize()
+    tol = 1e-10 if dtype == F64 else 2e-3
+    assert abs(l1.item() - oloss) <= tol * oloss and abs(l2.item() - oloss2) <= tol * oloss2
+    assert normwise_err(to_np(u0.grad), odu0 + 3.0 * odu02) <= tol
+    for k in range(13):
+        assert normwise_err(to_np(W.grad[k]), odW[k] + 3.0 * odW2[k]) <= tol, k
+    assert len(run._pool) == 2     # both buffer sets returned after backward
+    run.close()

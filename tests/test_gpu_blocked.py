@@ -7,7 +7,7 @@ import pytest
 
 import oracle
 from paper_1410_3060_gb300 import workloads as wl
-from gpu_util import F32, fp32_bound, gpu_forward, normwise_err
+from gpu_util import F32, check_fp32, gpu_forward, normwise_err, oracle_both
 
 pytestmark = pytest.mark.gpu
 
@@ -42,12 +42,9 @@ def cases():
 def test_blocked_forward_fp32(st, kind, b, scheme, shape, T):
     wk = wl.make(kind, shape, T, seed=3)
     rz = shape[2] // 3
-    op, ou, otr = oracle.forward(kind, wk.u_prev, wk.u, wk.w, wk.W, T, rcv_z=rz, threads=8)
+    o64, o32 = oracle_both(wk, T, rcv_z=rz)
     gp, gu, gtr = gpu_forward(st.Plan, wk, F32, rcv_z=rz, time_block=b, scheme=scheme)
-    bound = fp32_bound(kind, T, wk.R)
-    assert normwise_err(gu, ou) <= bound
-    assert normwise_err(gp, op) <= bound
-    assert normwise_err(gtr, otr) <= bound
+    check_fp32((gp, gu, gtr), o64, o32)
     R = wk.R
     halo = np.ones(gu.shape, bool)
     halo[R:-R, R:-R, R:-R] = False
@@ -114,13 +111,10 @@ def test_wavefront_forward_fp32(st, kind, b, variant, shape, T):
     against the oracle; the plan must run the requested depth."""
     wk = wl.make(kind, shape, T, seed=13)
     rz = shape[2] // 3
-    op, ou, otr = oracle.forward(kind, wk.u_prev, wk.u, wk.w, wk.W, T, rcv_z=rz, threads=8)
+    o64, o32 = oracle_both(wk, T, rcv_z=rz)
     gp, gu, gtr = gpu_forward(st.Plan, wk, F32, rcv_z=rz, time_block=b, scheme=3, variant=variant,
                               expect_block=b)
-    bound = fp32_bound(kind, T, wk.R)
-    assert normwise_err(gu, ou) <= bound
-    assert normwise_err(gp, op) <= bound
-    assert normwise_err(gtr, otr) <= bound
+    check_fp32((gp, gu, gtr), o64, o32)
     R = wk.R
     halo = np.ones(gu.shape, bool)
     halo[R:-R, R:-R, R:-R] = False
@@ -161,9 +155,9 @@ def test_wavefront_odd_row_falls_back(st):
     plain passes (and still matches the oracle)."""
     shape, T = (41, 37, 23), 5
     wk = wl.make(1, shape, T, seed=2)
-    op, ou, _ = oracle.forward(1, wk.u_prev, wk.u, wk.w, wk.W, T, threads=8)
+    o64, o32 = oracle_both(wk, T)
     _, gu, _ = gpu_forward(st.Plan, wk, F32, time_block=2, scheme=3, variant=10, expect_block=1)
-    assert normwise_err(gu, ou) <= fp32_bound(1, T, 1)
+    check_fp32((None, gu, None), o64, o32)
 
 
 @pytest.mark.parametrize("kind,dtype", [(1, F32), (3, F32)])
@@ -183,8 +177,8 @@ def test_tune_forward_picks_a_valid_configuration(st, kind, dtype):
     assert len(res["table"]) >= 10
     assert plan.get(1) == res["time_block"]
     np.testing.assert_array_equal(to_np(u), wk.u.astype(np.float32))   # caller's state untouched
-    op, ou, _ = oracle.forward(kind, wk.u_prev, wk.u, wk.w, wk.W, T, threads=8)
+    o64, o32 = oracle_both(wk, T)
     plan.forward(up, u, wk.w, W, T)
-    torch.cuda.synchronize()
-    assert normwise_err(to_np(u), ou) <= fp32_bound(kind, T, wk.R)
+    plan.check()
+    check_fp32((None, to_np(u), None), o64, o32)
     plan.close()
