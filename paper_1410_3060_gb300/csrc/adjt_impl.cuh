@@ -20,9 +20,11 @@
 // planes p - r and p + r (a register ring of 2R+1 partial sums), so output
 // plane p - R is complete once plane p has arrived.  Three slots: the copies
 // of planes p + 1 and p + 2 run while plane p is summed.  The plane waits are
-// bounded and give up as in the forward sweep: the CTA leaves together after
-// the barrier that follows the wait, the issuing thread waits (bounded) for
-// its copies in flight and counts one timeout.
+// bounded and give up as in the forward sweep: a wait that runs out raises
+// the CTA's abort word, the issuing thread stops issuing after its own wait
+// failed, the CTA agrees on leaving once per unrolled block of planes and
+// after the loop, and the issuing thread waits (bounded) for its copies in
+// flight and counts one timeout.
 #pragma once
 
 namespace stc {
@@ -48,7 +50,9 @@ struct AdjTile {
     static constexpr int NSLOT = 3;
     // bytes one plane's copies deliver (the boxes, zero fill included)
     static constexpr uint32_t BYTES = (uint32_t)sizeof(T) * (SW * SH + 4 * SW * TY + 4 * TX * SH);
-    static constexpr size_t smem = sizeof(T) * (size_t)NSLOT * SLOT + 8 * NSLOT + 128;
+    // slots, one mbarrier per slot, the abort word (16 bytes) and 128 bytes
+    // for the alignment of the first slot
+    static constexpr size_t smem = sizeof(T) * (size_t)NSLOT * SLOT + 8 * NSLOT + 16 + 128;
     static_assert((sizeof(T) * SLOT) % 128 == 0, "128-byte aligned slots");
 };
 
@@ -83,9 +87,16 @@ adjt_kernel(const SweepArgs<T> a, const __grid_constant__ CUtensorMap tm_lam, co
     const int ocx = w * SW + RH + lane * V;          // ... in an x-axis tile
     const int ocy = (R + w) * TX + lane * V;         // ... in a y-axis tile
 
-    // all copies of plane p (interior index) into slot s
+    // bounded waits: whether a wait of this thread gave up; the issuing
+    // thread's last issued plane (the copies possibly in flight when the CTA
+    // leaves are among the last two it issued)
+    bool bad = false;
+    int last_issued = qs - 1;
+    volatile int &abort_word = *reinterpret_cast<volatile int *>(bars + TL::NSLOT);
+    // all copies of plane p (interior index) into slot s (issuing thread)
     auto issue = [&](int p, int s) {
-        if (pv::skip_copy(a.skip_plane, p)) return;   // test hook: this copy never arrives
+        if (bad || pv::skip_copy(a.skip_plane, p)) return;   // stopped, or the test hook's missing copy
+        last_issued = p;
         T *d = sb + s * TL::SLOT;
         uint64_t *bar = &bars[s];
         const int zp = p + R;   // padded plane
@@ -132,6 +143,7 @@ adjt_kernel(const SweepArgs<T> a, const __grid_constant__ CUtensorMap tm_lam, co
         for (int i = 0; i < V; ++i) acc[s][i] = T(0);
 
     if (tid < TL::NSLOT) pv::mbar_init(&bars[tid], 1);
+    if (tid == 0) abort_word = 0;
     pv::mbar_init_fence();
     __syncthreads();
     if (tid == 0) {
@@ -142,20 +154,19 @@ adjt_kernel(const SweepArgs<T> a, const __grid_constant__ CUtensorMap tm_lam, co
     static_assert(RING % TL::NSLOT == 0, "slot of plane p: j mod NSLOT");
 
     const int wlim = pv::wait_limit_of(a.wait_limit);
-    int failed_p = qe;   // CTA-uniform: plane whose wait gave up (qe = none)
-    for (int pb = qs; pb < qe && failed_p == qe; pb += RING) {
+    bool stop = false;   // CTA-uniform: a wait gave up (agreed at a reduction barrier)
+    for (int pb = qs; pb < qe && !stop; pb += RING) {
         static_for<RING>([&](auto jj) {
             constexpr int j = decltype(jj)::value;
             constexpr int s = j % TL::NSLOT;
             const int p = pb + j;
-            if (p >= qe || failed_p != qe) return;
-            // k-th use of a slot completes phase k (parity k & 1); the
-            // barrier also makes every thread done with plane p - 1's slot
-            const bool ok = pv::mbar_wait(&bars[s], (uint32_t)(((p - qs) / TL::NSLOT) & 1), wlim);
-            if (__syncthreads_or(!ok)) {
-                failed_p = p;
-                return;
-            }
+            if (p >= qe) return;
+            // k-th use of a slot completes phase k (parity k & 1)
+            bad |= !pv::mbar_wait_or_abort(&bars[s], (uint32_t)(((p - qs) / TL::NSLOT) & 1), wlim, &abort_word);
+            // the barrier makes every thread done with plane p - 1's slot; the
+            // CTA agrees on leaving once per unrolled block
+            if constexpr (j == RING - 1) stop = __syncthreads_or(bad);
+            else __syncthreads();
             if (tid == 0 && p + 2 < qe) issue(p + 2, (j + 2) % TL::NSLOT);
             const T *sl = sb + s * TL::SLOT;
             if (own && p >= 0 && p < g.nz) {
@@ -245,14 +256,12 @@ adjt_kernel(const SweepArgs<T> a, const __grid_constant__ CUtensorMap tm_lam, co
             if (p + 1 < qe) load_own(p + 1);
         });
     }
-    if (failed_p != qe && tid == 0) {
-        // planes failed_p and failed_p + 1 were issued (or skipped) before
-        // the barrier that stopped the loop: wait, bounded, for those in
-        // flight, then count the timeout
-        for (int k = 0; k < 2 && failed_p + k < qe; ++k) {
-            const int pp = failed_p + k;
+    // a partial last block ends without the block's reduction barrier
+    if (__syncthreads_or(bad) && tid == 0) {
+        // the last two copies issued may still be in flight: wait, bounded,
+        // for each (a completed one returns at once), then count the timeout
+        for (int pp = max(last_issued - 1, qs); pp <= last_issued; ++pp)
             pv::mbar_wait(&bars[(pp - qs) % TL::NSLOT], (uint32_t)(((pp - qs) / TL::NSLOT) & 1), wlim);
-        }
         atomicAdd(&g_wait_timeouts, 1u);
     }
 }

@@ -18,12 +18,17 @@
 // tensor map, completing on a per-slot mbarrier that every thread waits on;
 // the tensor unit zero-fills everything outside the padded array.  The copy
 // then costs no per-thread instructions.  The wait is bounded: a thread
-// whose wait runs out reports it at the CTA barrier that follows every wait
-// (__syncthreads_or), and then the whole CTA leaves the plane loop together
-// -- no thread skips a barrier, nothing more is issued -- the issuing
-// thread waits (bounded again) for the copies it still has in flight, counts
-// one timeout in a device counter and the CTA returns.  stencil_check turns
-// the counter into STENCIL_ETIMEOUT.
+// whose wait runs out raises a shared abort word, and every other wait of
+// the CTA that is still polling sees the word and gives up at once; the
+// issuing thread stops issuing after its own wait failed (so no copy is ever
+// issued into a slot whose copy may still be in flight).  Every thread still
+// passes every barrier; the CTA agrees on leaving at the barrier of the last
+// step of each unrolled block of planes and after the loop
+// (__syncthreads_or -- one reduction barrier per 2R+1 planes: a reduction
+// barrier after every plane cost 13% of the constant wave's speed), then the
+// issuing thread waits (bounded again) for the copies it still has in
+// flight, counts one timeout in a device counter and the CTA returns; its
+// planes are wrong.  stencil_check turns the counter into STENCIL_ETIMEOUT.
 #pragma once
 #include <cuda.h>
 #include <cudaTypedefs.h>
@@ -83,7 +88,9 @@ struct Tile {
     static constexpr int NPS = (KindTraits<KIND>::WAVE ? 1 : 0) + ((KindTraits<KIND>::NARR == 1 && !ADJ) ? 1 : 0);
     static constexpr int PP = TX * TY;           // one per-point plane
     static constexpr size_t smem_of(int pd) {
-        return sizeof(T) * ((size_t)(R + 1 + pd) * SP + (size_t)(R + 1 + pd) * NPS * PP) + 8 * (R + 1 + pd) + 128;
+        // slots, per-point planes, one mbarrier per slot, the abort word
+        // (16 bytes) and 128 bytes for the alignment of the first slot
+        return sizeof(T) * ((size_t)(R + 1 + pd) * SP + (size_t)(R + 1 + pd) * NPS * PP) + 8 * (R + 1 + pd) + 16 + 128;
     }
     // planes in flight: one more with TMA (its copies take no registers) for
     // the constant wave (measured: 448 vs 402 GLUP/s at 512^3) and the
@@ -121,18 +128,32 @@ __device__ __forceinline__ void tma_load_3d(void *dst, const CUtensorMap *map, i
         "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(z), "r"(smem_u32(bar))
         : "memory");
 }
+__device__ __forceinline__ bool mbar_try(uint32_t b, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(b), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
 // wait for phase `parity` of `bar`; false when `limit` polls gave up
 __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity, int limit) {
     const uint32_t b = smem_u32(bar);
-    for (int it = 0; it < limit; ++it) {
-        uint32_t ok;
-        asm volatile(
-            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
-            : "=r"(ok)
-            : "r"(b), "r"(parity)
-            : "memory");
-        if (ok) return true;
+    for (int it = 0; it < limit; ++it)
+        if (mbar_try(b, parity)) return true;
+    return false;
+}
+// the same, also giving up as soon as another thread of the CTA raised the
+// shared abort word; a wait that runs out raises it
+__device__ __forceinline__ bool mbar_wait_or_abort(uint64_t *bar, uint32_t parity, int limit, volatile int *abort_word) {
+    const uint32_t b = smem_u32(bar);
+    if (mbar_try(b, parity)) return true;
+    for (int it = 1; it < limit; ++it) {
+        if (mbar_try(b, parity)) return true;
+        if ((it & 31) == 0 && *abort_word) return false;
     }
+    *abort_word = 1;
     return false;
 }
 
@@ -232,13 +253,22 @@ plainv_kernel(const SweepArgs<T> a, const __grid_constant__ CUtensorMap tm_u,
     const int poff = py * sy + px;
     const int scen = (R + w) * SW + RH + lane * V;     // shared offset of the own vector
     const int pown = w * TX + lane * V;                // offset in a per-point plane
+    // bounded waits: whether a wait of this thread gave up; the issuing
+    // thread's last issued plane (the copies possibly in flight when the CTA
+    // leaves are among the last PD it issued)
+    bool bad = false;
+    int last_issued = qs - 1;
+    volatile int &abort_word = *reinterpret_cast<volatile int *>(bars + NS);   // raised by a wait that ran out
+    (void)bad; (void)last_issued; (void)abort_word;
     // field plane q (tile and halo) and the per-point inputs of output plane
     // q - R into slot `slot`
     auto issue = [&](int q, int slot) {
         if constexpr (TMA) {
             // thread 0: the tile with its halo, and the per-point planes of
             // output plane q - R (outside the padded array: zero fill)
-            if (tid == 0 && !pv::skip_copy(a.skip_plane, q)) {
+            // the issuing thread stops after its own wait failed
+            if (tid == 0 && !bad && !pv::skip_copy(a.skip_plane, q)) {
+                last_issued = q;
                 pv::mbar_expect_tx(&bars[slot], (uint32_t)(sizeof(T) * (SP0 + NPS * PP)));
                 pv::tma_load_3d(sb + slot * SP, &tm_u, x0, y0, q + R, &bars[slot]);
                 if constexpr (KindTraits<KIND>::WAVE)
@@ -279,6 +309,7 @@ plainv_kernel(const SweepArgs<T> a, const __grid_constant__ CUtensorMap tm_u,
 
     if constexpr (TMA) {
         if (tid < NS) pv::mbar_init(&bars[tid], 1);
+        if (tid == 0) abort_word = 0;
         pv::mbar_init_fence();
         __syncthreads();
     }
@@ -294,12 +325,12 @@ plainv_kernel(const SweepArgs<T> a, const __grid_constant__ CUtensorMap tm_u,
     int slot = 0;   // shared slot of plane q
     const int wlim = pv::wait_limit_of(a.wait_limit);
     (void)wlim;
-    int failed_q = qe;  // CTA-uniform: plane whose wait gave up (qe = none)
-    for (int qb = qs; qb < qe && failed_q == qe; qb += RING) {
+    bool stop = false;   // CTA-uniform: a wait gave up (agreed at a reduction barrier)
+    for (int qb = qs; qb < qe && !stop; qb += RING) {
         static_for<RING>([&](auto jj) {
             constexpr int j = decltype(jj)::value;
             const int q = qb + j;
-            if (q >= qe || failed_q != qe) return;
+            if (q >= qe) return;
             const int z = q - R;
             const int64_t zo = (int64_t)(z + R) * sz + poff;
             // 13-array kinds: the coefficients of output plane z, issued before
@@ -318,13 +349,13 @@ plainv_kernel(const SweepArgs<T> a, const __grid_constant__ CUtensorMap tm_u,
                 }
             }
             if constexpr (TMA) {
-                // k-th use of a slot completes phase k (parity k & 1); every
-                // thread learns at the barrier whether any wait gave up
-                const bool ok = pv::mbar_wait(&bars[slot], (uint32_t)(((q - qs) / NS) & 1), wlim);
-                if (__syncthreads_or(!ok)) {
-                    failed_q = q;
-                    return;
-                }
+                // k-th use of a slot completes phase k (parity k & 1)
+                // (after a failure the abort word makes every later wait of
+                // the block give up within a few polls)
+                bad |= !pv::mbar_wait_or_abort(&bars[slot], (uint32_t)(((q - qs) / NS) & 1), wlim, &abort_word);
+                // the CTA agrees on leaving once per unrolled block
+                if constexpr (j == RING - 1) stop = __syncthreads_or(bad);
+                else __syncthreads();
             } else {
                 cp_async_wait<PD - 1>();
                 __syncthreads();
@@ -550,15 +581,14 @@ plainv_kernel(const SweepArgs<T> a, const __grid_constant__ CUtensorMap tm_u,
         });
     }
     if constexpr (TMA) {
-        if (failed_q != qe && tid == 0) {
-            // the copies of planes failed_q .. failed_q + PD - 1 were issued
-            // (or skipped) before the barrier that stopped the loop: wait,
-            // bounded, for those in flight before the CTA's shared memory is
-            // released, then count the timeout
-            for (int k = 0; k < PD && failed_q + k < qe; ++k) {
-                const int qq = failed_q + k;
+        // a partial last block ends without the block's reduction barrier
+        if (__syncthreads_or(bad) && tid == 0) {
+            // the last PD copies the issuing thread issued may still be in
+            // flight: wait, bounded, for each (a completed one returns at
+            // once) before the CTA's shared memory is released, then count
+            // the timeout
+            for (int qq = max(last_issued - PD + 1, qs); qq <= last_issued; ++qq)
                 pv::mbar_wait(&bars[(qq - qs) % NS], (uint32_t)(((qq - qs) / NS) & 1), wlim);
-            }
             atomicAdd(&g_wait_timeouts, 1u);
         }
     } else {

@@ -137,6 +137,11 @@ __global__ void __launch_bounds__(32 * WY) wavefront_kernel(const BlockedArgs<T>
     constexpr int NA = KindTraits<KIND>::NARR;
     static_assert(R == 1 && (KIND == J7_CONST || KIND == J7_VAR), "radius-1 kinds");
     using TL = WfTile<V, NR, WY, B, R, (int)sizeof(T)>;
+    // FP32 pairs of a row updated by packed instructions (sm_100 and later);
+    // measured at 512^3: faster for blocked passes (7-point constant depth
+    // 3: 951 vs 899 GLUP/s, depth 4: 767 vs 621), slower for one-level ones
+    // (521 vs 569)
+    constexpr bool PACK = sizeof(T) == 4 && V == 2 && B >= 2;
     constexpr int RING = TL::RING;
     constexpr int U = RING;               // steps per unrolled block: ring slots are constants
     constexpr int PD = TL::PD, NS = TL::NS;
@@ -203,6 +208,20 @@ __global__ void __launch_bounds__(32 * WY) wavefront_kernel(const BlockedArgs<T>
     }
     (void)wc; (void)wf; (void)pmask;
     const int off0 = r0 * sy + c0;               // in-plane offset of row 0 (used only when in the array)
+    // addressing without per-step 64-bit arithmetic: in-plane offsets of the
+    // thread's rows (a plane has fewer than 2^30 elements), 0 -- a valid
+    // address -- for rows outside the padded array, whose copies read 0 bytes
+    const int szi = (int)sz;
+    uint32_t ro[NR], rb[NR];
+#pragma unroll
+    for (int j = 0; j < NR; ++j) {
+        const bool in = (lmask >> j) & 1u;
+        ro[j] = in ? (uint32_t)(off0 + j * sy) : 0u;
+        rb[j] = in ? (uint32_t)(V * sizeof(T)) : 0u;
+    }
+    // receiver plane if it is one of this chunk's own planes (else a plane
+    // index no level reaches)
+    const int tz = (a.trace && a.rcv_z >= z0 && a.rcv_z < z1) ? a.rcv_z : -(1 << 30);
 
     T r0v[RING][NR][V];
     T rk[NK][RING][NR][V];
@@ -225,15 +244,12 @@ __global__ void __launch_bounds__(32 * WY) wavefront_kernel(const BlockedArgs<T>
     T *const s0t = s0b + (w * NR) * TXE + lane * V;
     // copy level-0 plane q (interior z) into slot `slot`; zeros outside the padded array
     auto issue0 = [&](int q, int slot) {
-        const bool zm = q >= -R && q < g.nz + R;
-        const T *pb = a.u + (zm ? (int64_t)(q + R) * sz : 0);
+        const int qc = min(max(q, -R), g.nz + R - 1);   // a plane of the padded array
+        const uint32_t zmask = qc == q ? ~0u : 0u;       // plane q itself is in the array
+        const T *pb = a.u + (ptrdiff_t)(qc + R) * szi;
         T *d = s0t + slot * S0;
 #pragma unroll
-        for (int j = 0; j < NR; ++j) {
-            const bool ok = zm && ((lmask >> j) & 1u);
-            cp_async_zfill<V * sizeof(T)>(d + j * TXE, ok ? (const void *)(pb + (off0 + j * sy)) : (const void *)a.u,
-                                           ok);
-        }
+        for (int j = 0; j < NR; ++j) cp_async_zfill_n<V * sizeof(T)>(d + j * TXE, pb + ro[j], rb[j] & zmask);
     };
     // plane slot of level m at plane offset p (relative to the block start)
     auto lev = [&](auto mI, auto pI) -> T (&)[NR][V] {
@@ -247,7 +263,7 @@ __global__ void __launch_bounds__(32 * WY) wavefront_kernel(const BlockedArgs<T>
 #pragma unroll
         for (int j = 0; j < NR; ++j) {
             if (!((smask >> j) & 1u)) continue;
-            T *p = base + (off0 + j * sy);
+            T *p = base + ro[j];
             if (call) {
                 vst<T, V>(p, v[j]);
             } else {
@@ -293,14 +309,13 @@ __global__ void __launch_bounds__(32 * WY) wavefront_kernel(const BlockedArgs<T>
             T cf1[NA > 0 ? NR : 1][NA > 0 ? NA : 1][V];
             (void)cf1;
             if constexpr (NA > 0) {
-                const T *cb = a.W + (int64_t)(q - R + R) * sz;
-                const bool zin = q - R >= 0 && q - R < g.nz;
+                const T *cb = a.W + (ptrdiff_t)q * szi;          // plane q - R of array 0
+                const bool zin = (unsigned)(q - R) < (unsigned)g.nz;
 #pragma unroll
                 for (int jr = 0; jr < NR; ++jr) {
                     if (zin && ((lmask >> jr) & 1u)) {
-                        const int o = off0 + jr * sy;
 #pragma unroll
-                        for (int t = 0; t < NA; ++t) vld_g<T, V>(cf1[jr][t], cb + t * g.nfield + o);
+                        for (int t = 0; t < NA; ++t) vld_g<T, V>(cf1[jr][t], cb + t * g.nfield + ro[jr]);
                     } else {
 #pragma unroll
                         for (int t = 0; t < NA; ++t)
@@ -345,7 +360,7 @@ __global__ void __launch_bounds__(32 * WY) wavefront_kernel(const BlockedArgs<T>
                 T(*D)[V];
                 if constexpr (k < B) D = rk[k - 1][cmod(pc, RING)];
                 else D = res;
-                if (k < B && (zk < 0 || zk >= g.nz)) {
+                if (k < B && (unsigned)zk >= (unsigned)g.nz) {
 #pragma unroll
                     for (int jr = 0; jr < NR; ++jr)
 #pragma unroll
@@ -358,7 +373,7 @@ __global__ void __launch_bounds__(32 * WY) wavefront_kernel(const BlockedArgs<T>
                     vld<T, V>(up, xup + j * XP + (k - 1) * XL);
                     vld<T, V>(dn, xdn + j * XP + (k - 1) * XL);
                     const T *cfb = nullptr;
-                    if constexpr (NA > 0) cfb = a.W + (int64_t)(zk + R) * sz;
+                    if constexpr (NA > 0) cfb = a.W + (ptrdiff_t)(zk + R) * szi;
                     (void)cfb;
 #pragma unroll
                     for (int jr = 0; jr < NR; ++jr) {
@@ -377,9 +392,8 @@ __global__ void __launch_bounds__(32 * WY) wavefront_kernel(const BlockedArgs<T>
                                 vld<T, V>(cf[t], cring + ((cs * NA + t) * NR + jr) * CRN + tidv);
                         } else if constexpr (NA > 0) {
                             if ((lmask >> jr) & 1u) {
-                                const int o = off0 + jr * sy;
 #pragma unroll
-                                for (int t = 0; t < NA; ++t) vld_g<T, V>(cf[t], cfb + t * g.nfield + o);
+                                for (int t = 0; t < NA; ++t) vld_g<T, V>(cf[t], cfb + t * g.nfield + ro[jr]);
                             } else {
 #pragma unroll
                                 for (int t = 0; t < NA; ++t)
@@ -389,35 +403,65 @@ __global__ void __launch_bounds__(32 * WY) wavefront_kernel(const BlockedArgs<T>
                         }
                         const T left = __shfl_up_sync(FULLMASK, C[jr][V - 1], 1);
                         const T right = __shfl_down_sync(FULLMASK, C[jr][0], 1);
-#pragma unroll
-                        for (int i = 0; i < V; ++i) {
-                            const T c = C[jr][i];
-                            const T xl = i > 0 ? C[jr][i - 1] : left;
-                            const T xr = i < V - 1 ? C[jr][i + 1] : right;
-                            const T yu = jr > 0 ? C[jr - 1][i] : up[i];
-                            const T yd = jr < NR - 1 ? C[jr + 1][i] : dn[i];
-                            const T zd = Zd[jr][i], zu = Zu[jr][i];
-                            T v;
+                        if constexpr (PACK) {
+                            // FP32 pairs: the two points of the row in one
+                            // packed add / multiply / FMA instruction
+                            // (Blackwell FADD2 / FMUL2 / FFMA2); same terms,
+                            // same order as the scalar form
+                            const float2 c2 = make_float2(C[jr][0], C[jr][1]);
+                            const float2 yu2 = jr > 0 ? make_float2(C[jr - 1][0], C[jr - 1][1]) : make_float2(up[0], up[1]);
+                            const float2 yd2 = jr < NR - 1 ? make_float2(C[jr + 1][0], C[jr + 1][1]) : make_float2(dn[0], dn[1]);
+                            const float2 zd2 = make_float2(Zd[jr][0], Zd[jr][1]), zu2 = make_float2(Zu[jr][0], Zu[jr][1]);
+                            float2 v;
                             if constexpr (KIND == J7_CONST) {
-                                v = wc[jr][i] * c + wf[jr][i] * (((xl + xr) + (yu + yd)) + (zd + zu));
+                                const float2 xs = make_float2(left + C[jr][1], C[jr][0] + right);
+                                const float2 sum = __fadd2_rn(__fadd2_rn(xs, __fadd2_rn(yu2, yd2)), __fadd2_rn(zd2, zu2));
+                                v = __ffma2_rn(make_float2(wc[jr][0], wc[jr][1]), c2,
+                                               __fmul2_rn(make_float2(wf[jr][0], wf[jr][1]), sum));
                             } else {
-                                v = cf[0][i] * c;
-                                v = fma(cf[1][i], xl, v);
-                                v = fma(cf[2][i], xr, v);
-                                v = fma(cf[3][i], yu, v);
-                                v = fma(cf[4][i], yd, v);
-                                v = fma(cf[5][i], zd, v);
-                                v = fma(cf[6][i], zu, v);
-                                v = ((pmask >> (jr * V + i)) & 1u) ? v : T(0);
+                                v = __fmul2_rn(make_float2(cf[0][0], cf[0][1]), c2);
+                                v = __ffma2_rn(make_float2(cf[1][0], cf[1][1]), make_float2(left, C[jr][0]), v);
+                                v = __ffma2_rn(make_float2(cf[2][0], cf[2][1]), make_float2(C[jr][1], right), v);
+                                v = __ffma2_rn(make_float2(cf[3][0], cf[3][1]), yu2, v);
+                                v = __ffma2_rn(make_float2(cf[4][0], cf[4][1]), yd2, v);
+                                v = __ffma2_rn(make_float2(cf[5][0], cf[5][1]), zd2, v);
+                                v = __ffma2_rn(make_float2(cf[6][0], cf[6][1]), zu2, v);
+                                v.x = ((pmask >> (jr * V)) & 1u) ? v.x : 0.0f;
+                                v.y = ((pmask >> (jr * V + 1)) & 1u) ? v.y : 0.0f;
                             }
-                            D[jr][i] = v;
+                            D[jr][0] = v.x;
+                            D[jr][1] = v.y;
+                        } else {
+#pragma unroll
+                            for (int i = 0; i < V; ++i) {
+                                const T c = C[jr][i];
+                                const T xl = i > 0 ? C[jr][i - 1] : left;
+                                const T xr = i < V - 1 ? C[jr][i + 1] : right;
+                                const T yu = jr > 0 ? C[jr - 1][i] : up[i];
+                                const T yd = jr < NR - 1 ? C[jr + 1][i] : dn[i];
+                                const T zd = Zd[jr][i], zu = Zu[jr][i];
+                                T v;
+                                if constexpr (KIND == J7_CONST) {
+                                    v = wc[jr][i] * c + wf[jr][i] * (((xl + xr) + (yu + yd)) + (zd + zu));
+                                } else {
+                                    v = cf[0][i] * c;
+                                    v = fma(cf[1][i], xl, v);
+                                    v = fma(cf[2][i], xr, v);
+                                    v = fma(cf[3][i], yu, v);
+                                    v = fma(cf[4][i], yd, v);
+                                    v = fma(cf[5][i], zd, v);
+                                    v = fma(cf[6][i], zu, v);
+                                    v = ((pmask >> (jr * V + i)) & 1u) ? v : T(0);
+                                }
+                                D[jr][i] = v;
+                            }
                         }
                     }
                 }
-                if (zk == a.rcv_z && a.trace && zk >= z0 && zk < z1) store_trace(a.trace + (k - 1) * plane_elems, D);
+                if (zk == tz) store_trace(a.trace + (k - 1) * plane_elems, D);
                 if constexpr (k == B) {
-                    store_plane(a.out + (int64_t)(zk + R) * sz, D);
-                    if (a.out_prev) store_plane(a.out_prev + (int64_t)(zk + R) * sz, lev(IC<B - 1>{}, IC<pc>{}));
+                    store_plane(a.out + (ptrdiff_t)(zk + R) * szi, D);
+                    if (a.out_prev) store_plane(a.out_prev + (ptrdiff_t)(zk + R) * szi, lev(IC<B - 1>{}, IC<pc>{}));
                 }
             });
             if constexpr (NA > 0 && CR > 0) {
