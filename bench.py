@@ -513,8 +513,17 @@ def run_sweep(args, torch, st, wl, pm, stream, ws, fp_peaks, hbm_peak):
     variant and block depth of every kind and dtype at the given size; one
     JSON line per case."""
     n, T = args.n, args.T
+    from paper_1410_3060_gb300 import tune
     kinds = [KIND_BY_NAME[k] for k in args.sweep_kinds.split(",") if k]
     dtypes = [st.F64 if d == "f64" else st.F32 for d in args.sweep_dtypes.split(",") if d]
+
+    def model_of(kind, dtype, b, scheme, variant):
+        # the GPU block model's record of the configuration (tune.model_candidates)
+        for cb, cs, cv, m in tune.model_candidates(kind, dtype):
+            if (cb, cs, cv) == (b, scheme or 0, variant or 0) or (b == 1 and cb == 1 and cv == variant):
+                return {k: (list(v) if isinstance(v, tuple) else v) for k, v in m.items()}
+        return None
+
     for kind in kinds:
         wk = wl.make(kind, n, T, seed=0) if kind != wl.J7_VAR else wl.j7_var(n, T, seed=0)
         r1 = wl.RADIUS[kind] == 1
@@ -523,6 +532,7 @@ def run_sweep(args, torch, st, wl, pm, stream, ws, fp_peaks, hbm_peak):
                 r, _ = forward_case(torch, st, wl, kind, n, T, dtype, args.steps, 1, ws, stream, time_block=1,
                                     wk=wk, variant=v)
                 r["roofline"] = roofline_of(pm, kind, r["dtype"], n, r, fp_peaks, hbm_peak)
+                r["model"] = model_of(kind, dtype, 1, 0, r["variant"])
                 print(json.dumps({"sweep": r}), flush=True)
             blocked = ((2, 3, 4) if r1 else (2,)) if dtype == st.F32 else ((2,) if r1 else ())
             for b in blocked:
@@ -531,6 +541,7 @@ def run_sweep(args, torch, st, wl, pm, stream, ws, fp_peaks, hbm_peak):
                     r, _ = forward_case(torch, st, wl, kind, n, T, dtype, args.steps, 1, ws, stream,
                                         time_block=b, wk=wk, scheme=sch, variant=v)
                     r["roofline"] = roofline_of(pm, kind, r["dtype"], n, r, fp_peaks, hbm_peak)
+                    r["model"] = model_of(kind, dtype, r["time_block"], sch, v)
                     print(json.dumps({"sweep": r}), flush=True)
         del wk
 

@@ -282,6 +282,28 @@ int stencil_misfit_static(int dtype, const void *trace, const void *d, int64_t n
  * ops and the total count to *n_ops.  Performs no CUDA call. */
 int stencil_schedule(int kind, int dtype, int64_t T, int b, int32_t *ops, int64_t max_ops, int64_t *n_ops);
 
+/* Debug builds (compiled with -DSTENCIL_DEBUG) check every store of a
+ * sweep's result: a store whose target is not an interior point of the
+ * padded array (a sweep never writes the halo or outside the array) is
+ * skipped and its linear element index recorded -- the kernels record and
+ * skip, they never trap.  Into *index: the first such index recorded by the
+ * plan's sweeps since its creation, or -1 if none.  Synchronises the
+ * device.  STENCIL_EUNSUPPORTED in the normal build. */
+int stencil_debug_bad_store(stencil_plan_t plan, int64_t *index);
+
+/* Host-only: the on-chip resources of one pass-kernel configuration -- the
+ * GPU counterpart of the cache block of a wavefront tile (Sect. 5.3): what
+ * one CTA keeps in shared memory while it marches through z.  Into
+ * info[0..5]: dynamic shared memory per CTA (bytes), threads per CTA, the x
+ * and y extent of the points a CTA computes per plane (owned points plus the
+ * overlapped halo of a blocked pass), and the x and y extent of the points it
+ * owns.  Served for the register wavefront (scheme 3, variant 0 = its
+ * default tile or 10-12, every depth it supports: 1-4 FP32, 1-2 FP64, 7-point
+ * kinds) and the vectorised one-level sweep (levels 1, variants 13-16);
+ * STENCIL_EUNSUPPORTED for other families, STENCIL_EINVAL for a bad
+ * argument.  Performs no CUDA call. */
+int stencil_pass_info(int kind, int dtype, int levels, int scheme, int variant, int64_t *info);
+
 /* Measure the device's FP64 (dtype STENCIL_F64) or FP32 fused multiply-add
  * throughput with independent FMA chains on every SM: *flops = flops per
  * second (FMA = 2), *sm_clock_hz = SM clock seen by the kernel's cycle

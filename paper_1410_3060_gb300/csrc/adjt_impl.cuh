@@ -249,7 +249,8 @@ adjt_kernel(const SweepArgs<T> a, const __grid_constant__ CUtensorMap tm_lam, co
                         if (a.trace) a.trace[pl + i] = res[i];
                     }
                 }
-                pv::st16<T>(a.out + (int64_t)(z + R) * g.sz + poff, res);
+                const int64_t zo = (int64_t)(z + R) * g.sz + poff;
+                if (dbg_store_ok(a.dbg, g, zo, V)) pv::st16<T>(a.out + zo, res);
             }
 #pragma unroll
             for (int i = 0; i < V; ++i) acc[jz][i] = T(0);   // now the slot of plane p + R + 1

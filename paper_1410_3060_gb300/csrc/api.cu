@@ -189,6 +189,7 @@ struct stencil_plan_s {
     int wait_limit;        // polls of a bounded mbarrier wait (0 = default)
     int skip_plane;        // test hook of the bounded waits (SKIP_NONE = off)
     uint64_t timeouts_seen;   // device timeout counters at the last stencil_check
+    unsigned long long *dbg;  // debug builds: first out-of-interior store index + 1 of the plan's sweeps
     // CUDA graph of the forward pass program (STENCIL_OPT_GRAPH)
     int graph;
     cudaStream_t cap_stream;
@@ -315,6 +316,7 @@ cudaError_t plain_step(stencil_plan_s *p, bool adjoint, const Scalars &s, const 
         w.rcv_z = (int)rcv_z;
         w.trace = trace;
         w.levels = 1;
+        w.dbg = p->dbg;
         return launch_wavefront<T>(p->kind, w, variant - 9, st, p->num_sms);
     }
     SweepArgs<T> a;
@@ -330,6 +332,7 @@ cudaError_t plain_step(stencil_plan_s *p, bool adjoint, const Scalars &s, const 
     a.inject = inject;
     a.wait_limit = p->wait_limit;
     a.skip_plane = p->skip_plane;
+    a.dbg = p->dbg;
     // the vectorised 25-point sweep (forward and adjoint)
     if (variant >= 13 && variant <= 16 && (!adjoint || kind_radius(p->kind) == 4) &&
         (p->dtype == 1 ? plainv_supported_f32(p->kind, p->g) : plainv_supported_f64(p->kind, p->g)))
@@ -399,6 +402,7 @@ int run_program(stencil_plan_s *p, void *pair_p, void *pair_c, const stencil_coe
             a.rcv_z = (int)rcv_z;
             a.trace = trace ? (T *)trace + t * plane : nullptr;
             a.levels = o.levels;
+            a.dbg = p->dbg;
             cudaError_t e;
             const int scheme = plan_scheme(p), variant = plan_variant(p);
             if (scheme == 3) {
@@ -573,6 +577,8 @@ void free_scratch(stencil_plan_s *p) {
     }
     if (p->partials) cudaFree(p->partials);
     p->partials = nullptr;
+    if (p->dbg) cudaFree(p->dbg);
+    p->dbg = nullptr;
 }
 
 }  // namespace
@@ -623,6 +629,11 @@ int stencil_plan(stencil_plan_t *plan, int kind, int64_t nx, int64_t ny, int64_t
     p->npartials = 1024;
     e = cudaMalloc(&p->partials, p->npartials * sizeof(double));
     if (e != cudaSuccess) { free_scratch(p); delete p; g_last_cuda_error = (int)e; cudaGetLastError(); return STENCIL_ENOMEM; }
+#ifdef STENCIL_DEBUG
+    e = cudaMalloc(&p->dbg, sizeof(unsigned long long));
+    if (e == cudaSuccess) e = cudaMemset(p->dbg, 0, sizeof(unsigned long long));
+    if (e != cudaSuccess) { free_scratch(p); delete p; g_last_cuda_error = (int)e; cudaGetLastError(); return STENCIL_ENOMEM; }
+#endif
     const int st = ensure_bands(p);
     if (st != STENCIL_OK) { free_scratch(p); delete p; return st; }
     *plan = p;
@@ -882,6 +893,31 @@ int stencil_schedule(int kind, int dtype, int64_t T, int b, int32_t *ops, int64_
         memcpy(ops + 6 * i, v, sizeof(v));
     }
     return STENCIL_OK;
+}
+
+int stencil_debug_bad_store(stencil_plan_t p, int64_t *index) {
+    if (!p || !index) return STENCIL_EINVAL;
+    if (!p->dbg) return STENCIL_EUNSUPPORTED;
+    unsigned long long v = 0;
+    cudaError_t e = cudaDeviceSynchronize();
+    if (e == cudaSuccess) e = cudaMemcpy(&v, p->dbg, sizeof(v), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(e);
+    *index = (int64_t)v - 1;
+    return STENCIL_OK;
+}
+
+int stencil_pass_info(int kind, int dtype, int levels, int scheme, int variant, int64_t *info) {
+    if (kind_radius(kind) < 0 || (dtype != STENCIL_F64 && dtype != STENCIL_F32) || !info || levels < 1)
+        return STENCIL_EINVAL;
+    bool ok = false;
+    if (scheme == 3 && (variant == 0 || (variant >= 10 && variant <= 12))) {
+        const int tile = variant ? variant - 9 : 0;
+        ok = dtype == STENCIL_F32 ? wavefront_info_f32(kind, levels, tile, info)
+                                  : wavefront_info_f64(kind, levels, tile, info);
+    } else if (levels == 1 && variant >= 13 && variant <= 16) {
+        ok = dtype == STENCIL_F32 ? plainv_info_f32(kind, variant, info) : plainv_info_f64(kind, variant, info);
+    }
+    return ok ? STENCIL_OK : STENCIL_EUNSUPPORTED;
 }
 
 int stencil_fma_peak(int dtype, void *stream, double *flops, double *sm_clock_hz) {

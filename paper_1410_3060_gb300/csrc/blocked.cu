@@ -366,7 +366,8 @@ blocked_kernel(const BlockedArgs<T> a) {
                                 if (Rw::owned(k, ry)) {
                                     if (z == a.rcv_z && a.trace)
                                         a.trace[(k - 1) * plane_elems + (int64_t)(Y0 + ry) * g.nx + x] = v;
-                                    if constexpr (k == B) a.out[zoff + jr * sy] = v;
+                                    if constexpr (k == B)
+                                        if (dbg_store_ok(a.dbg, g, zoff + jr * sy)) a.out[zoff + jr * sy] = v;
                                 }
                                 if constexpr (PHASE == PH_A && k < B) {
                                     if (Rw::band_store(k, ry)) a.bands[k][zoff + jr * sy] = v;
@@ -380,7 +381,7 @@ blocked_kernel(const BlockedArgs<T> a) {
                         // level B-1 at plane z: the next pass's u^{t-1}
                         if (a.out_prev && in && zown && xown && Rw::owned(B - 1, ry) &&
                             (PHASE != PH_OVL || Rw::owned(B, ry)))
-                            a.out_prev[zoff + jr * sy] = ring[B - 1][jc][jr];
+                            if (dbg_store_ok(a.dbg, g, zoff + jr * sy)) a.out_prev[zoff + jr * sy] = ring[B - 1][jc][jr];
                     } else {
                         ring[k][jc][jr] = v;
                     }

@@ -19,6 +19,7 @@ struct BlockedArgs {
     int levels;
     int zchunk;
     int wA;              // phase-A tile height (diamond scheme)
+    unsigned long long *dbg;   // debug builds: first bad store index + 1 (nullptr otherwise)
 };
 
 bool blocked_supported(int kind, int dtype, int levels);

@@ -71,6 +71,7 @@ struct SweepArgs {
     int variant;         // forward tile variant (0 = default of the kind / dtype)
     int wait_limit;      // polls of a bounded mbarrier wait before it gives up (TMA-staged kernels)
     int skip_plane;      // test hook: the first CTA does not issue the copy of this plane (SKIP_NONE = off)
+    unsigned long long *dbg;   // debug builds: first bad store index + 1 (nullptr otherwise)
 };
 
 // Polls of a bounded mbarrier wait when a plan sets no limit.
@@ -122,6 +123,28 @@ template <int N>
 __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory"); }
 
 __host__ __device__ constexpr int cmod(int a, int m) { return ((a % m) + m) % m; }
+
+// Debug build (-DSTENCIL_DEBUG): every store of a sweep's result checks that
+// its n points, from linear index idx on, are interior points of the padded
+// array (a sweep never writes the halo); a store that fails is skipped and
+// its index recorded in *dbg (the first one wins).  It never traps.  In the
+// normal build the check is the constant true.
+#ifdef STENCIL_DEBUG
+__device__ __forceinline__ bool dbg_store_ok(unsigned long long *dbg, const Geom &g, int64_t idx, int n = 1) {
+    const int R = (g.px - g.nx) / 2;
+    bool ok = idx >= 0 && idx + n <= g.nfield;
+    if (ok) {
+        const int64_t z = idx / g.sz, r = idx - z * g.sz, y = r / g.sy, x = r - y * g.sy;
+        ok = z >= R && z < g.nz + R && y >= R && y < g.ny + R && x >= R && x + n - 1 < g.nx + R;
+    }
+    if (!ok && dbg) atomicCAS(dbg, 0ull, (unsigned long long)(idx + 1));
+    return ok;
+}
+#else
+__device__ __forceinline__ constexpr bool dbg_store_ok(unsigned long long *, const Geom &, int64_t, int = 1) {
+    return true;
+}
+#endif
 
 // Compile-time loop: f(IC<0>{}), ..., f(IC<N-1>{}); the index is a constant
 // expression inside f (used for register-ring slots).

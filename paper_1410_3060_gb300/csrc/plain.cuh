@@ -52,6 +52,9 @@ bool plainv_supported_f64(int kind, const Geom &g);
 // bounded waits of the TMA-staged sweeps that gave up (device counters)
 unsigned int plainv_timeouts_f32();
 unsigned int plainv_timeouts_f64();
+// resources of a forward variant 13-16 (see wavefront_info_f32)
+bool plainv_info_f32(int kind, int variant, int64_t *info);
+bool plainv_info_f64(int kind, int variant, int64_t *info);
 template <typename T>
 cudaError_t launch_plainv_kind(int kind, bool adjoint, const SweepArgs<T> &a, int variant, cudaStream_t st,
                                int num_sms);

@@ -218,7 +218,7 @@ plain_sweep_kernel(const SweepArgs<T> a) {
                             if (a.inject) v += a.inject[pidx];
                             if (a.trace) a.trace[pidx] = v;
                         }
-                        a.out[idx] = v;
+                        if (dbg_store_ok(a.dbg, g, idx)) a.out[idx] = v;
                     }
                 }
             }
@@ -564,7 +564,8 @@ plain_stream_kernel(const SweepArgs<T> a) {
             }
 #pragma unroll
             for (int jr = 0; jr < NR; ++jr)
-                if (rowok & (1u << jr)) outp[jr * sy] = res[jr];
+                if ((rowok & (1u << jr)) && dbg_store_ok(a.dbg, g, (outp - a.out) + (int64_t)jr * sy))
+                    outp[jr * sy] = res[jr];
         });
         blk = (blk + 1 == M) ? 0 : blk + 1;
     }

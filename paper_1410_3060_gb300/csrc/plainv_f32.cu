@@ -5,6 +5,7 @@ namespace stc {
 
 bool plainv_supported_f32(int kind, const Geom &g) { return plainv_supported<float>(kind, g); }
 unsigned int plainv_timeouts_f32() { return plainv_read_timeouts(); }
+bool plainv_info_f32(int kind, int variant, int64_t *info) { return plainv_info<float>(kind, variant, info); }
 
 template cudaError_t launch_plainv_kind<float>(int, bool, const SweepArgs<float> &, int, cudaStream_t, int);
 

@@ -567,14 +567,14 @@ plainv_kernel(const SweepArgs<T> a, const __grid_constant__ CUtensorMap tm_u,
                 }
                 if constexpr (PARTIAL) {
                     if (call) {
-                        pv::st16<T>(a.out + zo, res);
+                        if (dbg_store_ok(a.dbg, g, zo, V)) pv::st16<T>(a.out + zo, res);
                     } else {
                         // a vector that straddles the edge of the interior
 #pragma unroll
                         for (int i = 0; i < V; ++i)
-                            if (cin[i]) a.out[zo + i] = res[i];
+                            if (cin[i] && dbg_store_ok(a.dbg, g, zo + i)) a.out[zo + i] = res[i];
                     }
-                } else {
+                } else if (dbg_store_ok(a.dbg, g, zo, V)) {
                     pv::st16<T>(a.out + zo, res);
                 }
             }
@@ -743,6 +743,40 @@ cudaError_t launch_plainv_kind(int kind, bool adjoint, const SweepArgs<T> &a, in
     const bool big = variant == 14 || variant == 16;
     if (variant >= 15) return launch_plainv_kind_t<T, true>(kind, adjoint, a, big, st, num_sms);
     return launch_plainv_kind_t<T, false>(kind, adjoint, a, big, st, num_sms);
+}
+
+// Resources of a forward configuration (as launch_plainv_kind selects it):
+// dynamic shared memory, threads, tile extents (computed = owned).
+template <typename T, int KIND, int WY, bool TMA>
+bool plainv_info_cfg(int64_t *info) {
+    using TL = pv::Tile<T, KIND, WY, false, TMA>;
+    info[0] = (int64_t)TL::smem;
+    info[1] = 32 * WY;
+    info[2] = info[4] = TL::TX;
+    info[3] = info[5] = TL::TY;
+    return true;
+}
+template <typename T, bool TMA>
+bool plainv_info_t(int kind, bool big, int64_t *info) {
+    switch (kind) {
+    case J7_CONST:
+        if constexpr (sizeof(T) == 8) return big ? plainv_info_cfg<T, J7_CONST, 16, TMA>(info) : plainv_info_cfg<T, J7_CONST, 8, TMA>(info);
+        return false;
+    case J7_VAR:
+        if constexpr (sizeof(T) == 8) return big ? plainv_info_cfg<T, J7_VAR, 16, TMA>(info) : plainv_info_cfg<T, J7_VAR, 8, TMA>(info);
+        return false;
+    case W25_CONST: return big ? plainv_info_cfg<T, W25_CONST, 16, TMA>(info) : plainv_info_cfg<T, W25_CONST, 8, TMA>(info);
+    case W25_VAR: return big ? plainv_info_cfg<T, W25_VAR, 4, TMA>(info) : plainv_info_cfg<T, W25_VAR, 8, TMA>(info);
+    case J25_VAR: return big ? plainv_info_cfg<T, J25_VAR, 4, TMA>(info) : plainv_info_cfg<T, J25_VAR, 8, TMA>(info);
+    case W25_ALPHA: return big ? plainv_info_cfg<T, W25_ALPHA, 16, TMA>(info) : plainv_info_cfg<T, W25_ALPHA, 8, TMA>(info);
+    default: return false;
+    }
+}
+template <typename T>
+bool plainv_info(int kind, int variant, int64_t *info) {
+    if (variant < 13 || variant > 16) return false;
+    const bool big = variant == 14 || variant == 16;
+    return variant >= 15 ? plainv_info_t<T, true>(kind, big, info) : plainv_info_t<T, false>(kind, big, info);
 }
 
 // Waits of this translation unit's kernels that gave up.

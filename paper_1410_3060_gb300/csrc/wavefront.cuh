@@ -12,5 +12,9 @@ bool wavefront_supported(int kind, int dtype, int levels, const Geom &g);
 // Tile variant of the register wavefront (0 = default of the kind / dtype).
 template <typename T>
 cudaError_t launch_wavefront(int kind, const BlockedArgs<T> &a, int tile, cudaStream_t st, int num_sms);
+// Resources of a pass configuration (info[0..5]: dynamic shared memory bytes,
+// threads, computed x / y extent, owned x / y extent); false if not served.
+bool wavefront_info_f32(int kind, int levels, int tile, int64_t *info);
+bool wavefront_info_f64(int kind, int levels, int tile, int64_t *info);
 
 }  // namespace stc

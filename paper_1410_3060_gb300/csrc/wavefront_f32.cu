@@ -18,4 +18,8 @@ cudaError_t launch_wavefront(int kind, const BlockedArgs<T> &a, int tile, cudaSt
 
 template cudaError_t launch_wavefront<float>(int, const BlockedArgs<float> &, int, cudaStream_t, int);
 
+bool wavefront_info_f32(int kind, int levels, int tile, int64_t *info) {
+    return wavefront_info_impl<float>(kind, levels, tile, info);
+}
+
 }  // namespace stc

@@ -10,4 +10,8 @@ cudaError_t launch_wavefront(int kind, const BlockedArgs<T> &a, int tile, cudaSt
 
 template cudaError_t launch_wavefront<double>(int, const BlockedArgs<double> &, int, cudaStream_t, int);
 
+bool wavefront_info_f64(int kind, int levels, int tile, int64_t *info) {
+    return wavefront_info_impl<double>(kind, levels, tile, info);
+}
+
 }  // namespace stc

@@ -258,18 +258,21 @@ __global__ void __launch_bounds__(32 * WY) wavefront_kernel(const BlockedArgs<T>
         if constexpr (m == 0) return r0v[cmod(p, RING)];
         else return rk[m - 1][cmod(p, RING)];
     };
-    // store the owned interior points of a plane
-    auto store_plane = [&](T *base, const T (*v)[V]) {
+    // store the owned interior points of padded plane zp of array arr
+    auto store_plane = [&](T *arr, int zp, const T (*v)[V]) {
+        T *const base = arr + (ptrdiff_t)zp * szi;
 #pragma unroll
         for (int j = 0; j < NR; ++j) {
             if (!((smask >> j) & 1u)) continue;
             T *p = base + ro[j];
+            const int64_t idx = (int64_t)zp * szi + ro[j];
+            (void)idx;
             if (call) {
-                vst<T, V>(p, v[j]);
+                if (dbg_store_ok(a.dbg, g, idx, V)) vst<T, V>(p, v[j]);
             } else {
 #pragma unroll
                 for (int i = 0; i < V; ++i)
-                    if (cin[i]) p[i] = v[j][i];
+                    if (cin[i] && dbg_store_ok(a.dbg, g, idx + i)) p[i] = v[j][i];
             }
         }
     };
@@ -460,8 +463,8 @@ __global__ void __launch_bounds__(32 * WY) wavefront_kernel(const BlockedArgs<T>
                 }
                 if (zk == tz) store_trace(a.trace + (k - 1) * plane_elems, D);
                 if constexpr (k == B) {
-                    store_plane(a.out + (ptrdiff_t)(zk + R) * szi, D);
-                    if (a.out_prev) store_plane(a.out_prev + (ptrdiff_t)(zk + R) * szi, lev(IC<B - 1>{}, IC<pc>{}));
+                    store_plane(a.out, zk + R, D);
+                    if (a.out_prev) store_plane(a.out_prev, zk + R, lev(IC<B - 1>{}, IC<pc>{}));
                 }
             });
             if constexpr (NA > 0 && CR > 0) {
@@ -522,7 +525,55 @@ cudaError_t launch_wf(const BlockedArgs<T> &a, cudaStream_t st, int num_sms) {
     return cudaGetLastError();
 }
 
+// Resources of one configuration (host-side constants, no CUDA call):
+// dynamic shared memory, threads, computed and owned tile extents.
+template <typename T, int KIND, int B, int V, int NR, int WY>
+bool wf_info(int64_t *info) {
+    constexpr int R = KindTraits<KIND>::R;
+    using TL = WfTile<V, NR, WY, B, R, (int)sizeof(T)>;
+    info[0] = (int64_t)wf_smem<T, V, NR, WY, B, R, KindTraits<KIND>::NARR>();
+    info[1] = 32 * WY;
+    info[2] = TL::TXE;
+    info[3] = TL::TYE;
+    info[4] = TL::SX;
+    info[5] = TL::SY;
+    return true;
+}
+
 constexpr int kVec(int elem) { return elem == 4 ? 2 : 2; }
+
+// The tile a variant selects (as launch_tile), resources only.
+template <typename T, int KIND, int B>
+bool tile_info(int tile, int64_t *info) {
+    constexpr int V = kVec((int)sizeof(T));
+    switch (tile) {
+    case 2: return wf_info<T, KIND, B, V, 2, 16>(info);
+    case 3:
+        if constexpr (B <= 3) return wf_info<T, KIND, B, V, 4, 16>(info);
+        else return wf_info<T, KIND, B, V, 2, 16>(info);
+    default: return wf_info<T, KIND, B, V, 4, 8>(info);
+    }
+}
+
+template <typename T, int KIND>
+bool depth_info(int levels, int tile, int64_t *info) {
+    switch (levels) {
+    case 1: return tile_info<T, KIND, 1>(tile, info);
+    case 2: return tile_info<T, KIND, 2>(tile, info);
+    case 3: if constexpr (sizeof(T) == 4) return tile_info<T, KIND, 3>(tile, info); else return false;
+    case 4: if constexpr (sizeof(T) == 4) return tile_info<T, KIND, 4>(tile, info); else return false;
+    default: return false;
+    }
+}
+
+template <typename T>
+bool wavefront_info_impl(int kind, int levels, int tile, int64_t *info) {
+    switch (kind) {
+    case J7_CONST: return depth_info<T, J7_CONST>(levels, tile, info);
+    case J7_VAR: return depth_info<T, J7_VAR>(levels, tile, info);
+    default: return false;
+    }
+}
 
 template <typename T, int KIND, int B>
 cudaError_t launch_tile(const BlockedArgs<T> &a, int tile, cudaStream_t st, int num_sms) {

@@ -70,3 +70,107 @@ def cache_block_bytes(Dw: int, NF: int, Nxb: float, ND: int = 1, R: int = 1) -> 
     N_xb [N_D (D_w^2/2 + D_w N_F) + 2 (D_w + W_w)]."""
     Ww = wavefront_width(Dw, NF, R)
     return Nxb * (ND * Dw * (Dw / 2.0 - R + NF + 1) + 2 * R * (Dw + Ww))
+
+
+# ---------------------------------------------------------------- GPU block model
+# The GPU counterpart of the cache block of Sect. 5.3.  There a wavefront tile
+# of D_w x W_w cells (in y-z) times the untiled x extent must fit the shared
+# L3 cache with its N_D domain-sized streams; the auto-tuner (Sect. 5.1)
+# searches only the tile sizes that fit.  Here one CTA marches a tile through
+# z; what must fit is its on-chip working set:
+#   shared memory  the staged level-0 planes, the y-edge rows every level
+#                  exchanges between warps and, for the coefficient streams,
+#                  the planes level 1 keeps for the levels above it,
+#                  <= 227 KB per CTA;
+#   registers      the 2R+1-plane z ring of every level (the counterpart of
+#                  the wavefront width W_w) for the thread's points, <= 255
+#                  per thread and <= 64 K per SM;
+# and the overlapped halo of a depth-B pass (B R columns and rows on each
+# side, the counterpart of the diamond slopes) makes a CTA compute more
+# points than it owns.  HBM bytes: each stream is read once per pass and the
+# result written once (the halo re-reads hit L2: measured 2.66 B per update
+# against 2.67 algorithmic for the depth-3 7-point constant pass).
+
+SMEM_PER_CTA = 227 * 1024
+REGS_PER_SM = 65536
+MAX_REGS_PER_THREAD = 255
+
+# register wavefront tile variants: (V points per thread along x, NR rows
+# per thread, WY warps); variant 12 keeps 2 rows per thread at depth 4
+_WF_TILES = {10: (2, 4, 8), 11: (2, 2, 16), 12: (2, 4, 16)}
+
+
+def wavefront_tile(variant: int, B: int):
+    """(V, NR, WY) of a register wavefront tile variant (0 = variant 10)."""
+    if variant == 12 and B > 3:
+        return (2, 2, 16)
+    return _WF_TILES.get(variant, _WF_TILES[10])
+
+
+def wavefront_block(kind: int, word: int, B: int, variant: int) -> dict:
+    """On-chip working set of one CTA of the register wavefront (7-point
+    kinds, R = 1) at depth B: shared bytes, threads, computed / owned tile
+    extents, the lower bound of registers per thread (the level rings and
+    the result plane; 8-byte values take two registers), whether it fits,
+    and the computed / owned ratio of the overlapped tile."""
+    R = 1
+    V, NR, WY = wavefront_tile(variant, B)
+    TXE, TYE = 32 * V, WY * NR
+    BR = B * R
+    AX = -(-BR // V) * V
+    SX = (TXE - BR - AX) // V * V
+    SY = TYE - 2 * BR
+    ring = 2 * R + 1
+    NS = 4                                         # level-0 slots (2 planes in flight)
+    base = word * (NS * TYE * TXE + ring * B * WY * 2 * R * TXE)
+    NA = _COEFF_ARRAYS[kind]
+    cring = 0
+    if NA and B >= 2:
+        c = word * (B - 1) * NA * TYE * TXE
+        cring = c if base + c <= SMEM_PER_CTA else 0
+    smem = base + cring
+    threads = 32 * WY
+    per_reg = word // 4
+    regs_min = per_reg * NR * V * (B * ring + 1 + (NA if NA else 2))
+    regs_cap = min(MAX_REGS_PER_THREAD, REGS_PER_SM // threads)
+    fits = SX > 0 and SY > 0 and smem <= SMEM_PER_CTA and regs_min <= regs_cap
+    return {"smem_bytes": smem, "threads": threads, "computed": (TXE, TYE), "owned": (SX, SY),
+            "regs_min": regs_min, "regs_cap": regs_cap, "fits": fits,
+            "redundancy": (TXE * TYE) / float(max(SX * SY, 1)), "coef_ring": cring > 0}
+
+
+def vector_sweep_block(kind: int, word: int, variant: int) -> dict:
+    """On-chip working set of one CTA of the vectorised one-level sweep
+    (tile variants 13-16; 15, 16 staged by TMA): shared bytes, threads, tile
+    extents.  16-byte vectors along x, a ring of R + 1 + PD plane slots (PD
+    planes in flight, 3 where the TMA-staged forward of the constant and
+    alpha-array waves fits it) with the u^{t-1} and alpha planes staged beside
+    the field plane, one mbarrier per slot, an abort word, alignment slack."""
+    R = 4 if kind in (W25_CONST, W25_VAR, J25_VAR, W25_ALPHA) else 1
+    V = 16 // word
+    big, tma = variant in (14, 16), variant >= 15
+    if kind in (W25_VAR, J25_VAR):
+        WY = 4 if big else 8
+    else:
+        WY = 16 if big else 8
+    TX = 32 * V
+    RH = -(-R // V) * V
+    SW, SH = TX + 2 * RH, WY + 2 * R
+    SP = -(-(SW * SH * word) // 128) * 128 // word
+    NPS = (1 if _SECOND_ORDER[kind] else 0) + (1 if _COEFF_ARRAYS[kind] == 1 else 0)
+    PP = TX * WY
+
+    def smem_of(pd):
+        slots = R + 1 + pd
+        return word * (slots * SP + slots * NPS * PP) + 8 * slots + 16 + 128
+
+    deep = tma and _COEFF_ARRAYS[kind] <= 1 and _SECOND_ORDER[kind]
+    PD = 3 if deep and smem_of(3) <= SMEM_PER_CTA else 2
+    return {"smem_bytes": smem_of(PD), "threads": 32 * WY, "computed": (TX, WY), "owned": (TX, WY),
+            "fits": smem_of(PD) <= SMEM_PER_CTA, "redundancy": 1.0, "planes_in_flight": PD}
+
+
+def dram_bytes_per_lup(kind: int, word: int, B: int = 1) -> float:
+    """Modelled HBM bytes per lattice update of a pass of B levels: the plain
+    sweep's streams once per pass (halo re-reads served by L2)."""
+    return gpu_bytes_per_lup(kind, word) / B

@@ -29,7 +29,8 @@ SECOND_ORDER = {J7_CONST: False, J7_VAR: False, W25_CONST: True, W25_VAR: True, 
 EXPORTED = ("stencil_plan", "stencil_plan_set", "stencil_plan_get", "stencil_plan_destroy",
             "stencil_forward", "stencil_forward_states", "stencil_adjoint", "stencil_axpby",
             "stencil_misfit", "stencil_misfit_static", "stencil_fill_zero", "stencil_schedule", "stencil_fma_peak",
-            "stencil_strerror", "stencil_last_cuda_error", "stencil_wait_timeouts", "stencil_check")
+            "stencil_strerror", "stencil_last_cuda_error", "stencil_wait_timeouts", "stencil_check",
+            "stencil_pass_info", "stencil_debug_bad_store")
 MISFIT_STATIC_MAX_ELEMS = 8192 * 2048
 
 _lock = threading.Lock()
@@ -51,7 +52,9 @@ class _Coeffs(ctypes.Structure):
 
 
 def library_path() -> str:
-    return _build.LIB
+    """The library this process loads: the in-tree build, or the file named
+    by the environment variable STENCIL_LIBRARY (e.g. the debug build)."""
+    return os.environ.get("STENCIL_LIBRARY") or _build.LIB
 
 
 def lib():
@@ -86,11 +89,13 @@ def lib():
             L.stencil_last_cuda_error.argtypes = []
             L.stencil_wait_timeouts.argtypes = [ctypes.POINTER(i64)]
             L.stencil_check.argtypes = [vp, vp]
+            L.stencil_pass_info.argtypes = [i32, i32, i32, i32, i32, ctypes.POINTER(i64)]
+            L.stencil_debug_bad_store.argtypes = [vp, ctypes.POINTER(i64)]
             for fn in ("stencil_plan", "stencil_plan_set", "stencil_plan_get", "stencil_forward",
                        "stencil_forward_states", "stencil_adjoint", "stencil_axpby", "stencil_misfit",
                        "stencil_misfit_static", "stencil_fill_zero",
                        "stencil_schedule", "stencil_fma_peak", "stencil_last_cuda_error", "stencil_wait_timeouts",
-                       "stencil_check"):
+                       "stencil_check", "stencil_pass_info", "stencil_debug_bad_store"):
                 getattr(L, fn).restype = i32
             _lib = L
     return _lib
@@ -147,6 +152,17 @@ def fill_zero(t, stream=None):
                                                         _stream_handle(stream)))
 
 
+def pass_info(kind: int, dtype: int, levels: int, scheme: int, variant: int):
+    """stencil_pass_info: on-chip resources of a pass kernel configuration, or
+    None where the library does not describe that family."""
+    buf = (ctypes.c_int64 * 6)()
+    st = lib().stencil_pass_info(kind, dtype, levels, scheme, variant, buf)
+    if st == EUNSUPPORTED:
+        return None
+    _check("stencil_pass_info", st)
+    return {"smem_bytes": buf[0], "threads": buf[1], "computed": (buf[2], buf[3]), "owned": (buf[4], buf[5])}
+
+
 def fma_peak(dtype: int, stream=None):
     """(flops/s, SM clock Hz) of FP64 (dtype 0) or FP32 (1) FMA chains."""
     f, c = ctypes.c_double(0), ctypes.c_double(0)
@@ -195,6 +211,16 @@ class Plan:
         StencilError (status ETIMEOUT) if a bounded device wait gave up since
         the previous check."""
         _check("stencil_check", lib().stencil_check(self._h, _stream_handle(stream)))
+
+    def debug_bad_store(self):
+        """stencil_debug_bad_store: first out-of-interior store index of the
+        plan's sweeps (-1: none); None in the normal build."""
+        v = ctypes.c_int64(0)
+        status = lib().stencil_debug_bad_store(self._h, ctypes.byref(v))
+        if status == EUNSUPPORTED:
+            return None
+        _check("stencil_debug_bad_store", status)
+        return v.value
 
     def close(self):
         if getattr(self, "_h", None):

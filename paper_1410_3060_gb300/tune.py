@@ -1,26 +1,72 @@
-"""Run-time tuning of a plan's pass kernels: the analogue of the paper's
-auto-tuning of the wavefront-diamond tile parameters (Sect. 5.1, the block
-size model of Sect. 5.3 giving the candidates), done by timing each candidate
-on the caller's own data with CUDA events.
+"""Run-time tuning of a plan's pass kernels: the GPU analogue of the paper's
+auto-tuning of the wavefront-diamond tile parameters (Sect. 5.1), whose
+search space is narrowed to the tiles whose cache block fits the cache
+(Sect. 5.3).
 
-Candidates are (time block b, scheme, tile variant) triples the library
-accepts for the plan; a candidate the library rejects is skipped.  The trial
-runs advance copies of the caller's state, never the caller's buffers.
+Candidates are (time block b, scheme, tile variant) triples.  The GPU block
+model (perfmodel.wavefront_block, perfmodel.vector_sweep_block: a CTA's
+shared memory and register ring against 227 KB and the register file, and
+the redundancy of its overlapped halo) proposes them, drops those that do
+not fit, and orders the rest by modelled HBM bytes per update (fewest
+first; then the least redundant tile).  Families the model does not describe
+(the streaming tiles 1-9 and the shared-memory blocked schemes 1 and 2)
+follow, in the model's byte order as well.  Each candidate is then timed on
+the caller's own data with CUDA events -- the measurement decides, as in the
+paper.  A candidate the library rejects is skipped.  The trial runs advance
+copies of the caller's state, never the caller's buffers.
 """
 from __future__ import annotations
 
+from . import perfmodel as pm
 from . import stencil as st
 
 
+def model_candidates(kind: int, dtype: int):
+    """[(b, scheme, variant, model)] for the kind and dtype: the register
+    wavefront (7-point kinds) at every depth and tile, the vectorised sweep
+    tiles (one level), the streaming tiles and the shared-memory blocked
+    schemes, each with its model record; infeasible ones removed, the rest
+    ordered by modelled HBM bytes per update, then redundancy."""
+    word = 8 if dtype == st.F64 else 4
+    r1 = st.RADIUS[kind] == 1
+    out = []
+    depths = (1, 2, 3, 4) if dtype == st.F32 else (1, 2)
+    if r1:
+        for b in depths:
+            for v in (10, 11, 12):
+                m = pm.wavefront_block(kind, word, b, v)
+                m["family"] = "register wavefront"
+                out.append((b, 3, v, m))
+    for v in (13, 14, 15, 16):
+        if r1 and word == 4:
+            continue          # FP32 7-point rows are not 16-byte aligned
+        m = pm.vector_sweep_block(kind, word, v)
+        m["family"] = "vectorised sweep" + (" (TMA)" if v >= 15 else "")
+        out.append((1, 0, v, m))
+    for v in range(1, 10):
+        out.append((1, 0, v, {"family": "streaming tile", "fits": True, "redundancy": 1.0}))
+    blocked = ((2, 3, 4) if r1 else (2,)) if dtype == st.F32 else ((2,) if r1 else ())
+    for b in blocked:
+        for s in (1, 2):
+            out.append((b, s, 0, {"family": "shared-memory blocked", "fits": True, "redundancy": None}))
+    for b, s, v, m in out:
+        m["dram_bytes_per_lup"] = pm.dram_bytes_per_lup(kind, word, b)
+    keep = [c for c in out if c[3]["fits"]]
+    keep.sort(key=lambda c: (c[3]["dram_bytes_per_lup"], c[3]["redundancy"] or 1e9))
+    return keep
+
+
 def default_candidates(plan: st.Plan):
-    """Every one-level tile variant, and every block depth with every blocked
-    kernel family (register wavefront tiles, shared-memory overlapped and
-    diamond tiles)."""
-    out = [(1, 0, v) for v in range(1, 17)]
-    for b in (2, 3, 4):
-        out += [(b, 3, v) for v in (10, 11, 12)]
-        out += [(b, s, 0) for s in (1, 2)]
-    return out
+    """(b, scheme, variant) triples of model_candidates for the plan (every
+    one-level tile variant and every blocked configuration when no plan is
+    given)."""
+    if plan is None:
+        out = [(1, 0, v) for v in range(1, 17)]
+        for b in (2, 3, 4):
+            out += [(b, 3, v) for v in (10, 11, 12)]
+            out += [(b, s, 0) for s in (1, 2)]
+        return out
+    return [(b, s, v) for b, s, v, _ in model_candidates(plan.kind, plan.dtype)]
 
 
 def tune_forward(plan: st.Plan, u_prev, u, w=None, W=None, T: int = 8, candidates=None, reps: int = 2,

@@ -42,3 +42,85 @@ def test_gpu_bytes():
     # no write-allocate on the GPU: FP64 7pt const 16, 7pt var 72, 25pt wave 24, 25pt var wave 128
     assert [pm.gpu_bytes_per_lup(k, 8) for k in (1, 2, 3, 4)] == [16, 72, 24, 128]
     assert [pm.gpu_bytes_per_lup(k, 4) for k in (1, 2, 3, 4)] == [8, 36, 12, 64]
+
+
+# ---- GPU block model (the counterpart of the Sect. 5.3 cache block)
+
+PROFILED = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "profiled_smem.json")))
+
+
+@pytest.fixture(scope="module")
+def st():
+    from paper_1410_3060_gb300 import build, stencil
+    build.build()
+    return stencil
+
+
+def _configs():
+    for kind in (1, 2):
+        for dtype, word in ((1, 4), (0, 8)):
+            for B in (1, 2, 3, 4):
+                for v in (0, 10, 11, 12):
+                    yield ("wf", kind, dtype, word, B, v)
+    for kind in (1, 2, 3, 4, 5, 6):
+        for dtype, word in ((1, 4), (0, 8)):
+            for v in (13, 14, 15, 16):
+                yield ("vec", kind, dtype, word, 1, v)
+
+
+def test_block_model_reproduces_every_kernel_configuration(st):
+    """The model's shared memory, threads and tile extents equal the kernels'
+    own launch constants (stencil_pass_info) for every configuration the
+    library serves."""
+    n = 0
+    for fam, kind, dtype, word, B, v in _configs():
+        ref = st.pass_info(kind, dtype, B, 3 if fam == "wf" else 0, v)
+        if ref is None:
+            continue
+        m = pm.wavefront_block(kind, word, B, v) if fam == "wf" else pm.vector_sweep_block(kind, word, v)
+        assert (m["smem_bytes"], m["threads"], tuple(m["computed"]), tuple(m["owned"])) == (
+            ref["smem_bytes"], ref["threads"], ref["computed"], ref["owned"]), (fam, kind, dtype, B, v)
+        n += 1
+    assert n >= 60
+
+
+@pytest.mark.parametrize("e", PROFILED["entries"])
+def test_block_model_reproduces_profiled_shared_memory(e):
+    """Against ncu's launch__shared_mem_per_block_dynamic of profiled launches."""
+    word = 4 if e["dtype"] == 1 else 8
+    assert pm.wavefront_block(e["kind"], word, e["levels"], e["variant"])["smem_bytes"] == e["smem_bytes"]
+
+
+def test_block_model_limits():
+    """Depth-4 7-point variable tiles: the coefficient ring of 3 planes x 7
+    arrays does not fit beside the other buffers (levels above 1 read their
+    coefficients from L2); the ring's register lower bound grows with the
+    depth and every served tile fits the 128 registers a 512-thread CTA
+    allows; the overlapped halo makes deeper passes more redundant."""
+    m4 = pm.wavefront_block(2, 4, 4, 11)
+    assert not m4["coef_ring"] and m4["fits"]
+    assert pm.wavefront_block(2, 4, 2, 11)["coef_ring"]
+    assert [pm.wavefront_block(1, 4, B, 12)["regs_min"] for B in (1, 2, 3)] == [48, 72, 96]
+    assert pm.wavefront_block(1, 4, 3, 12)["regs_cap"] == 128
+    red = [pm.wavefront_block(1, 4, B, 12)["redundancy"] for B in (1, 2, 3)]
+    assert red[0] < red[1] < red[2]
+    # a 64 x 64 tile at depth 4 would need 4 x 3 x 8 + 8 + 16 = 120 of 128
+    # registers for its rings alone: the library serves depth 4 with 2 rows
+    # per thread instead
+    assert pm.wavefront_tile(12, 4) == (2, 2, 16)
+
+
+def test_tuner_candidates_follow_the_model():
+    """Candidates are the model's feasible configurations in modelled HBM
+    byte order; the 7-point FP32 list starts with the deepest register
+    wavefront passes and the one-level tiles come last."""
+    from paper_1410_3060_gb300 import tune
+    c = tune.model_candidates(1, 1)
+    bytes_ = [m["dram_bytes_per_lup"] for _, _, _, m in c]
+    assert bytes_ == sorted(bytes_)
+    assert c[0][0] == 4 and c[0][1] == 3 and all(m["fits"] for *_, m in c)
+    assert c[-1][0] == 1
+    # FP32 7-point rows are not 16-byte aligned: no vectorised 16-byte tiles
+    assert not any(v >= 13 for _, _, v, _ in c)
+    c25 = tune.model_candidates(4, 1)
+    assert {v for _, _, v, _ in c25 if v >= 13} == {13, 14, 15, 16}
