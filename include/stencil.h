@@ -89,7 +89,10 @@ enum stencil_option {
        shared-memory planes with diamond (split) tiles in y and overlapped x,
        3 = register wavefront with overlapped tiles (7-point kinds; FP32
        depths 1-4, FP64 depths 1-2; needs an even padded row length, else
-       the plan runs plain passes). */
+       the plan runs plain passes), 4 = two-level pass of the 13-array
+       25-point kinds (W25_VAR, J25_VAR; FP32, depth 2, nx a multiple of 4):
+       plane rings of both levels in shared memory, level-0 planes and
+       u^{t-1} staged by TMA. */
     STENCIL_OPT_SCHEME = 2,
     /* Read-only: bytes of device scratch the plan holds. */
     STENCIL_OPT_SCRATCH_BYTES = 3,

@@ -260,6 +260,7 @@ int default_time_block(const stencil_plan_s *p) {
 // geometry; the shared-memory blocked kernels serve schemes 1 and 2.
 bool pass_supported(const stencil_plan_s *p, int levels) {
     if (plan_scheme(p) == 3) return wavefront_supported(p->kind, p->dtype, levels, p->g);
+    if (plan_scheme(p) == 4) return p->dtype == 1 && blk25_supported_f32(p->kind, levels, p->g);
     return blocked_supported(p->kind, p->dtype, levels);
 }
 
@@ -403,10 +404,14 @@ int run_program(stencil_plan_s *p, void *pair_p, void *pair_c, const stencil_coe
             a.trace = trace ? (T *)trace + t * plane : nullptr;
             a.levels = o.levels;
             a.dbg = p->dbg;
+            a.wait_limit = p->wait_limit;
             cudaError_t e;
             const int scheme = plan_scheme(p), variant = plan_variant(p);
             if (scheme == 3) {
                 e = launch_wavefront<T>(p->kind, a, (variant >= 10 && variant <= 12) ? variant - 9 : 0, st, p->num_sms);
+            } else if (scheme == 4) {
+                if constexpr (sizeof(T) == 4) e = launch_blk25_f32(p->kind, a, st, p->num_sms);
+                else return STENCIL_EUNSUPPORTED;
             } else {
                 if (blocked_scratch_levels(o.levels) > p->nbands) return STENCIL_EUNSUPPORTED;
                 for (int k = 1; k < o.levels; ++k) a.bands[k] = (T *)p->bands[k - 1];
@@ -526,7 +531,7 @@ void free_bands(stencil_plan_s *p) {
 // Allocate the band buffers of the effective block depth (plan time only).
 int ensure_bands(stencil_plan_s *p) {
     const int b = effective_time_block(p);
-    const int need = (b > 1 && plan_scheme(p) != 3) ? blocked_scratch_levels(b) : 0;
+    const int need = (b > 1 && plan_scheme(p) != 3 && plan_scheme(p) != 4) ? blocked_scratch_levels(b) : 0;
     if (need <= p->nbands) return STENCIL_OK;
     free_bands(p);
     for (int i = 0; i < need; ++i) {
@@ -647,12 +652,13 @@ int stencil_plan_set(stencil_plan_t p, int option, int64_t value) {
     case STENCIL_OPT_TIME_BLOCK:
         if (value < 0 || value > 64) return STENCIL_EINVAL;
         if (value > 1 && !blocked_supported(p->kind, p->dtype, (int)value) &&
-            !wavefront_supported(p->kind, p->dtype, (int)value, p->g))
+            !wavefront_supported(p->kind, p->dtype, (int)value, p->g) &&
+            !(p->dtype == STENCIL_F32 && blk25_supported_f32(p->kind, (int)value, p->g)))
             return STENCIL_EUNSUPPORTED;
         p->time_block = (int)value;
         return ensure_bands(p);
     case STENCIL_OPT_SCHEME:
-        if (value < 0 || value > 3) return STENCIL_EINVAL;
+        if (value < 0 || value > 4) return STENCIL_EINVAL;
         p->scheme = (int)value;
         return ensure_bands(p);
     case STENCIL_OPT_VARIANT:

@@ -20,6 +20,7 @@ struct BlockedArgs {
     int zchunk;
     int wA;              // phase-A tile height (diamond scheme)
     unsigned long long *dbg;   // debug builds: first bad store index + 1 (nullptr otherwise)
+    int wait_limit;      // polls of a bounded mbarrier wait (TMA-staged passes)
 };
 
 bool blocked_supported(int kind, int dtype, int levels);

@@ -17,4 +17,9 @@ cudaError_t launch_wavefront(int kind, const BlockedArgs<T> &a, int tile, cudaSt
 bool wavefront_info_f32(int kind, int levels, int tile, int64_t *info);
 bool wavefront_info_f64(int kind, int levels, int tile, int64_t *info);
 
+// Two-level TMA-staged pass of the 13-array 25-point kinds, FP32 (scheme 4;
+// blk25_impl.cuh).
+bool blk25_supported_f32(int kind, int levels, const Geom &g);
+cudaError_t launch_blk25_f32(int kind, const BlockedArgs<float> &a, cudaStream_t st, int num_sms);
+
 }  // namespace stc

@@ -182,3 +182,26 @@ def test_tune_forward_picks_a_valid_configuration(st, kind, dtype):
     plan.check()
     check_fp32((None, to_np(u), None), o64, o32)
     plan.close()
+
+
+# ---- two-level pass of the 13-array 25-point kinds (scheme 4)
+
+B25_SHAPES = [(136, 45, 40), (64, 19, 11), (200, 33, 70), (8, 7, 5)]
+
+
+@pytest.mark.parametrize("kind", [4, 5])
+@pytest.mark.parametrize("shape", B25_SHAPES)
+@pytest.mark.parametrize("T", [9, 4, 2])
+def test_two_level_25pt_pass_fp32(st, kind, shape, T):
+    """Scheme 4 at depth 2 against the oracle (FP32 bar): several tiles in x
+    and y with ragged edges, z chunks, odd and even T (a plain pass for the
+    remainder), receiver traces of both levels; the plan runs depth 2."""
+    wk = wl.make(kind, shape, T, seed=23)
+    rz = shape[2] // 2
+    o64, o32 = oracle_both(wk, T, rcv_z=rz)
+    gp, gu, gtr = gpu_forward(st.Plan, wk, F32, rcv_z=rz, time_block=2, scheme=4, expect_block=2)
+    check_fp32((gp, gu, gtr), o64, o32)
+    R = wk.R
+    halo = np.ones(gu.shape, bool)
+    halo[R:-R, R:-R, R:-R] = False
+    assert not gu[halo].any() and not gp[halo].any()
