@@ -358,7 +358,13 @@ def forward_case(torch, st, wl, kind, n, T, dtype, steps, warmup, ws, stream, ti
 # pass, tile variant); the roofline record reports them scaled to one launch
 # of the benchmarked size, null for any configuration without a profile of
 # its current kernel.
-MEASURED_TRAFFIC = {("j7_var", "f64", 1, 8): (72.5, "profiles/plain_stream_j7_var_256_fp64.md")}
+MEASURED_TRAFFIC = {
+    ("j7_var", "f64", 1, 8): (72.5, "profiles/plain_stream_j7_var_256_fp64.md"),
+    ("j7_const", "f32", 3, 12): (2.53, "profiles/wavefront_j7_const_384_fp32_b3_64x64.md"),
+    ("j7_var", "f32", 2, 11): (18.47, "profiles/wavefront_j7_var_384_fp32_b2_ring.md"),
+    ("w25_var", "f32", 1, 16): (67.88, "profiles/plainv_tma_w25_var_384_fp32.md"),
+    ("w25_const", "f32", 1, 15): (12.22, "profiles/plainv_tma_w25_const_512_fp32.md"),
+}
 
 
 def add_traffic(rec, kind_name, dtype_name, res, n):
@@ -370,11 +376,9 @@ def add_traffic(rec, kind_name, dtype_name, res, n):
 # warp instructions x 32 / updates of the profiled launch): the issue view of
 # their roofline, ceiling = 4 warp instructions per clock per SM
 MEASURED_INSTR = {
-    ("j7_const", "f32", 3, 10): (28.5, "profiles/wavefront_j7_const_512_fp32_b3.md"),
-    ("j7_const", "f32", 3, 12): (26.6, "profiles/wavefront_j7_const_512_fp32_b3_64x64.md"),
-    ("j7_var", "f32", 2, 11): (63.6, "profiles/wavefront_j7_var_384_fp32_b2_ring.md"),
-    ("j7_var", "f32", 4, 11): (70.4, "profiles/wavefront_j7_var_384_fp32_b4.md"),
-    ("w25_const", "f32", 1, 15): (47.3, "profiles/plainv_tma_w25_const_512_fp32.md"),
+    ("j7_const", "f32", 3, 12): (21.9, "profiles/wavefront_j7_const_384_fp32_b3_64x64.md"),
+    ("j7_var", "f32", 2, 11): (46.1, "profiles/wavefront_j7_var_384_fp32_b2_ring.md"),
+    ("w25_const", "f32", 1, 15): (49.5, "profiles/plainv_tma_w25_const_512_fp32.md"),
 }
 
 

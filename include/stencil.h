@@ -302,7 +302,8 @@ int stencil_debug_bad_store(stencil_plan_t plan, int64_t *index);
  * overlapped halo of a blocked pass), and the x and y extent of the points it
  * owns.  Served for the register wavefront (scheme 3, variant 0 = its
  * default tile or 10-12, every depth it supports: 1-4 FP32, 1-2 FP64, 7-point
- * kinds) and the vectorised one-level sweep (levels 1, variants 13-16);
+ * kinds), the two-level pass of the 13-array kinds (scheme 4, levels 2,
+ * FP32) and the vectorised one-level sweep (levels 1, variants 13-16);
  * STENCIL_EUNSUPPORTED for other families, STENCIL_EINVAL for a bad
  * argument.  Performs no CUDA call. */
 int stencil_pass_info(int kind, int dtype, int levels, int scheme, int variant, int64_t *info);

@@ -920,6 +920,8 @@ int stencil_pass_info(int kind, int dtype, int levels, int scheme, int variant, 
         const int tile = variant ? variant - 9 : 0;
         ok = dtype == STENCIL_F32 ? wavefront_info_f32(kind, levels, tile, info)
                                   : wavefront_info_f64(kind, levels, tile, info);
+    } else if (scheme == 4 && levels == 2 && dtype == STENCIL_F32) {
+        ok = blk25_info_f32(kind, info);
     } else if (levels == 1 && variant >= 13 && variant <= 16) {
         ok = dtype == STENCIL_F32 ? plainv_info_f32(kind, variant, info) : plainv_info_f64(kind, variant, info);
     }

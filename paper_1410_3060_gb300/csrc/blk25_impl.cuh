@@ -247,6 +247,19 @@ inline bool blk25_supported(int kind, int levels, const Geom &g) {
            (int64_t)g.px * g.py < ((int64_t)1 << 30);
 }
 
+// Resources (as stencil_pass_info reports them).
+inline bool blk25_info(int kind, int64_t *info) {
+    using namespace b25;
+    if (kind != W25_VAR && kind != J25_VAR) return false;
+    info[0] = (int64_t)smem_of(kind == W25_VAR);
+    info[1] = NT;
+    info[2] = TX1;
+    info[3] = TY1;
+    info[4] = TXO;
+    info[5] = TYO;
+    return true;
+}
+
 inline cudaError_t launch_blk25(int kind, const BlockedArgs<float> &a, cudaStream_t st, int num_sms) {
     using namespace b25;
     const bool wave = kind == W25_VAR;

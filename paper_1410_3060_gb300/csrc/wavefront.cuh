@@ -21,5 +21,6 @@ bool wavefront_info_f64(int kind, int levels, int tile, int64_t *info);
 // blk25_impl.cuh).
 bool blk25_supported_f32(int kind, int levels, const Geom &g);
 cudaError_t launch_blk25_f32(int kind, const BlockedArgs<float> &a, cudaStream_t st, int num_sms);
+bool blk25_info_f32(int kind, int64_t *info);
 
 }  // namespace stc

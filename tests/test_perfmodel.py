@@ -88,7 +88,22 @@ def test_block_model_reproduces_every_kernel_configuration(st):
 def test_block_model_reproduces_profiled_shared_memory(e):
     """Against ncu's launch__shared_mem_per_block_dynamic of profiled launches."""
     word = 4 if e["dtype"] == 1 else 8
-    assert pm.wavefront_block(e["kind"], word, e["levels"], e["variant"])["smem_bytes"] == e["smem_bytes"]
+    if e["family"] == "wavefront":
+        m = pm.wavefront_block(e["kind"], word, e["levels"], e["variant"])
+    elif e["family"] == "vector":
+        m = pm.vector_sweep_block(e["kind"], word, e["variant"])
+    else:
+        m = pm.two_level_block(e["kind"])
+    assert m["smem_bytes"] == e["smem_bytes"]
+
+
+def test_two_level_model_matches_library(st):
+    for kind in (4, 5):
+        ref = st.pass_info(kind, 1, 2, 4, 0)
+        m = pm.two_level_block(kind)
+        assert (m["smem_bytes"], m["threads"], tuple(m["computed"]), tuple(m["owned"])) == (
+            ref["smem_bytes"], ref["threads"], ref["computed"], ref["owned"])
+    assert st.pass_info(4, 0, 2, 4, 0) is None       # FP32 only
 
 
 def test_block_model_limits():
