@@ -119,7 +119,8 @@ enum stencil_option {
        per plane tile, mbarrier completion; the adjoint of W25_VAR and
        J25_VAR then stages every coefficient tile by TMA as well).  A variant
        a kind or geometry cannot use runs the default streaming tile.  The
-       default is the measured best: 12 / 11 for FP32 J7_CONST / J7_VAR, 15
+       default is the measured best: 12 / 11 for FP32 J7_CONST / J7_VAR (the
+       one-level passes of a default J7_CONST plan run 11), 15
        for FP32 W25_CONST, 16 for FP32 W25_ALPHA and for W25_VAR and
        J25_VAR, else a streaming tile. */
     STENCIL_OPT_VARIANT = 5,
