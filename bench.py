@@ -532,7 +532,8 @@ def run_sweep(args, torch, st, wl, pm, stream, ws, fp_peaks, hbm_peak):
         wk = wl.make(kind, n, T, seed=0) if kind != wl.J7_VAR else wl.j7_var(n, T, seed=0)
         r1 = wl.RADIUS[kind] == 1
         for dtype in dtypes:
-            for v in (1, 2, 3, 4, 5, 6, 7, 8, 9) + ((10, 11, 12, 13, 14, 15, 16) if r1 else (13, 14, 15, 16)):
+            wide = (17,) if r1 and dtype == st.F32 else ()
+            for v in (1, 2, 3, 4, 5, 6, 7, 8, 9) + ((10, 11, 12, 13, 14, 15, 16) if r1 else (13, 14, 15, 16)) + wide:
                 r, _ = forward_case(torch, st, wl, kind, n, T, dtype, args.steps, 1, ws, stream, time_block=1,
                                     wk=wk, variant=v)
                 r["roofline"] = roofline_of(pm, kind, r["dtype"], n, r, fp_peaks, hbm_peak)
@@ -540,7 +541,8 @@ def run_sweep(args, torch, st, wl, pm, stream, ws, fp_peaks, hbm_peak):
                 print(json.dumps({"sweep": r}), flush=True)
             blocked = ((2, 3, 4) if r1 else (2,)) if dtype == st.F32 else ((2,) if r1 else ())
             for b in blocked:
-                cases = [(1, None), (2, None)] + ([(3, 10), (3, 11), (3, 12)] if r1 else [])
+                cases = [(1, None), (2, None)] + ([(3, 10), (3, 11), (3, 12)] if r1 else []) + \
+                    ([(3, 17)] if r1 and dtype == st.F32 else [])
                 for sch, v in cases:
                     r, _ = forward_case(torch, st, wl, kind, n, T, dtype, args.steps, 1, ws, stream,
                                         time_block=b, wk=wk, scheme=sch, variant=v)

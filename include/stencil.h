@@ -117,8 +117,12 @@ enum stencil_option {
        (4 rows for the 13-array kinds; needs nx a multiple of 4 in FP32, of
        2 in FP64), 15 and 16 = the same tiles staged by TMA (one tensor copy
        per plane tile, mbarrier completion; the adjoint of W25_VAR and
-       J25_VAR then stages every coefficient tile by TMA as well).  A variant
-       a kind or geometry cannot use runs the default streaming tile.  The
+       J25_VAR then stages every coefficient tile by TMA as well), 17 =
+       FP32 register wavefront tile of 128x32 points, 4 points per thread
+       row and 2 rows per thread (128x16 at depth 4; an FP64 plan rejects
+       it with EUNSUPPORTED).  A
+       variant a kind or geometry cannot use runs the default streaming
+       tile.  The
        default is the measured best: 12 / 11 for FP32 J7_CONST / J7_VAR (the
        one-level passes of a default J7_CONST plan run 11), 15
        for FP32 W25_CONST, 16 for FP32 W25_ALPHA and for W25_VAR and

@@ -225,6 +225,15 @@ bool wavefront_default(const stencil_plan_s *p) {
            wavefront_supported(p->kind, p->dtype, 1, p->g);
 }
 
+// Register wavefront tile of a tile variant: 10-12 -> tiles 1-3 (64-column
+// tiles), 17 -> tile 4 (FP32, 128-column tile of 4 points per thread row);
+// 0 if the variant names no wavefront tile.
+int wf_tile(int variant) {
+    if (variant >= 10 && variant <= 12) return variant - 9;
+    if (variant == 17) return 4;
+    return 0;
+}
+
 int plan_scheme(const stencil_plan_s *p) {
     if (p->scheme) return p->scheme;
     return wavefront_default(p) ? 3 : 2;
@@ -310,7 +319,7 @@ cudaError_t plain_step(stencil_plan_s *p, bool adjoint, const Scalars &s, const 
     // 64 x 32 tile of 2 rows per thread (measured at 512^3: 599 vs 557 GLUP/s
     // for the 64 x 64 tile its blocked passes use)
     if (!p->variant && variant == 12 && p->kind == J7_CONST && p->dtype == 1) variant = 11;
-    if (!adjoint && variant >= 10 && variant <= 12 && wavefront_supported(p->kind, p->dtype, 1, p->g)) {
+    if (!adjoint && wf_tile(variant) && wavefront_supported(p->kind, p->dtype, 1, p->g)) {
         BlockedArgs<T> w;
         memset(&w, 0, sizeof(w));
         w.u = (const T *)in_c;
@@ -322,7 +331,7 @@ cudaError_t plain_step(stencil_plan_s *p, bool adjoint, const Scalars &s, const 
         w.trace = trace;
         w.levels = 1;
         w.dbg = p->dbg;
-        return launch_wavefront<T>(p->kind, w, variant - 9, st, p->num_sms);
+        return launch_wavefront<T>(p->kind, w, wf_tile(variant), st, p->num_sms);
     }
     SweepArgs<T> a;
     memset(&a, 0, sizeof(a));
@@ -412,7 +421,7 @@ int run_program(stencil_plan_s *p, void *pair_p, void *pair_c, const stencil_coe
             cudaError_t e;
             const int scheme = plan_scheme(p), variant = plan_variant(p);
             if (scheme == 3) {
-                e = launch_wavefront<T>(p->kind, a, (variant >= 10 && variant <= 12) ? variant - 9 : 0, st, p->num_sms);
+                e = launch_wavefront<T>(p->kind, a, wf_tile(variant), st, p->num_sms);
             } else if (scheme == 4) {
                 if constexpr (sizeof(T) == 4) e = launch_blk25_f32(p->kind, a, st, p->num_sms);
                 else return STENCIL_EUNSUPPORTED;
@@ -666,7 +675,8 @@ int stencil_plan_set(stencil_plan_t p, int option, int64_t value) {
         p->scheme = (int)value;
         return ensure_bands(p);
     case STENCIL_OPT_VARIANT:
-        if (value < 0 || value > 16) return STENCIL_EINVAL;
+        if (value < 0 || value > 17) return STENCIL_EINVAL;
+        if (value == 17 && p->dtype != STENCIL_F32) return STENCIL_EUNSUPPORTED;
         p->variant = (int)value;
         return STENCIL_OK;
     case STENCIL_OPT_GRAD_BATCH:
@@ -926,8 +936,8 @@ int stencil_pass_info(int kind, int dtype, int levels, int scheme, int variant, 
     if (kind_radius(kind) < 0 || (dtype != STENCIL_F64 && dtype != STENCIL_F32) || !info || levels < 1)
         return STENCIL_EINVAL;
     bool ok = false;
-    if (scheme == 3 && (variant == 0 || (variant >= 10 && variant <= 12))) {
-        const int tile = variant ? variant - 9 : 0;
+    if (scheme == 3 && (variant == 0 || wf_tile(variant))) {
+        const int tile = wf_tile(variant);
         ok = dtype == STENCIL_F32 ? wavefront_info_f32(kind, levels, tile, info)
                                   : wavefront_info_f64(kind, levels, tile, info);
     } else if (scheme == 4 && levels == 2 && dtype == STENCIL_F32) {

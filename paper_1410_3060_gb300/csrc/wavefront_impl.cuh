@@ -141,13 +141,15 @@ __global__ void __launch_bounds__(32 * WY) wavefront_kernel(const BlockedArgs<T>
     // measured at 512^3: faster for blocked passes (7-point constant depth
     // 3: 951 vs 899 GLUP/s, depth 4: 767 vs 621), slower for one-level ones
     // (521 vs 569)
-    constexpr bool PACK = sizeof(T) == 4 && V == 2 && B >= 2;
+    constexpr bool PACK = sizeof(T) == 4 && (V == 2 || V == 4) && B >= 2;
     constexpr int RING = TL::RING;
     constexpr int U = RING;               // steps per unrolled block: ring slots are constants
     constexpr int PD = TL::PD, NS = TL::NS;
     constexpr int TXE = TL::TXE, TYE = TL::TYE, BR = TL::BR, AX = TL::AX, SX = TL::SX, SY = TL::SY;
     static_assert(SX > 0 && SY > 0 && NR >= R, "tile too small for the depth");
     constexpr int NK = B > 1 ? B - 1 : 1;
+    constexpr int GC = (sizeof(T) == 4 && V == 4) ? 2 : 1;   // global chunks per row vector
+    constexpr int GE = V / GC;                               // elements per chunk
     // shared: level-0 planes [NS][WY][NR][32 lanes][V] (each thread copies
     // and reads back only its own points), then the edge rows
     // [U][level m][warp][R top rows, R bottom rows][TXE]
@@ -209,16 +211,40 @@ __global__ void __launch_bounds__(32 * WY) wavefront_kernel(const BlockedArgs<T>
     (void)wc; (void)wf; (void)pmask;
     const int off0 = r0 * sy + c0;               // in-plane offset of row 0 (used only when in the array)
     // addressing without per-step 64-bit arithmetic: in-plane offsets of the
-    // thread's rows (a plane has fewer than 2^30 elements), 0 -- a valid
-    // address -- for rows outside the padded array, whose copies read 0 bytes
+    // thread's row chunks (a plane has fewer than 2^30 elements), 0 -- a
+    // valid address -- for chunks outside the padded array, whose copies
+    // read 0 bytes.  A global row vector is GC chunks of GE elements: FP32
+    // vectors of 4 go as two 8-byte halves, since a padded row of even
+    // length keeps the rows 8-byte aligned only.
     const int szi = (int)sz;
-    uint32_t ro[NR], rb[NR];
+    uint32_t ro[NR][GC], rb[NR][GC];
 #pragma unroll
     for (int j = 0; j < NR; ++j) {
         const bool in = (lmask >> j) & 1u;
-        ro[j] = in ? (uint32_t)(off0 + j * sy) : 0u;
-        rb[j] = in ? (uint32_t)(V * sizeof(T)) : 0u;
+#pragma unroll
+        for (int h = 0; h < GC; ++h) {
+            const bool hin = in && c0 + h * GE < g.px;
+            ro[j][h] = hin ? (uint32_t)(off0 + j * sy + h * GE) : 0u;
+            rb[j][h] = hin ? (uint32_t)(GE * sizeof(T)) : 0u;
+        }
     }
+    // coefficient vector of the thread's row jr from the plane at cb (zeros
+    // for chunks outside the padded array)
+    auto ldcoef = [&](T (&d)[V], const T *cb, int jr) {
+#pragma unroll
+        for (int h = 0; h < GC; ++h) {
+            T c[GE];
+            if (rb[jr][h]) {
+                vld_g<T, GE>(c, cb + ro[jr][h]);
+            } else {
+#pragma unroll
+                for (int i = 0; i < GE; ++i) c[i] = T(0);
+            }
+#pragma unroll
+            for (int i = 0; i < GE; ++i) d[h * GE + i] = c[i];
+        }
+    };
+    (void)ldcoef;
     // receiver plane if it is one of this chunk's own planes (else a plane
     // index no level reaches)
     const int tz = (a.trace && a.rcv_z >= z0 && a.rcv_z < z1) ? a.rcv_z : -(1 << 30);
@@ -250,17 +276,23 @@ __global__ void __launch_bounds__(32 * WY) wavefront_kernel(const BlockedArgs<T>
             const uint32_t zmask = qc == q ? ~0u : 0u;       // plane q itself is in the array
             const T *pb = a.u + (ptrdiff_t)(qc + R) * szi;
 #pragma unroll
-            for (int j = 0; j < NR; ++j) cp_async_zfill_n<V * sizeof(T)>(d + j * TXE, pb + ro[j], rb[j] & zmask);
+            for (int j = 0; j < NR; ++j)
+#pragma unroll
+                for (int h = 0; h < GC; ++h)
+                    cp_async_zfill_n<GE * sizeof(T)>(d + j * TXE + h * GE, pb + ro[j][h], rb[j][h] & zmask);
         } else {
             // one-level variable-coefficient pass: the select form (measured
             // 180 vs 167 GLUP/s at 512^3 FP32)
             const bool zm = q >= -R && q < g.nz + R;
             const T *pb = a.u + (zm ? (int64_t)(q + R) * sz : 0);
 #pragma unroll
-            for (int j = 0; j < NR; ++j) {
-                const bool ok = zm && ((lmask >> j) & 1u);
-                cp_async_zfill<V * sizeof(T)>(d + j * TXE, ok ? (const void *)(pb + (off0 + j * sy)) : (const void *)a.u, ok);
-            }
+            for (int j = 0; j < NR; ++j)
+#pragma unroll
+                for (int h = 0; h < GC; ++h) {
+                    const bool ok = zm && rb[j][h] != 0u;
+                    cp_async_zfill<GE * sizeof(T)>(d + j * TXE + h * GE,
+                                                   ok ? (const void *)(pb + ro[j][h]) : (const void *)a.u, ok);
+                }
         }
     };
     // plane slot of level m at plane offset p (relative to the block start)
@@ -276,11 +308,19 @@ __global__ void __launch_bounds__(32 * WY) wavefront_kernel(const BlockedArgs<T>
 #pragma unroll
         for (int j = 0; j < NR; ++j) {
             if (!((smask >> j) & 1u)) continue;
-            T *p = base + ro[j];
-            const int64_t idx = (int64_t)zp * szi + ro[j];
+            T *p = base + ro[j][0];
+            const int64_t idx = (int64_t)zp * szi + ro[j][0];
             (void)idx;
             if (call) {
-                if (dbg_store_ok(a.dbg, g, idx, V)) vst<T, V>(p, v[j]);
+                if (dbg_store_ok(a.dbg, g, idx, V)) {
+#pragma unroll
+                    for (int h = 0; h < GC; ++h) {
+                        T c[GE];
+#pragma unroll
+                        for (int i = 0; i < GE; ++i) c[i] = v[j][h * GE + i];
+                        vst<T, GE>(p + h * GE, c);
+                    }
+                }
             } else {
 #pragma unroll
                 for (int i = 0; i < V; ++i)
@@ -330,7 +370,7 @@ __global__ void __launch_bounds__(32 * WY) wavefront_kernel(const BlockedArgs<T>
                 for (int jr = 0; jr < NR; ++jr) {
                     if (zin && ((lmask >> jr) & 1u)) {
 #pragma unroll
-                        for (int t = 0; t < NA; ++t) vld_g<T, V>(cf1[jr][t], cb + t * g.nfield + ro[jr]);
+                        for (int t = 0; t < NA; ++t) ldcoef(cf1[jr][t], cb + t * g.nfield, jr);
                     } else {
 #pragma unroll
                         for (int t = 0; t < NA; ++t)
@@ -408,7 +448,7 @@ __global__ void __launch_bounds__(32 * WY) wavefront_kernel(const BlockedArgs<T>
                         } else if constexpr (NA > 0) {
                             if ((lmask >> jr) & 1u) {
 #pragma unroll
-                                for (int t = 0; t < NA; ++t) vld_g<T, V>(cf[t], cfb + t * g.nfield + ro[jr]);
+                                for (int t = 0; t < NA; ++t) ldcoef(cf[t], cfb + t * g.nfield, jr);
                             } else {
 #pragma unroll
                                 for (int t = 0; t < NA; ++t)
@@ -419,33 +459,42 @@ __global__ void __launch_bounds__(32 * WY) wavefront_kernel(const BlockedArgs<T>
                         const T left = __shfl_up_sync(FULLMASK, C[jr][V - 1], 1);
                         const T right = __shfl_down_sync(FULLMASK, C[jr][0], 1);
                         if constexpr (PACK) {
-                            // FP32 pairs: the two points of the row in one
-                            // packed add / multiply / FMA instruction
-                            // (Blackwell FADD2 / FMUL2 / FFMA2); same terms,
-                            // same order as the scalar form
-                            const float2 c2 = make_float2(C[jr][0], C[jr][1]);
-                            const float2 yu2 = jr > 0 ? make_float2(C[jr - 1][0], C[jr - 1][1]) : make_float2(up[0], up[1]);
-                            const float2 yd2 = jr < NR - 1 ? make_float2(C[jr + 1][0], C[jr + 1][1]) : make_float2(dn[0], dn[1]);
-                            const float2 zd2 = make_float2(Zd[jr][0], Zd[jr][1]), zu2 = make_float2(Zu[jr][0], Zu[jr][1]);
-                            float2 v;
-                            if constexpr (KIND == J7_CONST) {
-                                const float2 xs = make_float2(left + C[jr][1], C[jr][0] + right);
-                                const float2 sum = __fadd2_rn(__fadd2_rn(xs, __fadd2_rn(yu2, yd2)), __fadd2_rn(zd2, zu2));
-                                v = __ffma2_rn(make_float2(wc[jr][0], wc[jr][1]), c2,
-                                               __fmul2_rn(make_float2(wf[jr][0], wf[jr][1]), sum));
-                            } else {
-                                v = __fmul2_rn(make_float2(cf[0][0], cf[0][1]), c2);
-                                v = __ffma2_rn(make_float2(cf[1][0], cf[1][1]), make_float2(left, C[jr][0]), v);
-                                v = __ffma2_rn(make_float2(cf[2][0], cf[2][1]), make_float2(C[jr][1], right), v);
-                                v = __ffma2_rn(make_float2(cf[3][0], cf[3][1]), yu2, v);
-                                v = __ffma2_rn(make_float2(cf[4][0], cf[4][1]), yd2, v);
-                                v = __ffma2_rn(make_float2(cf[5][0], cf[5][1]), zd2, v);
-                                v = __ffma2_rn(make_float2(cf[6][0], cf[6][1]), zu2, v);
-                                v.x = ((pmask >> (jr * V)) & 1u) ? v.x : 0.0f;
-                                v.y = ((pmask >> (jr * V + 1)) & 1u) ? v.y : 0.0f;
+                            // FP32 pairs: two points of the row in one packed
+                            // add / multiply / FMA instruction (Blackwell
+                            // FADD2 / FMUL2 / FFMA2); same terms, same order
+                            // as the scalar form
+#pragma unroll
+                            for (int pp = 0; pp < V / 2; ++pp) {
+                                const int i0 = 2 * pp, i1 = 2 * pp + 1;
+                                const float xl0 = i0 > 0 ? C[jr][i0 - 1] : left;    // x - 1 of point i0
+                                const float xr1 = i1 < V - 1 ? C[jr][i1 + 1] : right;  // x + 1 of point i1
+                                const float2 c2 = make_float2(C[jr][i0], C[jr][i1]);
+                                const float2 yu2 = jr > 0 ? make_float2(C[jr - 1][i0], C[jr - 1][i1])
+                                                          : make_float2(up[i0], up[i1]);
+                                const float2 yd2 = jr < NR - 1 ? make_float2(C[jr + 1][i0], C[jr + 1][i1])
+                                                               : make_float2(dn[i0], dn[i1]);
+                                const float2 zd2 = make_float2(Zd[jr][i0], Zd[jr][i1]);
+                                const float2 zu2 = make_float2(Zu[jr][i0], Zu[jr][i1]);
+                                float2 v;
+                                if constexpr (KIND == J7_CONST) {
+                                    const float2 xs = make_float2(xl0 + C[jr][i1], C[jr][i0] + xr1);
+                                    const float2 sum = __fadd2_rn(__fadd2_rn(xs, __fadd2_rn(yu2, yd2)), __fadd2_rn(zd2, zu2));
+                                    v = __ffma2_rn(make_float2(wc[jr][i0], wc[jr][i1]), c2,
+                                                   __fmul2_rn(make_float2(wf[jr][i0], wf[jr][i1]), sum));
+                                } else {
+                                    v = __fmul2_rn(make_float2(cf[0][i0], cf[0][i1]), c2);
+                                    v = __ffma2_rn(make_float2(cf[1][i0], cf[1][i1]), make_float2(xl0, C[jr][i0]), v);
+                                    v = __ffma2_rn(make_float2(cf[2][i0], cf[2][i1]), make_float2(C[jr][i1], xr1), v);
+                                    v = __ffma2_rn(make_float2(cf[3][i0], cf[3][i1]), yu2, v);
+                                    v = __ffma2_rn(make_float2(cf[4][i0], cf[4][i1]), yd2, v);
+                                    v = __ffma2_rn(make_float2(cf[5][i0], cf[5][i1]), zd2, v);
+                                    v = __ffma2_rn(make_float2(cf[6][i0], cf[6][i1]), zu2, v);
+                                    v.x = ((pmask >> (jr * V + i0)) & 1u) ? v.x : 0.0f;
+                                    v.y = ((pmask >> (jr * V + i1)) & 1u) ? v.y : 0.0f;
+                                }
+                                D[jr][i0] = v.x;
+                                D[jr][i1] = v.y;
                             }
-                            D[jr][0] = v.x;
-                            D[jr][1] = v.y;
                         } else {
 #pragma unroll
                             for (int i = 0; i < V; ++i) {
@@ -563,6 +612,10 @@ bool tile_info(int tile, int64_t *info) {
     case 3:
         if constexpr (B <= 3) return wf_info<T, KIND, B, V, 4, 16>(info);
         else return wf_info<T, KIND, B, V, 2, 16>(info);
+    case 4:
+        if constexpr (sizeof(T) != 4) return false;
+        else if constexpr (B <= 3) return wf_info<T, KIND, B, 4, 2, 16>(info);
+        else return wf_info<T, KIND, B, 4, 2, 8>(info);
     default: return wf_info<T, KIND, B, V, 4, 8>(info);
     }
 }
@@ -595,8 +648,17 @@ cudaError_t launch_tile(const BlockedArgs<T> &a, int tile, cudaStream_t st, int 
     case 3:
         if constexpr (B <= 3) return launch_wf<T, KIND, B, V, 4, 16>(a, st, num_sms);   // 64 x 64
         else return launch_wf<T, KIND, B, V, 2, 16>(a, st, num_sms);
+    // FP32, 4 points per thread row (measured at 512^3, T = 64: 7-point
+    // constant depth 3 918 vs 932 GLUP/s for tile 3, depth 2 774 vs 897 for
+    // tile 1; one-level 7-point variable 171 vs 150 for tile 2; 128 x 32
+    // with 4 rows per thread and 128 x 16 tiles were slower still)
+    case 4:   // 128 x 32 (depth 4: 128 x 16, for shared memory)
+        if constexpr (sizeof(T) != 4) break;
+        else if constexpr (B <= 3) return launch_wf<T, KIND, B, 4, 2, 16>(a, st, num_sms);
+        else return launch_wf<T, KIND, B, 4, 2, 8>(a, st, num_sms);
     default: return launch_wf<T, KIND, B, V, 4, 8>(a, st, num_sms);   // 64 x 32, 4 rows per thread
     }
+    return cudaErrorNotSupported;
 }
 
 template <typename T>

@@ -96,14 +96,19 @@ REGS_PER_SM = 65536
 MAX_REGS_PER_THREAD = 255
 
 # register wavefront tile variants: (V points per thread along x, NR rows
-# per thread, WY warps); variant 12 keeps 2 rows per thread at depth 4
-_WF_TILES = {10: (2, 4, 8), 11: (2, 2, 16), 12: (2, 4, 16)}
+# per thread, WY warps); variant 12 keeps 2 rows per thread at depth 4,
+# variant 17 (FP32) takes 8 warps at depth 4
+_WF_TILES = {10: (2, 4, 8), 11: (2, 2, 16), 12: (2, 4, 16), 17: (4, 2, 16)}
+WF_VARIANTS = (10, 11, 12, 17)
+WF_VARIANTS_WIDE = (17,)               # FP32 only: 4 points per thread row
 
 
 def wavefront_tile(variant: int, B: int):
     """(V, NR, WY) of a register wavefront tile variant (0 = variant 10)."""
     if variant == 12 and B > 3:
         return (2, 2, 16)
+    if variant == 17 and B > 3:
+        return (4, 2, 8)
     return _WF_TILES.get(variant, _WF_TILES[10])
 
 

@@ -33,7 +33,9 @@ def model_candidates(kind: int, dtype: int):
     depths = (1, 2, 3, 4) if dtype == st.F32 else (1, 2)
     if r1:
         for b in depths:
-            for v in (10, 11, 12):
+            for v in pm.WF_VARIANTS:
+                if v in pm.WF_VARIANTS_WIDE and word != 4:
+                    continue
                 m = pm.wavefront_block(kind, word, b, v)
                 m["family"] = "register wavefront"
                 out.append((b, 3, v, m))
@@ -65,9 +67,9 @@ def default_candidates(plan: st.Plan):
     one-level tile variant and every blocked configuration when no plan is
     given)."""
     if plan is None:
-        out = [(1, 0, v) for v in range(1, 17)]
+        out = [(1, 0, v) for v in range(1, 18)]
         for b in (2, 3, 4):
-            out += [(b, 3, v) for v in (10, 11, 12)]
+            out += [(b, 3, v) for v in pm.WF_VARIANTS]
             out += [(b, s, 0) for s in (1, 2)]
         return out
     return [(b, s, v) for b, s, v, _ in model_candidates(plan.kind, plan.dtype)]

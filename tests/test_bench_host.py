@@ -72,10 +72,10 @@ def test_fp64_roofline_takes_the_lower_ceiling(bench):
 def test_tuner_candidates_cover_every_kernel_family():
     from paper_1410_3060_gb300 import tune
     c = tune.default_candidates(None)
-    assert set(v for b, s, v in c if b == 1) == set(range(1, 17))
+    assert set(v for b, s, v in c if b == 1) == set(range(1, 18))
     for b in (2, 3, 4):
         fams = {(s, v) for bb, s, v in c if bb == b}
-        assert {(3, 10), (3, 11), (3, 12), (1, 0), (2, 0)} <= fams
+        assert {(3, 10), (3, 11), (3, 12), (3, 17), (1, 0), (2, 0)} <= fams
 
 
 def test_reference_arm_prints_one_contract_line():

@@ -96,14 +96,15 @@ def test_time_block_option_roundtrip(st):
     p.close()
 
 
-# ---- register wavefront (scheme 3; tile variants 10-12 also for one-level passes)
+# ---- register wavefront (scheme 3; tile variants 10-12 and, FP32 only,
+# 17 -- 4 points per thread row -- also for one-level passes)
 
 WF_SHAPES = [(130, 75, 70), (62, 37, 23), (200, 33, 18)]
 
 
 @pytest.mark.parametrize("kind", R1)
 @pytest.mark.parametrize("b", [1, 2, 3, 4])
-@pytest.mark.parametrize("variant", [10, 11, 12])
+@pytest.mark.parametrize("variant", [10, 11, 12, 17])
 @pytest.mark.parametrize("shape", WF_SHAPES)
 @pytest.mark.parametrize("T", [9, 4])
 def test_wavefront_forward_fp32(st, kind, b, variant, shape, T):

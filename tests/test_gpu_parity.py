@@ -217,6 +217,19 @@ def test_vectorised_25pt_sweep(st, kind, dtype, variant, shape):
     check_forward_variant(st, kind, dtype, variant, shape)
 
 
+@pytest.mark.parametrize("kind", KINDS)
+@pytest.mark.parametrize("variant", [17])
+def test_forward_tile_variants_fp32_wide(st, kind, variant):
+    """The FP32-only wavefront tile of 4 points per thread row (the other
+    kinds run their default sweep) against the oracle; an FP64 plan
+    rejects it."""
+    check_forward_variant(st, kind, F32, variant, (150, 45, 40))
+    plan = st.Plan(kind, 16, 16, 16, F64)
+    with pytest.raises(st.StencilError):
+        plan.set(st.OPT_VARIANT, variant)
+    plan.close()
+
+
 def check_forward_variant(st, kind, dtype, variant, shape):
     T = 3
     wk = wl.make(kind, shape, T, seed=8)

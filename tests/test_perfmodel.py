@@ -60,7 +60,7 @@ def _configs():
     for kind in (1, 2):
         for dtype, word in ((1, 4), (0, 8)):
             for B in (1, 2, 3, 4):
-                for v in (0, 10, 11, 12):
+                for v in (0, 10, 11, 12, 17):
                     yield ("wf", kind, dtype, word, B, v)
     for kind in (1, 2, 3, 4, 5, 6):
         for dtype, word in ((1, 4), (0, 8)):
@@ -135,7 +135,10 @@ def test_tuner_candidates_follow_the_model():
     assert bytes_ == sorted(bytes_)
     assert c[0][0] == 4 and c[0][1] == 3 and all(m["fits"] for *_, m in c)
     assert c[-1][0] == 1
-    # FP32 7-point rows are not 16-byte aligned: no vectorised 16-byte tiles
-    assert not any(v >= 13 for _, _, v, _ in c)
+    # FP32 7-point rows are not 16-byte aligned: no vectorised 16-byte
+    # tiles; the wavefront's 4-point rows (8-byte halves) are candidates
+    assert not any(13 <= v <= 16 for _, _, v, _ in c)
+    assert {v for _, _, v, _ in c if v >= 17} == {17}
+    assert not any(v >= 17 for _, _, v, _ in tune.model_candidates(1, 0))
     c25 = tune.model_candidates(4, 1)
     assert {v for _, _, v, _ in c25 if v >= 13} == {13, 14, 15, 16}
