@@ -512,6 +512,68 @@ def fwd_adj_case(torch, st, wl, n, T, K, dtype, steps, warmup, ws, stream, fw=No
     return res, fw
 
 
+def adjoint_bytes_per_lup(kind, elem, levels):
+    """Algorithmic HBM bytes per update of the adjoint sweep of a 7-point
+    kind (no gradient): a pass of `levels` levels reads lam^{t+1} and the
+    coefficient arrays once and writes every level (the gradient needs each
+    one)."""
+    arrays = 7 if kind == 2 else 0
+    return elem * (1 + arrays + levels) / levels
+
+
+def adjoint_case(torch, st, wl, kind, n, T, dtype, steps, warmup, ws, stream, adj_block=None, hbm_peak=None):
+    """The adjoint sweep of a 7-point kind: one step = T adjoint levels of the
+    n^3 lattice with a residual plane injected at every level (no
+    gradient), lam reset from a device copy before every step (outside the
+    events).  GLUP/s = n^3 T / time."""
+    tdt = torch.float64 if dtype == st.F64 else torch.float32
+    wk = wl.make(kind, n, 1, seed=0) if kind != wl.J7_VAR else wl.j7_var(n, 1, seed=0)
+    plan = st.Plan(kind, n, n, n, dtype)
+    if adj_block is not None:
+        plan.set(st.OPT_ADJ_TIME_BLOCK, adj_block)
+    W = torch.from_numpy(wk.W).to("cuda", tdt) if wk.W is not None else None
+    lam0 = torch.from_numpy(wk.u).to("cuda", tdt)
+    l2, l1 = torch.zeros_like(lam0), lam0.clone()
+    g = torch.Generator(device="cuda")
+    g.manual_seed(0)
+    res = torch.rand((T, n, n), device="cuda", generator=g, dtype=tdt)
+    rz = n // 3
+
+    def one():
+        plan.adjoint(l2, l1, wk.w, W, T, residual=res, rcv_z=rz, stream=stream)
+
+    for _ in range(warmup):
+        l2.zero_()
+        l1.copy_(lam0)
+        one()
+    barrier(torch, ws)
+    tot = 0.0
+    for _ in range(steps):
+        l2.zero_()
+        l1.copy_(lam0)
+        with Timer(torch, stream) as t:
+            one()
+        tot += t.ms
+    barrier(torch, ws)
+    plan.check()
+    ms = max_over_ranks(torch, ws, tot / steps)
+    lups = float(n) ** 3 * T
+    b = plan.get(st.OPT_ADJ_TIME_BLOCK)
+    res_ = {"kind": wl.KIND_NAMES[kind] + "_adjoint", "n": n, "T": T, "dtype": "f64" if dtype == st.F64 else "f32",
+            "adjoint_levels_per_pass": b, "ms_per_step": ms, "glups": lups * ws / (ms * 1e-3) / 1e9,
+            "variant": plan.get(st.OPT_VARIANT)}
+    if hbm_peak:
+        bpl = adjoint_bytes_per_lup(kind, 4 if dtype == st.F32 else 8, b)
+        ach = res_["glups"] / ws * bpl
+        res_["roofline"] = {"bound": "hbm", "bytes_per_lup": bpl, "achieved": ach, "peak": hbm_peak, "unit": "GB/s",
+                            "frac": ach / hbm_peak,
+                            "note": "algorithmic bytes: lam^{t+1} and the coefficients once per pass, every level written"}
+    plan.close()
+    del W, lam0, l1, l2, res
+    torch.cuda.empty_cache()
+    return res_
+
+
 def run_sweep(args, torch, st, wl, pm, stream, ws, fp_peaks, hbm_peak):
     """Tuning sweep (the auto-tuning of tile parameters): every forward tile
     variant and block depth of every kind and dtype at the given size; one
@@ -630,6 +692,12 @@ def run_ours(args):
                 r["roofline"]["issue_view"] = iv
             variants.append(r)
         cache.clear()
+        # adjoint sweeps of the 7-point kinds (FP32): two levels per pass (the
+        # default) and one
+        for vk in (wl.J7_VAR, wl.J7_CONST):
+            for ab in (None, 1):
+                variants.append(adjoint_case(torch, st, wl, vk, n, T, st.F32, max(1, args.steps // 2), 1, ws,
+                                             stream, adj_block=ab, hbm_peak=hbm_peak))
         # forward + adjoint of the differentiable wave workload (256^3, T = 200, K = 20)
         fw = None
         for vd in (st.F32, st.F64):

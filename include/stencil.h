@@ -149,7 +149,20 @@ enum stencil_option {
        then waits for a copy that never comes, gives up and returns; no copy
        is left in flight).  -1 = off (default).  Only for tests of the
        ETIMEOUT path, together with a small STENCIL_OPT_WAIT_LIMIT. */
-    STENCIL_OPT_TEST_SKIP_COPY = 8
+    STENCIL_OPT_TEST_SKIP_COPY = 8,
+    /* Time levels per pass of stencil_adjoint (Sect. 4.1 wavefront applied
+       to the transposed sweep): 1 = one level per pass, 2 = passes of two
+       levels for the 7-point kinds (the register wavefront's adjoint; each
+       pass reads lam^{t+1} and the coefficients once and writes lam^t and
+       lam^{t-1}; EUNSUPPORTED for other kinds or where the wavefront does
+       not serve the geometry).  With a gradient, levels are paired only
+       inside a gradient batch (STENCIL_OPT_GRAD_BATCH >= 2); with batch 1
+       every pass is one level.  0 = default: 2 in FP32 where served
+       (measured at 512^3: 7-point variable 168 vs 129 GLUP/s, constant 789
+       vs 584), 1 in FP64 (bound by the FP64 pipe either way).  Passes run
+       the plan's register wavefront tile (variants 10-12), else the 64x64
+       tile.  Reading it gives the depth the adjoint runs. */
+    STENCIL_OPT_ADJ_TIME_BLOCK = 9
 };
 
 typedef struct stencil_plan_s *stencil_plan_t;
@@ -207,7 +220,8 @@ int stencil_forward_states(stencil_plan_t plan, const void *u_prev, const void *
                            const stencil_coeffs_t *coeffs, int64_t T, void *const *states,
                            void *stream, void *trace, int64_t rcv_z);
 
-/* T steps of the adjoint (transposed) sweep, backward in time, for a loss
+/* T steps of the adjoint (transposed) sweep, backward in time (one or two
+ * levels per pass, STENCIL_OPT_ADJ_TIME_BLOCK), for a loss
  * L = sum_n l_n(u^n) with explicit partials g^n = P^T r^n injected on
  * receiver plane rcv_z.  With A the spatial operator and A^T its transpose
  * ((A^T y)(q) = sum_k A_k(q - o_k) y(q - o_k) over interior source points):

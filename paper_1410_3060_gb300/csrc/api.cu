@@ -188,6 +188,7 @@ struct stencil_plan_s {
     int npartials;
     int wait_limit;        // polls of a bounded mbarrier wait (0 = default)
     int skip_plane;        // test hook of the bounded waits (SKIP_NONE = off)
+    int adj_tb;            // levels per adjoint pass (0 = default)
     uint64_t timeouts_seen;   // device timeout counters at the last stencil_check
     unsigned long long *dbg;  // debug builds: first out-of-interior store index + 1 of the plan's sweeps
     // CUDA graph of the forward pass program (STENCIL_OPT_GRAPH)
@@ -273,6 +274,30 @@ bool pass_supported(const stencil_plan_s *p, int levels) {
     return blocked_supported(p->kind, p->dtype, levels);
 }
 
+// Adjoint passes of depth 2 (the register wavefront's adjoint, 7-point
+// kinds, both levels written): served where the wavefront serves a forward
+// pass of depth 2 on the plan's geometry.
+bool adj_pass_supported(const stencil_plan_s *p) {
+    return (p->kind == J7_CONST || p->kind == J7_VAR) && wavefront_supported(p->kind, p->dtype, 2, p->g);
+}
+
+// Default adjoint depth: 2 in FP32 (measured at 512^3, T = 64: J7_VAR 168 vs
+// 129 GLUP/s, J7_CONST 789 vs 584), 1 in FP64 (FP64-pipe bound: 54.0 vs
+// 55.3 for J7_VAR).
+int effective_adj_block(const stencil_plan_s *p) {
+    const int b = p->adj_tb > 0 ? p->adj_tb : (p->dtype == STENCIL_F32 ? 2 : 1);
+    return (b == 2 && adj_pass_supported(p)) ? 2 : 1;
+}
+
+// Tile of the adjoint passes: the plan's register wavefront tile variant
+// 10-12 when one is set, else the 64 x 64 tile (measured at 512^3 FP32:
+// J7_VAR 168 GLUP/s vs 159 for 64 x 32 with 2 rows per thread and 106 with
+// 4; J7_CONST 789 vs 697 and 786).
+int adj_tile(const stencil_plan_s *p) {
+    const int t = wf_tile(p->variant);
+    return (t >= 1 && t <= 3) ? t : 3;
+}
+
 int effective_time_block(const stencil_plan_s *p) {
     int b = p->time_block > 0 ? p->time_block : default_time_block(p);
     if (b > 1 && !pass_supported(p, b)) b = 1;
@@ -355,15 +380,39 @@ cudaError_t plain_step(stencil_plan_s *p, bool adjoint, const Scalars &s, const 
     return launch_plain<T>(p->kind, adjoint, a, st, p->num_sms);
 }
 
+// One depth-2 adjoint pass of the 7-point kinds: lam^{t+1} (in) gives
+// lam^t (into out1, if not null) and lam^{t-1} (into out2); inj1 is the
+// residual plane of the first level (the second level's is the plane before
+// it in the residual stack), added on plane rcv_z.
+template <typename T>
+cudaError_t adjoint_pair(stencil_plan_s *p, const Scalars &s, const stencil_coeffs_t *coeffs, const void *in,
+                         void *out1, void *out2, const T *inj1, int64_t rcv_z, cudaStream_t st) {
+    BlockedArgs<T> a;
+    memset(&a, 0, sizeof(a));
+    a.u = (const T *)in;
+    a.out_prev = (T *)out1;
+    a.out = (T *)out2;
+    a.W = coeffs ? (const T *)coeffs->arrays : nullptr;
+    a.s = s;
+    a.g = p->g;
+    a.rcv_z = (int)rcv_z;
+    a.levels = 2;
+    a.dbg = p->dbg;
+    a.wait_limit = p->wait_limit;
+    a.inject = inj1;
+    a.inject_step = -(int64_t)p->g.nx * p->g.ny;
+    return launch_wavefront_adj<T>(p->kind, a, adj_tile(p), st, p->num_sms);
+}
+
 template <typename T>
 int run_program(stencil_plan_s *p, void *pair_p, void *pair_c, const stencil_coeffs_t *coeffs, int64_t nsteps,
                  cudaStream_t st, bool adjoint, void *trace, const void *inject, int64_t rcv_z,
                  const void *const *fwd_states, double *grad) {
-    const int b = effective_time_block(p);
-    const int kind = p->kind, dtype = p->dtype;
-    (void)kind;
-    (void)dtype;
-    const std::vector<Op> ops = build_program(p->kind, nsteps, b, [&](int L) { return pass_supported(p, L); });
+    // adjoint: the caller sets time_block to the adjoint depth (1 or 2)
+    const int b = adjoint ? p->time_block : effective_time_block(p);
+    const std::vector<Op> ops = build_program(p->kind, nsteps, b, [&](int L) {
+        return adjoint ? (L == 2 && adj_pass_supported(p)) : pass_supported(p, L);
+    });
     void *buf[4] = {pair_p, pair_c, p->scratch[0], p->scratch[1]};
     const Scalars s = fold_scalars(p->kind, coeffs);
     const int64_t plane = (int64_t)p->g.nx * p->g.ny;
@@ -402,8 +451,16 @@ int run_program(stencil_plan_s *p, void *pair_p, void *pair_c, const stencil_coe
                                           (adjoint && inject) ? (const T *)inject + (nsteps - j) * plane : nullptr,
                                           rcv_z, st);
             if (e != cudaSuccess) return cuda_fail(e);
+        } else if (adjoint) {
+            // depth-2 adjoint pass: steps j = t+1 and t+2 (residual planes
+            // nsteps-j and nsteps-j-1); only level 2 is kept
+            if (o.levels != 2 || !adj_pass_supported(p)) return STENCIL_EUNSUPPORTED;
+            const int64_t j = t + 1;
+            cudaError_t e = adjoint_pair<T>(p, s, coeffs, buf[o.in_c], o.out_p >= 0 ? buf[o.out_p] : nullptr,
+                                            buf[o.out_c], inject ? (const T *)inject + (nsteps - j) * plane : nullptr,
+                                            rcv_z, st);
+            if (e != cudaSuccess) return cuda_fail(e);
         } else {
-            if (adjoint) return STENCIL_EUNSUPPORTED;
             BlockedArgs<T> a;
             memset(&a, 0, sizeof(a));
             a.u_prev = (const T *)buf[o.in_p];
@@ -497,19 +554,29 @@ int run_adjoint_ring(stencil_plan_s *p, void *lam_next, void *lam, const stencil
         for (int r = 0; r <= 4; ++r) ga.s.c[r] = coeffs->w[r];
     ga.g = p->g;
     int64_t batch = 0;   // batches launched
-    for (int64_t j = 1; j <= nsteps; ++j) {
+    const bool pairs = effective_adj_block(p) == 2;
+    for (int64_t j = 1; j <= nsteps;) {
         // first sweep of batch b >= 2 overwrites the levels batch b-2's gradient reads
-        if ((j - 1) % G == 0 && batch >= 2) {
+        if (ga.nsteps == 0 && batch >= 2) {
             e = cudaStreamWaitEvent(st, p->ev_grad[batch % 2], 0);
             if (e != cudaSuccess) return cuda_fail(e);
         }
         const T *inj = inject ? (const T *)inject + (nsteps - j) * plane : nullptr;
-        e = plain_step<T>(p, true, s, coeffs, level(j - 2), level(j - 1), level(j), nullptr, inj, rcv_z, st);
+        // depth-2 pass of steps j, j+1 when both fall into this batch: it
+        // writes lam^{m-j} and lam^{m-j-1} into their ring slots
+        const int n = (pairs && j + 1 <= nsteps && ga.nsteps + 2 <= G) ? 2 : 1;
+        if (n == 2)
+            e = adjoint_pair<T>(p, s, coeffs, level(j - 1), level(j), level(j + 1), inj, rcv_z, st);
+        else
+            e = plain_step<T>(p, true, s, coeffs, level(j - 2), level(j - 1), level(j), nullptr, inj, rcv_z, st);
         if (e != cudaSuccess) return cuda_fail(e);
-        ga.u[ga.nsteps] = (const T *)fwd_states[nsteps - j];
-        ga.lam[ga.nsteps] = (const T *)level(j - 1);
-        ++ga.nsteps;
-        if (ga.nsteps == G || j == nsteps) {
+        for (int i = 0; i < n; ++i) {
+            ga.u[ga.nsteps] = (const T *)fwd_states[nsteps - j - i];
+            ga.lam[ga.nsteps] = (const T *)level(j - 1 + i);
+            ++ga.nsteps;
+        }
+        j += n;
+        if (ga.nsteps == G || j > nsteps) {
             // the gradient stream starts this batch once its sweeps (and all
             // earlier work of the caller's stream) are done
             e = cudaEventRecord(p->ev_sweeps, st);
@@ -691,6 +758,11 @@ int stencil_plan_set(stencil_plan_t p, int option, int64_t value) {
         if (value < 0 || value > (1 << 30)) return STENCIL_EINVAL;
         p->wait_limit = (int)value;
         return STENCIL_OK;
+    case STENCIL_OPT_ADJ_TIME_BLOCK:
+        if (value < 0 || value > 2) return STENCIL_EINVAL;
+        if (value == 2 && !adj_pass_supported(p)) return STENCIL_EUNSUPPORTED;
+        p->adj_tb = (int)value;
+        return STENCIL_OK;
     case STENCIL_OPT_TEST_SKIP_COPY:
         if (value < -1 || value >= p->g.nz) return STENCIL_EINVAL;
         p->skip_plane = value < 0 ? SKIP_NONE : (int)value;
@@ -716,6 +788,7 @@ int stencil_plan_get(stencil_plan_t p, int option, int64_t *value) {
     case STENCIL_OPT_GRAPH: *value = p->graph; return STENCIL_OK;
     case STENCIL_OPT_WAIT_LIMIT: *value = p->wait_limit > 0 ? p->wait_limit : WAIT_LIMIT_DEFAULT; return STENCIL_OK;
     case STENCIL_OPT_TEST_SKIP_COPY: *value = p->skip_plane == SKIP_NONE ? -1 : p->skip_plane; return STENCIL_OK;
+    case STENCIL_OPT_ADJ_TIME_BLOCK: *value = effective_adj_block(p); return STENCIL_OK;
     case STENCIL_OPT_SCRATCH_BYTES:
         *value = (int64_t)((p->scratch[0] ? 2 * p->field_bytes : 0) + (p->nbands + p->ngring) * p->field_bytes +
                            p->npartials * sizeof(double));
@@ -824,9 +897,10 @@ int stencil_adjoint(stencil_plan_t p, void *lam_next, void *lam, const stencil_c
         return run_adjoint_ring<float>(p, lam_next, lam, coeffs, T, (cudaStream_t)stream, residual,
                                        residual ? rcv_z : -1, fwd_states, grad);
     }
-    // the adjoint runs plain passes (time block 1)
+    // one-level passes, or depth-2 passes without a gradient (with a
+    // gradient of batch 1 every level is summed before the next sweep)
     const int saved = p->time_block;
-    p->time_block = 1;
+    p->time_block = grad ? 1 : effective_adj_block(p);
     int r;
     if (p->dtype == STENCIL_F64)
         r = run_program<double>(p, lam_next, lam, coeffs, T, (cudaStream_t)stream, true, nullptr, residual,

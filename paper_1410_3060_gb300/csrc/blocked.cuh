@@ -21,6 +21,10 @@ struct BlockedArgs {
     int wA;              // phase-A tile height (diamond scheme)
     unsigned long long *dbg;   // debug builds: first bad store index + 1 (nullptr otherwise)
     int wait_limit;      // polls of a bounded mbarrier wait (TMA-staged passes)
+    // adjoint passes: residual plane [ny][nx] added to level 1 on plane
+    // rcv_z (nullptr: none); level k's plane is inject + (k-1) * inject_step
+    const T *inject;
+    int64_t inject_step;
 };
 
 bool blocked_supported(int kind, int dtype, int levels);

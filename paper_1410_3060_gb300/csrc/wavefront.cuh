@@ -12,6 +12,12 @@ bool wavefront_supported(int kind, int dtype, int levels, const Geom &g);
 // Tile variant of the register wavefront (0 = default of the kind / dtype).
 template <typename T>
 cudaError_t launch_wavefront(int kind, const BlockedArgs<T> &a, int tile, cudaStream_t st, int num_sms);
+// Adjoint pass of depth 2 (a.levels == 2) of the 7-point kinds: lam^{t+1}
+// in a.u, level 1 (lam^t) into a.out_prev, level 2 (lam^{t-1}) into a.out,
+// residual planes a.inject / a.inject + a.inject_step on plane a.rcv_z;
+// tiles 0-3 (wavefront_adj.cu).
+template <typename T>
+cudaError_t launch_wavefront_adj(int kind, const BlockedArgs<T> &a, int tile, cudaStream_t st, int num_sms);
 // Resources of a pass configuration (info[0..5]: dynamic shared memory bytes,
 // threads, computed x / y extent, owned x / y extent); false if not served.
 bool wavefront_info_f32(int kind, int levels, int tile, int64_t *info);

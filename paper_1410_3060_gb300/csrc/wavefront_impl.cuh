@@ -131,17 +131,27 @@ constexpr size_t wf_smem() {
            sizeof(T) * (size_t)wf_coef_slots<T, V, NR, WY, B, R, NA>() * NA * NR * 32 * WY * V;
 }
 
-template <typename T, int KIND, int B, int V, int NR, int WY>
+// ADJ: the adjoint pass (first-order kinds: lam^t = A^T lam^{t+1} + r^t on
+// the receiver plane).  The constant kind is symmetric and keeps the
+// forward update; the variable kind gathers each term's coefficient at its
+// source point, (A^T y)(q) = sum_k A_k(q - o_k) y(q - o_k): W1 at q+x, W2 at
+// q-x, W3 at q+y, W4 at q-y, W5 at q+z, W6 at q-z (x shifts by warp
+// shuffle, the rest by loads from the neighbouring rows and planes, served
+// mostly by L1 / L2).  The residual plane of level k is added to every
+// computed point of plane rcv_z, overlapped halo points included.  Depth 2
+// writes both levels (out_prev = level 1, out = level 2).
+template <typename T, int KIND, int B, int V, int NR, int WY, bool ADJ = false>
 __global__ void __launch_bounds__(32 * WY) wavefront_kernel(const BlockedArgs<T> a) {
     constexpr int R = KindTraits<KIND>::R;
-    constexpr int NA = KindTraits<KIND>::NARR;
+    constexpr int NA = ADJ ? 0 : KindTraits<KIND>::NARR;   // forward coefficient arrays per point
+    constexpr bool ADJV = ADJ && KIND == J7_VAR;           // adjoint with gathered coefficients
     static_assert(R == 1 && (KIND == J7_CONST || KIND == J7_VAR), "radius-1 kinds");
     using TL = WfTile<V, NR, WY, B, R, (int)sizeof(T)>;
     // FP32 pairs of a row updated by packed instructions (sm_100 and later);
     // measured at 512^3: faster for blocked passes (7-point constant depth
     // 3: 951 vs 899 GLUP/s, depth 4: 767 vs 621), slower for one-level ones
     // (521 vs 569)
-    constexpr bool PACK = sizeof(T) == 4 && (V == 2 || V == 4) && B >= 2;
+    constexpr bool PACK = !ADJ && sizeof(T) == 4 && (V == 2 || V == 4) && B >= 2;
     constexpr int RING = TL::RING;
     constexpr int U = RING;               // steps per unrolled block: ring slots are constants
     constexpr int PD = TL::PD, NS = TL::NS;
@@ -228,14 +238,35 @@ __global__ void __launch_bounds__(32 * WY) wavefront_kernel(const BlockedArgs<T>
             rb[j][h] = hin ? (uint32_t)(GE * sizeof(T)) : 0u;
         }
     }
-    // coefficient vector of the thread's row jr from the plane at cb (zeros
-    // for chunks outside the padded array)
-    auto ldcoef = [&](T (&d)[V], const T *cb, int jr) {
+    // adjoint of the variable kind: offsets of the rows just above and below
+    // the thread's rows (index 0: row -1, index 1: row NR)
+    uint32_t roe[2][GC], rbe[2][GC];
+#pragma unroll
+    for (int e = 0; e < 2; ++e) {
+        const int r = e == 0 ? r0 - 1 : r0 + NR;
+        const bool in = cmem && r >= 0 && r < g.py;
+#pragma unroll
+        for (int h = 0; h < GC; ++h) {
+            const bool hin = in && c0 + h * GE < g.px;
+            roe[e][h] = hin ? (uint32_t)(r * sy + c0 + h * GE) : 0u;
+            rbe[e][h] = hin ? 1u : 0u;
+        }
+    }
+    (void)roe; (void)rbe;
+    // vector of row jr (-1 .. NR) of the plane at cb (zeros for chunks
+    // outside the padded array)
+    auto ldrow = [&](T (&d)[V], const T *cb, auto jI) {
+        constexpr int jr = decltype(jI)::value;
 #pragma unroll
         for (int h = 0; h < GC; ++h) {
             T c[GE];
-            if (rb[jr][h]) {
-                vld_g<T, GE>(c, cb + ro[jr][h]);
+            bool on;
+            uint32_t off;
+            if constexpr (jr < 0) { on = rbe[0][h] != 0u; off = roe[0][h]; }
+            else if constexpr (jr >= NR) { on = rbe[1][h] != 0u; off = roe[1][h]; }
+            else { on = rb[jr][h] != 0u; off = ro[jr][h]; }
+            if (on) {
+                vld_g<T, GE>(c, cb + off);
             } else {
 #pragma unroll
                 for (int i = 0; i < GE; ++i) c[i] = T(0);
@@ -244,10 +275,35 @@ __global__ void __launch_bounds__(32 * WY) wavefront_kernel(const BlockedArgs<T>
             for (int i = 0; i < GE; ++i) d[h * GE + i] = c[i];
         }
     };
+    (void)ldrow;
+    // coefficient vector of the thread's row jr (inside the padded array)
+    // from the plane at cb (zeros for chunks outside it; one chunk per
+    // vector: the row's test is the caller's)
+    auto ldcoef = [&](T (&d)[V], const T *cb, int jr) {
+        if constexpr (GC == 1) {
+            vld_g<T, V>(d, cb + ro[jr][0]);
+        } else {
+#pragma unroll
+            for (int h = 0; h < GC; ++h) {
+                T c[GE];
+                if (rb[jr][h]) {
+                    vld_g<T, GE>(c, cb + ro[jr][h]);
+                } else {
+#pragma unroll
+                    for (int i = 0; i < GE; ++i) c[i] = T(0);
+                }
+#pragma unroll
+                for (int i = 0; i < GE; ++i) d[h * GE + i] = c[i];
+            }
+        }
+    };
     (void)ldcoef;
     // receiver plane if it is one of this chunk's own planes (else a plane
     // index no level reaches)
     const int tz = (a.trace && a.rcv_z >= z0 && a.rcv_z < z1) ? a.rcv_z : -(1 << 30);
+    // adjoint: plane of the residual injection (every computed copy of it)
+    const int iz = (ADJ && a.inject) ? a.rcv_z : -(1 << 30);
+    (void)iz;
 
     T r0v[RING][NR][V];
     T rk[NK][RING][NR][V];
@@ -430,6 +486,32 @@ __global__ void __launch_bounds__(32 * WY) wavefront_kernel(const BlockedArgs<T>
                     const T *cfb = nullptr;
                     if constexpr (NA > 0) cfb = a.W + (ptrdiff_t)(zk + R) * szi;
                     (void)cfb;
+                    // adjoint of the variable kind: every term's coefficient
+                    // at its source point
+                    T ac[ADJV ? NR : 1][7][V];
+                    (void)ac;
+                    if constexpr (ADJV) {
+                        const T *cb = a.W + (ptrdiff_t)(zk + R) * szi;
+                        const int64_t nf = g.nfield;
+                        static_for<NR>([&](auto jI) {
+                            constexpr int jq = decltype(jI)::value;
+                            T w1[V], w2[V];
+                            ldrow(ac[jq][0], cb, IC<jq>{});
+                            ldrow(w1, cb + nf, IC<jq>{});
+                            ldrow(w2, cb + 2 * nf, IC<jq>{});
+                            const T w1r = __shfl_down_sync(FULLMASK, w1[0], 1);     // W1 at the next lane's first point
+                            const T w2l = __shfl_up_sync(FULLMASK, w2[V - 1], 1);   // W2 at the previous lane's last point
+#pragma unroll
+                            for (int i = 0; i < V; ++i) {
+                                ac[jq][1][i] = i < V - 1 ? w1[i + 1] : w1r;
+                                ac[jq][2][i] = i > 0 ? w2[i - 1] : w2l;
+                            }
+                            ldrow(ac[jq][3], cb + 3 * nf, IC<jq + 1>{});
+                            ldrow(ac[jq][4], cb + 4 * nf, IC<jq - 1>{});
+                            ldrow(ac[jq][5], cb + 5 * nf + szi, IC<jq>{});
+                            ldrow(ac[jq][6], cb + 6 * nf - szi, IC<jq>{});
+                        });
+                    }
 #pragma unroll
                     for (int jr = 0; jr < NR; ++jr) {
                         T cf[NA > 0 ? NA : 1][V];
@@ -507,6 +589,16 @@ __global__ void __launch_bounds__(32 * WY) wavefront_kernel(const BlockedArgs<T>
                                 T v;
                                 if constexpr (KIND == J7_CONST) {
                                     v = wc[jr][i] * c + wf[jr][i] * (((xl + xr) + (yu + yd)) + (zd + zu));
+                                } else if constexpr (ADJV) {
+                                    // the plain adjoint sweep's terms and order
+                                    v = ac[jr][0][i] * c;
+                                    v = fma(ac[jr][1][i], xr, v);
+                                    v = fma(ac[jr][2][i], xl, v);
+                                    v = fma(ac[jr][3][i], yd, v);
+                                    v = fma(ac[jr][4][i], yu, v);
+                                    v = fma(ac[jr][5][i], zu, v);
+                                    v = fma(ac[jr][6][i], zd, v);
+                                    v = ((pmask >> (jr * V + i)) & 1u) ? v : T(0);
                                 } else {
                                     v = cf[0][i] * c;
                                     v = fma(cf[1][i], xl, v);
@@ -520,6 +612,19 @@ __global__ void __launch_bounds__(32 * WY) wavefront_kernel(const BlockedArgs<T>
                                 D[jr][i] = v;
                             }
                         }
+                    }
+                }
+                if constexpr (ADJ) {
+                    // residual of level k on the receiver plane, at every
+                    // interior point this thread computes
+                    if (zk == iz) {
+                        const T *inj = a.inject + (k - 1) * a.inject_step;
+#pragma unroll
+                        for (int jr = 0; jr < NR; ++jr)
+#pragma unroll
+                            for (int i = 0; i < V; ++i)
+                                if ((pmask >> (jr * V + i)) & 1u)
+                                    D[jr][i] += inj[(int64_t)(r0 + jr - R) * g.nx + (c0 + i - R)];
                     }
                 }
                 if (zk == tz) store_trace(a.trace + (k - 1) * plane_elems, D);
@@ -545,7 +650,7 @@ __global__ void __launch_bounds__(32 * WY) wavefront_kernel(const BlockedArgs<T>
 // ---------------------------------------------------------------- launch
 namespace {
 
-template <typename T, int KIND, int B, int V, int NR, int WY>
+template <typename T, int KIND, int B, int V, int NR, int WY, bool ADJ = false>
 cudaError_t launch_wf(const BlockedArgs<T> &a, cudaStream_t st, int num_sms) {
     constexpr int R = KindTraits<KIND>::R;
     constexpr int TXE = 32 * V, TYE = WY * NR;
@@ -553,8 +658,8 @@ cudaError_t launch_wf(const BlockedArgs<T> &a, cudaStream_t st, int num_sms) {
     constexpr int AX = WfGeom<V, B, R>::AX;
     constexpr int SX = (TXE - BR - AX) / V * V;
     constexpr int SY = TYE - 2 * BR;
-    auto kern = wavefront_kernel<T, KIND, B, V, NR, WY>;
-    constexpr size_t smem = wf_smem<T, V, NR, WY, B, R, KindTraits<KIND>::NARR>();
+    auto kern = wavefront_kernel<T, KIND, B, V, NR, WY, ADJ>;
+    constexpr size_t smem = wf_smem<T, V, NR, WY, B, R, ADJ ? 0 : KindTraits<KIND>::NARR>();
     static_assert(smem <= 227 * 1024, "shared memory per CTA");
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
@@ -640,29 +745,26 @@ bool wavefront_info_impl(int kind, int levels, int tile, int64_t *info) {
     }
 }
 
-template <typename T, int KIND, int B>
+template <typename T, int KIND, int B, bool ADJ = false>
 cudaError_t launch_tile(const BlockedArgs<T> &a, int tile, cudaStream_t st, int num_sms) {
     constexpr int V = kVec((int)sizeof(T));
     switch (tile) {
-    case 2: return launch_wf<T, KIND, B, V, 2, 16>(a, st, num_sms);   // 64 x 32, 2 rows per thread
+    case 2: return launch_wf<T, KIND, B, V, 2, 16, ADJ>(a, st, num_sms);   // 64 x 32, 2 rows per thread
     case 3:
-        if constexpr (B <= 3) return launch_wf<T, KIND, B, V, 4, 16>(a, st, num_sms);   // 64 x 64
-        else return launch_wf<T, KIND, B, V, 2, 16>(a, st, num_sms);
+        if constexpr (B <= 3) return launch_wf<T, KIND, B, V, 4, 16, ADJ>(a, st, num_sms);   // 64 x 64
+        else return launch_wf<T, KIND, B, V, 2, 16, ADJ>(a, st, num_sms);
     // FP32, 4 points per thread row (measured at 512^3, T = 64: 7-point
     // constant depth 3 918 vs 932 GLUP/s for tile 3, depth 2 774 vs 897 for
     // tile 1; one-level 7-point variable 171 vs 150 for tile 2; 128 x 32
     // with 4 rows per thread and 128 x 16 tiles were slower still)
-    case 4:   // 128 x 32 (depth 4: 128 x 16, for shared memory)
-        if constexpr (sizeof(T) != 4) break;
+    case 4:   // 128 x 32 (depth 4: 128 x 16, for shared memory); forward only
+        if constexpr (sizeof(T) != 4 || ADJ) break;
         else if constexpr (B <= 3) return launch_wf<T, KIND, B, 4, 2, 16>(a, st, num_sms);
         else return launch_wf<T, KIND, B, 4, 2, 8>(a, st, num_sms);
-    default: return launch_wf<T, KIND, B, V, 4, 8>(a, st, num_sms);   // 64 x 32, 4 rows per thread
+    default: return launch_wf<T, KIND, B, V, 4, 8, ADJ>(a, st, num_sms);   // 64 x 32, 4 rows per thread
     }
     return cudaErrorNotSupported;
 }
-
-template <typename T>
-cudaError_t launch_wavefront_impl(int kind, const BlockedArgs<T> &a, int tile, cudaStream_t st, int num_sms);
 
 template <typename T, int KIND>
 cudaError_t launch_depth(const BlockedArgs<T> &a, int tile, cudaStream_t st, int num_sms) {
@@ -681,6 +783,18 @@ cudaError_t launch_wavefront_impl(int kind, const BlockedArgs<T> &a, int tile, c
     switch (kind) {
     case J7_CONST: return launch_depth<T, J7_CONST>(a, tile, st, num_sms);
     case J7_VAR: return launch_depth<T, J7_VAR>(a, tile, st, num_sms);
+    default: return cudaErrorNotSupported;
+    }
+}
+
+// Adjoint passes (instantiated in their own translation unit): depth 2,
+// both levels written, tiles 0-3.
+template <typename T>
+cudaError_t launch_wavefront_adj_impl(int kind, const BlockedArgs<T> &a, int tile, cudaStream_t st, int num_sms) {
+    if (a.levels != 2 || tile > 3) return cudaErrorNotSupported;
+    switch (kind) {
+    case J7_CONST: return launch_tile<T, J7_CONST, 2, true>(a, tile, st, num_sms);
+    case J7_VAR: return launch_tile<T, J7_VAR, 2, true>(a, tile, st, num_sms);
     default: return cudaErrorNotSupported;
     }
 }

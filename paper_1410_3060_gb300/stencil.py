@@ -18,6 +18,7 @@ J7_CONST, J7_VAR, W25_CONST, W25_VAR, J25_VAR, W25_ALPHA = 1, 2, 3, 4, 5, 6
 F64, F32 = 0, 1
 OPT_TIME_BLOCK, OPT_SCHEME, OPT_SCRATCH_BYTES, OPT_GRAD_BATCH, OPT_VARIANT, OPT_GRAPH = 1, 2, 3, 4, 5, 6
 OPT_WAIT_LIMIT, OPT_TEST_SKIP_COPY = 7, 8
+OPT_ADJ_TIME_BLOCK = 9
 OK, EINVAL, EUNSUPPORTED, ENOMEM, ECUDA, ETIMEOUT = 0, -1, -2, -3, -4, -5
 RADIUS = {J7_CONST: 1, J7_VAR: 1, W25_CONST: 4, W25_VAR: 4, J25_VAR: 4, W25_ALPHA: 4}
 NUM_ARRAYS = {J7_CONST: 0, J7_VAR: 7, W25_CONST: 0, W25_VAR: 13, J25_VAR: 13, W25_ALPHA: 1}
