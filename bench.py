@@ -59,6 +59,9 @@ def parse():
     p.add_argument("--sweep-dtypes", default="f64,f32", help="comma-separated dtypes of the tuning sweep")
     p.add_argument("--fwd-adj", action="store_true",
                    help="time only the forward+adjoint of the differentiable wave workload (size --n, T --T)")
+    p.add_argument("--adjoint", action="store_true",
+                   help="time only the adjoint sweep of a 7-point --kind (size --n, T --T, levels per pass "
+                        "--time-block, default: library choice)")
     p.add_argument("--no-variants", action="store_true")
     p.add_argument("--no-cpu", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
@@ -365,12 +368,19 @@ MEASURED_TRAFFIC = {
     ("w25_var", "f32", 1, 16): (67.88, "profiles/plainv_tma_w25_var_384_fp32.md"),
     ("w25_const", "f32", 1, 15): (12.22, "profiles/plainv_tma_w25_const_512_fp32.md"),
 }
+# adjoint passes (bench.py --adjoint, no gradient): (kind, dtype, levels)
+MEASURED_TRAFFIC_ADJ = {
+    ("j7_var", "f32", 2): (18.48, "profiles/wavefront_adj_j7_var_384_fp32_b2.md"),
+    ("j7_const", "f32", 2): (3.78, "profiles/wavefront_adj_j7_const_384_fp32_b2.md"),
+}
 
 
 def add_traffic(rec, kind_name, dtype_name, res, n):
+    """DRAM traffic per launch of a profiled configuration: the profiled
+    bytes per update x the n^3 x levels updates one pass makes."""
     tr = MEASURED_TRAFFIC.get((kind_name, dtype_name, res["time_block"], res["variant"]))
     if tr is not None:
-        rec["traffic"] = tr[0] * float(n) ** 3
+        rec["traffic"] = tr[0] * float(n) ** 3 * res["time_block"]
         rec["traffic_source"] = tr[1] + " (DRAM bytes per update x updates per launch)"
 # thread instructions per update of the on-chip-bound FP32 kernels (ncu
 # warp instructions x 32 / updates of the profiled launch): the issue view of
@@ -514,11 +524,11 @@ def fwd_adj_case(torch, st, wl, n, T, K, dtype, steps, warmup, ws, stream, fw=No
 
 def adjoint_bytes_per_lup(kind, elem, levels):
     """Algorithmic HBM bytes per update of the adjoint sweep of a 7-point
-    kind (no gradient): a pass of `levels` levels reads lam^{t+1} and the
-    coefficient arrays once and writes every level (the gradient needs each
-    one)."""
+    kind without a gradient: a pass of `levels` levels reads lam^{t+1} and
+    the coefficient arrays once and writes its last level (with a gradient
+    every level is written, one more field per extra level)."""
     arrays = 7 if kind == 2 else 0
-    return elem * (1 + arrays + levels) / levels
+    return elem * (2 + arrays) / levels
 
 
 def adjoint_case(torch, st, wl, kind, n, T, dtype, steps, warmup, ws, stream, adj_block=None, hbm_peak=None):
@@ -567,7 +577,11 @@ def adjoint_case(torch, st, wl, kind, n, T, dtype, steps, warmup, ws, stream, ad
         ach = res_["glups"] / ws * bpl
         res_["roofline"] = {"bound": "hbm", "bytes_per_lup": bpl, "achieved": ach, "peak": hbm_peak, "unit": "GB/s",
                             "frac": ach / hbm_peak,
-                            "note": "algorithmic bytes: lam^{t+1} and the coefficients once per pass, every level written"}
+                            "note": "algorithmic bytes: lam^{t+1} and the coefficients read, the last level written, once per pass"}
+        tr = MEASURED_TRAFFIC_ADJ.get((wl.KIND_NAMES[kind], res_["dtype"], b))
+        if tr is not None:
+            res_["roofline"]["traffic"] = tr[0] * float(n) ** 3 * b
+            res_["roofline"]["traffic_source"] = tr[1] + " (DRAM bytes per update x updates per launch)"
     plan.close()
     del W, lam0, l1, l2, res
     torch.cuda.empty_cache()
@@ -648,6 +662,13 @@ def run_ours(args):
         r, _ = fwd_adj_case(torch, st, wl, n, T, 20, dtype, args.steps, args.warmup, ws, stream,
                             variant=args.variant, hbm_peak=hbm_peak)
         print(json.dumps({"fwd_adj": r}), flush=True)
+        return
+    if args.adjoint:
+        if kind not in (wl.J7_CONST, wl.J7_VAR):
+            raise SystemExit("--adjoint: a 7-point kind (j7_const, j7_var)")
+        r = adjoint_case(torch, st, wl, kind, n, T, dtype, args.steps, args.warmup, ws, stream,
+                         adj_block=args.time_block, hbm_peak=hbm_peak)
+        print(json.dumps({"adjoint": r}), flush=True)
         return
     dev_index = torch.cuda.current_device()
     sampler = ClockSampler(dev_index)

@@ -158,10 +158,11 @@ enum stencil_option {
        not serve the geometry).  With a gradient, levels are paired only
        inside a gradient batch (STENCIL_OPT_GRAD_BATCH >= 2); with batch 1
        every pass is one level.  0 = default: 2 in FP32 where served
-       (measured at 512^3: 7-point variable 168 vs 129 GLUP/s, constant 789
+       (measured at 512^3: 7-point variable 259 vs 129 GLUP/s, constant 789
        vs 584), 1 in FP64 (bound by the FP64 pipe either way).  Passes run
-       the plan's register wavefront tile (variants 10-12), else the 64x64
-       tile.  Reading it gives the depth the adjoint runs. */
+       the plan's register wavefront tile (variants 10-12), else the 64x32
+       tile of 2 rows per thread (variable kind) or the 64x64 tile
+       (constant kind).  Reading it gives the depth the adjoint runs. */
     STENCIL_OPT_ADJ_TIME_BLOCK = 9
 };
 

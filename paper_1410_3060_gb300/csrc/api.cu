@@ -281,7 +281,7 @@ bool adj_pass_supported(const stencil_plan_s *p) {
     return (p->kind == J7_CONST || p->kind == J7_VAR) && wavefront_supported(p->kind, p->dtype, 2, p->g);
 }
 
-// Default adjoint depth: 2 in FP32 (measured at 512^3, T = 64: J7_VAR 168 vs
+// Default adjoint depth: 2 in FP32 (measured at 512^3, T = 64: J7_VAR 259 vs
 // 129 GLUP/s, J7_CONST 789 vs 584), 1 in FP64 (FP64-pipe bound: 54.0 vs
 // 55.3 for J7_VAR).
 int effective_adj_block(const stencil_plan_s *p) {
@@ -290,12 +290,14 @@ int effective_adj_block(const stencil_plan_s *p) {
 }
 
 // Tile of the adjoint passes: the plan's register wavefront tile variant
-// 10-12 when one is set, else the 64 x 64 tile (measured at 512^3 FP32:
-// J7_VAR 168 GLUP/s vs 159 for 64 x 32 with 2 rows per thread and 106 with
-// 4; J7_CONST 789 vs 697 and 786).
+// 10-12 when one is set, else the measured best at 512^3 FP32: J7_VAR the
+// 64 x 32 tile of 2 rows per thread (259 GLUP/s, its gathered coefficients
+// reused through a shared slot; 197 with 4 rows per thread, 140 for
+// 64 x 64), J7_CONST 64 x 64 (789 vs 697 and 786).
 int adj_tile(const stencil_plan_s *p) {
     const int t = wf_tile(p->variant);
-    return (t >= 1 && t <= 3) ? t : 3;
+    if (t >= 1 && t <= 3) return t;
+    return p->kind == J7_VAR ? 2 : 3;
 }
 
 int effective_time_block(const stencil_plan_s *p) {

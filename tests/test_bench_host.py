@@ -96,3 +96,17 @@ def test_reference_arm_prints_one_contract_line():
         assert k in d, k
     assert d["impl"] == "reference" and d["value"] > 0
     assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["cores"] >= 1
+
+
+def test_traffic_is_per_launch(bench):
+    """A profiled configuration's DRAM traffic is per launch: bytes per update
+    x the n^3 x levels updates of one pass (3 levels of the 7-point constant
+    FP32 wavefront: 2.53 B x 3 n^3, close to its 8 algorithmic bytes per
+    point and pass)."""
+    n = 512
+    rec = {}
+    bench.add_traffic(rec, "j7_const", "f32", {"time_block": 3, "variant": 12}, n)
+    assert abs(rec["traffic"] - 2.53 * 3 * n ** 3) < 1.0
+    assert abs(rec["traffic"] / n ** 3 - 8.0) < 0.5
+    assert bench.adjoint_bytes_per_lup(2, 4, 2) == 18.0 and bench.adjoint_bytes_per_lup(2, 4, 1) == 36.0
+    assert bench.adjoint_bytes_per_lup(1, 4, 2) == 4.0
