@@ -58,7 +58,8 @@ def parse():
                    help="comma-separated kinds of the tuning sweep")
     p.add_argument("--sweep-dtypes", default="f64,f32", help="comma-separated dtypes of the tuning sweep")
     p.add_argument("--fwd-adj", action="store_true",
-                   help="time only the forward+adjoint of the differentiable wave workload (size --n, T --T)")
+                   help="time only the forward+adjoint of the differentiable workload: the 25-point variable wave "
+                        "(K = 20), or --kind j7_var (K = 16) (size --n, T --T)")
     p.add_argument("--adjoint", action="store_true",
                    help="time only the adjoint sweep of a 7-point --kind (size --n, T --T, levels per pass "
                         "--time-block, default: library choice)")
@@ -461,6 +462,82 @@ def fwd_adj_bytes_per_lup(elem, T, K, grad_batch):
     return sweep * (2 + recomputed) + 2 * elem + 13 * 16 / grad_batch
 
 
+def fwd_adj_j7_bytes_per_lup(elem, T, K, grad_batch, levels):
+    """Algorithmic HBM bytes per lattice update of one forward + backward of
+    the 7-point variable kind with passes of `levels` levels (forward,
+    recompute and adjoint): the forward reads the state and the 7 arrays and
+    writes the last level once per pass; the recompute of every segment but
+    the last and the adjoint write every level; the gradient reads the
+    adjoint level and the state of every step and reads and writes the 7
+    FP64 gradient arrays once per batch."""
+    b = levels
+    fwd = elem * (1 + 7 + 1) / b
+    every = elem * (1 + 7 + b) / b
+    nseg = (T + K - 1) // K
+    recomputed = (T - (T - (nseg - 1) * K)) / T
+    return fwd + every * recomputed + every + 2 * elem + 7 * 16 / grad_batch
+
+
+def fwd_adj_j7_case(torch, st, wl, n, T, K, dtype, steps, warmup, ws, stream, hbm_peak=None):
+    """Differentiable 7-point variable workload through MisfitRunner: one step
+    = the checkpointed forward (T steps, state kept every K steps, receiver
+    trace on plane n/8, FP64 misfit) plus the backward (recompute and
+    adjoint with the FP64 coefficient gradient in 16-step batches).  Inputs:
+    the standard 7-point variable recipe (U[-1,1] field, U[0,0.14] weights);
+    the observed data come from a forward run of the same library with the
+    weights scaled by 1 + 0.05 U[-1,1] (on the device)."""
+    from paper_1410_3060_gb300.autograd import MisfitRunner
+    tdt = torch.float64 if dtype == st.F64 else torch.float32
+    wk = wl.j7_var(n, 1, seed=0)
+    rz = max(1, n // 8)
+    run = MisfitRunner(wl.J7_VAR, (n, n, n), T, K, rz, dtype=dtype)
+    u0 = torch.from_numpy(wk.u).to("cuda", tdt)
+    W = torch.from_numpy(wk.W).to("cuda", tdt)
+    del wk
+    g = torch.Generator(device="cuda")
+    g.manual_seed(3)
+    Wt = W * (1.0 + 0.05 * (2.0 * torch.rand(W.shape, device="cuda", generator=g, dtype=tdt) - 1.0))
+    d = torch.zeros((T, n, n), device="cuda", dtype=tdt)
+    up, uc = u0.clone(), u0.clone()
+    run.plan.forward(up, uc, None, Wt, T, trace=d, rcv_z=rz)
+    del up, uc, Wt
+
+    for _ in range(warmup):
+        loss, state = run.forward_pass(u0, W, d)
+        run.backward_pass(state, W, torch.ones((), dtype=torch.float64))
+        del state
+    barrier(torch, ws)
+    t_f = t_b = 0.0
+    for _ in range(steps):
+        with Timer(torch, stream) as tf:
+            loss, state = run.forward_pass(u0, W, d)
+        with Timer(torch, stream) as tb:
+            run.backward_pass(state, W, torch.ones((), dtype=torch.float64))
+        t_f += tf.ms
+        t_b += tb.ms
+        del state
+    barrier(torch, ws)
+    ms = max_over_ranks(torch, ws, (t_f + t_b) / steps)
+    lups = float(n) ** 3 * T
+    b = run.plan.get(st.OPT_TIME_BLOCK)
+    ab = run.plan.get(st.OPT_ADJ_TIME_BLOCK)
+    res = {"kind": "j7_var_fwd_adj", "n": n, "T": T, "K": K, "dtype": "f64" if dtype == st.F64 else "f32",
+           "ms_per_step": ms, "glups": lups * ws / (ms * 1e-3) / 1e9,
+           "forward_ms": t_f / steps, "backward_ms": t_b / steps,
+           "forward_glups": lups / (t_f / steps * 1e-3) / 1e9, "loss": float(loss.item()),
+           "time_block": b, "adjoint_levels_per_pass": ab, "grad_batch": run.plan.get(st.OPT_GRAD_BATCH)}
+    if hbm_peak and b == ab:
+        bpl = fwd_adj_j7_bytes_per_lup(4 if dtype == st.F32 else 8, T, K, res["grad_batch"], b)
+        ach = res["glups"] / ws * bpl
+        res["roofline"] = {"bound": "hbm", "bytes_per_lup": bpl, "achieved": ach, "peak": hbm_peak, "unit": "GB/s",
+                           "frac": ach / hbm_peak,
+                           "note": "algorithmic bytes of forward + recompute + adjoint + gradient"}
+    run.close()
+    del u0, W, d
+    torch.cuda.empty_cache()
+    return res
+
+
 def fwd_adj_case(torch, st, wl, n, T, K, dtype, steps, warmup, ws, stream, fw=None, variant=None, hbm_peak=None):
     """Differentiable 25-point variable wave workload: one step = the
     checkpointed forward (T steps, state pair kept every K steps, receiver
@@ -658,6 +735,10 @@ def run_ours(args):
     if args.sweep:
         run_sweep(args, torch, st, wl, pm, stream, ws, fp_peaks, hbm_peak)
         return
+    if args.fwd_adj and kind == wl.J7_VAR:
+        r = fwd_adj_j7_case(torch, st, wl, n, T, 16, dtype, args.steps, args.warmup, ws, stream, hbm_peak=hbm_peak)
+        print(json.dumps({"fwd_adj": r}), flush=True)
+        return
     if args.fwd_adj:
         r, _ = fwd_adj_case(torch, st, wl, n, T, 20, dtype, args.steps, args.warmup, ws, stream,
                             variant=args.variant, hbm_peak=hbm_peak)
@@ -719,6 +800,9 @@ def run_ours(args):
             for ab in (None, 1):
                 variants.append(adjoint_case(torch, st, wl, vk, n, T, st.F32, max(1, args.steps // 2), 1, ws,
                                              stream, adj_block=ab, hbm_peak=hbm_peak))
+        # forward + adjoint of the differentiable 7-point variable workload
+        # (512^3, T = 64, K = 16, FP32: blocked forward, recompute and adjoint)
+        variants.append(fwd_adj_j7_case(torch, st, wl, n, T, 16, st.F32, 1, 1, ws, stream, hbm_peak=hbm_peak))
         # forward + adjoint of the differentiable wave workload (256^3, T = 200, K = 20)
         fw = None
         for vd in (st.F32, st.F64):

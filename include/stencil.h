@@ -211,12 +211,15 @@ void stencil_plan_destroy(stencil_plan_t plan);
 int stencil_forward(stencil_plan_t plan, void *u_prev, void *u, const stencil_coeffs_t *coeffs,
                     int64_t T, void *stream, void *trace, int64_t rcv_z);
 
-/* Forward T steps of plain sweeps storing every state (the recompute pass
- * of checkpointed differentiation): states is a host array of T device
- * pointers, states[t] receives u^{t+1}.  u_prev, u hold (u^{-1}, u^0) and
- * are only read.  trace / rcv_z as in stencil_forward.  The state arrays
- * must be distinct from each other and from the inputs, and their halos
- * must be zero (only interiors are written). */
+/* Forward T steps storing every state (the recompute pass of checkpointed
+ * differentiation): states is a host array of T device pointers, states[t]
+ * receives u^{t+1}.  u_prev, u hold (u^{-1}, u^0) and are only read.
+ * trace / rcv_z as in stencil_forward.  The state arrays must be distinct
+ * from each other and from the inputs, and their halos must be zero (only
+ * interiors are written).  Plain one-level sweeps, except for the 7-point
+ * kinds on a plan whose passes run the register wavefront at depth >= 2
+ * (the FP32 default): there one depth-2 pass writes two consecutive
+ * states. */
 int stencil_forward_states(stencil_plan_t plan, const void *u_prev, const void *u,
                            const stencil_coeffs_t *coeffs, int64_t T, void *const *states,
                            void *stream, void *trace, int64_t rcv_z);

@@ -504,11 +504,37 @@ int run_forward_states(stencil_plan_s *p, const void *u_prev, const void *u, con
                        int64_t nsteps, void *const *states, cudaStream_t st, void *trace, int64_t rcv_z) {
     const Scalars s = fold_scalars(p->kind, coeffs);
     const int64_t plane = (int64_t)p->g.nx * p->g.ny;
-    for (int64_t t = 0; t < nsteps; ++t) {
+    // 7-point kinds whose plan runs register wavefront passes of depth >= 2:
+    // a depth-2 pass writes both of its levels (and the trace of each), so
+    // one pass gives two consecutive states
+    const bool pairs = plan_scheme(p) == 3 && effective_time_block(p) >= 2 && !kind_wave(p->kind) &&
+                       wavefront_supported(p->kind, p->dtype, 2, p->g);
+    for (int64_t t = 0; t < nsteps;) {
         const void *ip = t >= 2 ? states[t - 2] : (t == 1 ? u : u_prev);
         const void *ic = t >= 1 ? states[t - 1] : u;
-        cudaError_t e = plain_step<T>(p, false, s, coeffs, ip, ic, states[t],
-                                      trace ? (T *)trace + t * plane : nullptr, nullptr, rcv_z, st);
+        cudaError_t e;
+        if (pairs && t + 1 < nsteps) {
+            BlockedArgs<T> a;
+            memset(&a, 0, sizeof(a));
+            a.u_prev = (const T *)ip;
+            a.u = (const T *)ic;
+            a.out_prev = (T *)states[t];
+            a.out = (T *)states[t + 1];
+            a.W = coeffs ? (const T *)coeffs->arrays : nullptr;
+            a.s = s;
+            a.g = p->g;
+            a.rcv_z = (int)rcv_z;
+            a.trace = trace ? (T *)trace + t * plane : nullptr;
+            a.levels = 2;
+            a.dbg = p->dbg;
+            a.wait_limit = p->wait_limit;
+            e = launch_wavefront<T>(p->kind, a, wf_tile(plan_variant(p)), st, p->num_sms);
+            t += 2;
+        } else {
+            e = plain_step<T>(p, false, s, coeffs, ip, ic, states[t], trace ? (T *)trace + t * plane : nullptr,
+                              nullptr, rcv_z, st);
+            t += 1;
+        }
         if (e != cudaSuccess) return cuda_fail(e);
     }
     return STENCIL_OK;

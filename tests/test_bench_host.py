@@ -110,3 +110,12 @@ def test_traffic_is_per_launch(bench):
     assert abs(rec["traffic"] / n ** 3 - 8.0) < 0.5
     assert bench.adjoint_bytes_per_lup(2, 4, 2) == 18.0 and bench.adjoint_bytes_per_lup(2, 4, 1) == 36.0
     assert bench.adjoint_bytes_per_lup(1, 4, 2) == 4.0
+
+
+def test_fwd_adj_j7_bytes(bench):
+    """7-point variable forward + backward, FP32, passes of 2 levels, T = 64,
+    K = 16, gradient batch 16: forward 18 B, recompute of 3 of 4 segments
+    20 B x 0.75, adjoint 20 B, gradient reads 8 B and 7 FP64 arrays read and
+    written once per 16 steps (7 B)."""
+    assert abs(bench.fwd_adj_j7_bytes_per_lup(4, 64, 16, 16, 2) - (18 + 15 + 20 + 8 + 7)) < 1e-12
+    assert abs(bench.fwd_adj_j7_bytes_per_lup(4, 64, 16, 16, 1) - (36 + 27 + 36 + 8 + 7)) < 1e-12

@@ -206,3 +206,36 @@ def test_two_level_25pt_pass_fp32(st, kind, shape, T):
     halo = np.ones(gu.shape, bool)
     halo[R:-R, R:-R, R:-R] = False
     assert not gu[halo].any() and not gp[halo].any()
+
+
+@pytest.mark.parametrize("kind", R1)
+@pytest.mark.parametrize("dtype", [0, 1])
+@pytest.mark.parametrize("T", [5, 6])
+def test_forward_states_in_depth2_passes(st, kind, dtype, T):
+    """stencil_forward_states on a plan of register wavefront passes: one
+    depth-2 pass writes two consecutive states and the trace of both; every
+    state and trace row against the oracle's steps (FP64 plans set scheme 3
+    and depth 2 explicitly; FP32 plans run them by default)."""
+    import torch
+    from gpu_util import F64, to_dev, to_np
+    shape = (130, 45, 40)
+    wk = wl.make(kind, shape, T, seed=23)
+    rz = 17
+    plan = st.Plan(kind, *shape, dtype)
+    if dtype == F64:
+        plan.set(st.OPT_SCHEME, 3)
+        plan.set(st.OPT_TIME_BLOCK, 2)
+    assert plan.get(st.OPT_TIME_BLOCK) >= 2
+    tdt = plan.torch_dtype()
+    states = [torch.zeros(plan.padded_shape, device="cuda", dtype=tdt) for _ in range(T)]
+    trace = torch.zeros((T, shape[1], shape[0]), device="cuda", dtype=tdt)
+    W = to_dev(wk.W, dtype) if wk.W is not None else None
+    plan.forward_states(to_dev(wk.u_prev, dtype), to_dev(wk.u, dtype), wk.w, W, states, trace=trace, rcv_z=rz)
+    torch.cuda.synchronize()
+    p, c = wk.u_prev, wk.u
+    tol = 1e-12 if dtype == F64 else 1e-5
+    for t in range(T):
+        p, c, tr = oracle.forward(kind, p, c, wk.w, wk.W, 1, rcv_z=rz, threads=8)
+        assert normwise_err(to_np(states[t]), c) <= tol, t
+        assert normwise_err(to_np(trace[t]), tr[0]) <= tol, t
+    plan.close()
