@@ -4,37 +4,41 @@
 // bounded-wait counter of that translation unit).
 //
 // The z wavefront of Sect. 4.1 with two levels: when level-0 plane q has
-// arrived, level 1 updates plane q - R and level 2 plane q - 2R (frontline
-// slope -1/R).  A CTA owns a 64 x 16 tile of every plane; level 1 is computed
-// on the tile with a halo of R points on each side (72 x 24: the y and x
-// extent level 2 reads), from level 0 on the tile with a halo of 2R (80 x 32).
-// All three live in shared memory as plane rings:
-//   level 0   11 slots (the 2R+1 planes level 1 reads, two planes in flight),
-//             each brought by one bulk tensor copy (zero fill outside the
-//             padded array), with u^{t-1} of level 1's plane beside it
-//             (3 slots) for the second-order kind;
-//   level 1   9 slots (the 2R+1 planes level 2 reads), written by the CTA.
-// Every neighbour, in x, y and z, is an aligned 16-byte shared load (4 points
-// per thread-vector).  The 13 coefficient vectors of a point are read from
-// global memory at the point: level 1 reads them for its halo'd tile, level 2
-// R steps later for the owned tile -- the second read is meant to hit L2
-// (all tiles of a plane march z together: the grid covers the lattice's x-y
-// extent with resident CTAs).  HBM then carries u^t, u^{t-1} and the 13
-// arrays once and the two written levels once per two time steps.
+// arrived, level 1 updates plane q - R and level 2 plane q - 2R - 1 (one
+// plane behind level 1's output, so the two levels of a step need no
+// barrier between them).  A CTA owns a 64 x 16 tile of every plane; level 1
+// is computed on the tile with a halo of R points on each side (72 x 24: the
+// y and x extent level 2 reads), from level 0 on the tile with a halo of 2R
+// (80 x 32).  The warps split by level: 14 warps update one level-1 vector
+// (4 points) each, 8 warps one owned level-2 vector each, and all meet at
+// one barrier per step.  The levels live in shared memory as plane rings:
+//   level 0   2R + 3 slots (the 2R + 1 planes level 1 reads, the plane
+//             level 2 takes as u^{t-1}, one plane in flight), each brought
+//             by one bulk tensor copy (zero fill outside the padded array),
+//             with u^{t-1} of level 1's plane beside it (2 slots) for the
+//             second-order kind;
+//   level 1   2R + 2 slots (the 2R + 1 planes level 2 reads and the one
+//             level 1 writes), written by the CTA.
+// Every neighbour, in x, y and z, is an aligned 16-byte shared load; the two
+// points of each half-vector are updated by packed FP32 pairs.  The 13
+// coefficient vectors of a point are read from global memory at the point
+// (the first 4 before the step's barrier, the rest at the start of the
+// update): level 1 reads them for its halo'd tile, level 2 R + 1 steps later
+// for the owned tile -- the second read is meant to hit L2 (all tiles of a
+// plane march z together).  HBM then carries u^t, u^{t-1} and the 13 arrays
+// once and the two written levels once per two time steps.
 // Points outside the interior hold the zero Dirichlet value at level 1 (their
 // value is selected to zero; their coefficients are not read).
 // Level 2 and, for the next pass's u^{t-1}, level 1 are written for the owned
 // points; the receiver trace of both levels as well.
 //
-// Measured (512^3, FP32, T = 64): 71 GLUP/s for W25_VAR and 75 for J25_VAR,
-// against 105 and 114 for the one-level TMA sweep, so it is not the default.
-// ncu (384^3, one pass): DRAM 36.5 bytes per update (34 algorithmic, 64 for
-// the one-level sweep) with an L2 hit rate of 50% -- the coefficient re-read
-// is served by L2 -- but the 196 KB of plane rings leave one 256-thread CTA
-// per SM: 8 warps, 28% issue activity, long-scoreboard and barrier stalls.
-// A warp-specialised form (14 level-1 and 8 level-2 warps working on the
-// same step, one barrier per step) was measured slower (42 GLUP/s): 704
-// threads leave 80 registers per thread and the coefficient vectors spill.
+// Measured (512^3, FP32, T = 64): 81 GLUP/s for W25_VAR and 86 for J25_VAR,
+// against 103 and 112 for the one-level TMA sweep, so it is not the default.
+// Earlier forms: one 256-thread CTA doing both levels in turn with all 13
+// coefficient vectors prefetched (72 / 76 GLUP/s; 245 registers and 196 KB
+// of rings leave 8 warps per SM, 28% issue activity); the same split by
+// level with two planes in flight (60 GLUP/s for W25_VAR: its 213 KB of rings
+// leave too little L1 for the coefficient loads in flight).
 #pragma once
 #include "blocked.cuh"
 
@@ -47,13 +51,29 @@ constexpr int TX1 = TXO + 2 * R, TY1 = TYO + 2 * R;   // level-1 tile (72 x 24)
 constexpr int TX0 = TXO + 4 * R, TY0 = TYO + 4 * R;   // level-0 tile (80 x 32)
 constexpr int NV1 = TX1 / V, NP1 = NV1 * TY1;  // level-1 vectors per row / per plane (18, 432)
 constexpr int NVO = TXO / V, NPO = NVO * TYO;  // owned vectors per row / per plane (16, 256)
-constexpr int NT = 256;                        // threads
-constexpr int PD = 2;                          // level-0 planes in flight
-constexpr int NS0 = 2 * R + 1 + PD;            // level-0 slots
+constexpr int NW1 = (NP1 + 31) / 32;           // level-1 warps (14)
+constexpr int NW2 = NPO / 32;                  // level-2 warps (8)
+constexpr int NT = 32 * (NW1 + NW2);           // threads (704)
+// level-0 planes in flight: one (a step takes several microseconds, far
+// longer than a plane's copy), which keeps the wave kind's rings under
+// the 196 KB shared-memory carve-out and leaves L1 room for the
+// coefficient loads in flight
+constexpr int PD = 1;
+// level 2 updates plane q - 2R - 1 in step q, one plane behind the level-1
+// plane q - R written in the same step, so the two levels need no barrier
+// between them: level 0 keeps planes q - 2R - 1 .. q + PD, level 1 planes
+// q - 3R - 1 .. q - R
+constexpr int NS0 = 2 * R + 2 + PD;            // level-0 slots (12)
 constexpr int NSP = PD + 1;                    // u^{t-1} slots
-constexpr int NS1 = 2 * R + 1;                 // level-1 slots
+constexpr int NS1 = 2 * R + 2;                 // level-1 slots (10)
 constexpr int P0 = TX0 * TY0, P1 = TX1 * TY1;  // plane sizes (floats)
 static_assert((P0 * 4) % 128 == 0 && (P1 * 4) % 128 == 0, "128-byte aligned planes");
+static_assert(NPO % 32 == 0, "whole level-2 warps");
+// coefficient vectors of a point loaded before the step's barrier (the
+// rest at the start of its update): measured at 512^3, T = 64, W25_VAR /
+// J25_VAR GLUP/s: 0 -> 76 / 81, 4 -> 81 / 86, 7 -> 82 / 72, 13 -> 50 / 54
+// (the 80 registers a 704-thread CTA allows then spill)
+constexpr int NPF = 4;
 constexpr size_t smem_of(bool wave) {
     return 4 * ((size_t)NS0 * P0 + (wave ? (size_t)NSP * P1 : 0) + (size_t)NS1 * P1) + 8 * NS0 + 16 + 128;
 }
@@ -74,38 +94,28 @@ blk25_kernel(const BlockedArgs<float> a, const __grid_constant__ CUtensorMap tm_
 
     const Geom &g = a.g;
     const int tid = threadIdx.x;
+    const bool lev1 = tid < 32 * NW1;                      // warp role: level 1 or level 2
     const int xo = blockIdx.x * TXO + R, yo = blockIdx.y * TYO + R;   // padded origin of the owned tile
     const int z0 = blockIdx.z * a.zchunk;
     const int z1 = min(z0 + a.zchunk, g.nz);
-    const int qs = z0 - 2 * R, qe = z1 + 2 * R;            // level-0 planes this chunk reads
+    const int qs = z0 - 2 * R, qe = z1 + 2 * R;            // level-0 planes this chunk reads: [qs, qe)
     const int64_t sz = g.sz, sy = g.sy, nf = g.nfield;
     const int64_t plane_elems = (int64_t)g.nx * g.ny;
 
-    // level-1 vectors of this thread: k = tid and tid + NT (while < NP1)
-    constexpr int NK1 = (NP1 + NT - 1) / NT;
-    int r1[NK1], c1[NK1];           // level-1 tile row, column
-    bool in1[NK1], act1[NK1];       // interior point vector; computed by this thread
-    int64_t g1[NK1];                // in-plane padded offset
-#pragma unroll
-    for (int u = 0; u < NK1; ++u) {
-        const int k = tid + u * NT;
-        act1[u] = k < NP1;
-        r1[u] = act1[u] ? k / NV1 : 0;
-        c1[u] = act1[u] ? (k % NV1) * V : 0;
-        const int py = yo - R + r1[u], px = xo - R + c1[u];
-        in1[u] = act1[u] && py >= R && py < g.ny + R && px >= R && px < g.nx + R;
-        g1[u] = in1[u] ? (int64_t)py * sy + px : 0;
-    }
-    // owned vector of this thread (level 2)
-    const int r2 = tid / NVO, c2 = (tid % NVO) * V;
+    // level-1 thread: vector k = tid of the level-1 tile (k < NP1)
+    const int k1 = lev1 ? tid : 0;
+    const bool act1 = lev1 && k1 < NP1;
+    const int r1 = act1 ? k1 / NV1 : 0, c1 = act1 ? (k1 % NV1) * V : 0;
+    const int py1 = yo - R + r1, px1 = xo - R + c1;
+    const bool in1 = act1 && py1 >= R && py1 < g.ny + R && px1 >= R && px1 < g.nx + R;
+    const int64_t g1 = in1 ? (int64_t)py1 * sy + px1 : 0;
+    const bool own1 = in1 && r1 >= R && r1 < R + TYO && c1 >= R && c1 < R + TXO;
+    // level-2 thread: owned vector k2
+    const int k2 = lev1 ? 0 : tid - 32 * NW1;
+    const int r2 = k2 / NVO, c2 = (k2 % NVO) * V;
     const int py2 = yo + r2, px2 = xo + c2;
-    const bool in2 = py2 < g.ny + R && px2 < g.nx + R;
+    const bool in2 = !lev1 && py2 < g.ny + R && px2 < g.nx + R;
     const int64_t g2 = in2 ? (int64_t)py2 * sy + px2 : 0;
-    // owned level-1 vectors (for out_prev and the level-1 trace)
-    bool own1[NK1];
-#pragma unroll
-    for (int u = 0; u < NK1; ++u)
-        own1[u] = in1[u] && r1[u] >= R && r1[u] < R + TYO && c1[u] >= R && c1[u] < R + TXO;
 
     bool bad = false;
     int last_issued = qs - 1;
@@ -127,111 +137,144 @@ blk25_kernel(const BlockedArgs<float> a, const __grid_constant__ CUtensorMap tm_
         for (int i = 0; i < PD && qs + i < qe; ++i) issue(qs + i);
 
     // stencil of the 13-array kinds at a 4-point vector: tile row r, column
-    // c of planes of width W; plane_at(d) is the plane d planes from the centre
-    auto update = [&](auto plane_at, int W, int r, int c, const float4 (&cf)[13], float4 prev) -> float4 {
-        const float *C = plane_at(0) + r * W + c;
+    // c of planes of width W in the ring at buf, whose 9 planes around the
+    // centre (z offsets -R..R) start at the float offsets pl[0..8]; the 13
+    // coefficient vectors are read at the point (cf: array 0) as they are
+    // needed.  The two points of each half-vector are updated by packed
+    // FP32 pairs (FADD2 / FMUL2 / FFMA2): the scalar form's terms in its
+    // order.
+    // cf: the first NPF coefficient vectors of the point, loaded before the
+    // step's barrier; the rest are read from cfp (array 0 at the point) at
+    // the start of the update, so that their latency overlaps the first
+    // terms
+    auto update = [&](const float *buf, const uint32_t (&pl)[2 * R + 1], int W, int r, int c, const float4 (&cf)[NPF],
+                      const float *cfp, float4 prev) -> float4 {
+        float4 cl[NPF < 13 ? 13 - NPF : 1];
+#pragma unroll
+        for (int t = NPF; t < 13; ++t) cl[t - NPF] = __ldg(reinterpret_cast<const float4 *>(cfp + t * nf));
+        auto coef = [&](int t) { return t < NPF ? cf[t] : cl[t - NPF]; };
+        const int rc = r * W + c;
+        const float *C = buf + pl[R] + rc;
         const float4 cv = *reinterpret_cast<const float4 *>(C);
         const float4 lv = *reinterpret_cast<const float4 *>(C - V);
         const float4 rv = *reinterpret_cast<const float4 *>(C + V);
         const float cc[4] = {cv.x, cv.y, cv.z, cv.w};
         const float ll[4] = {lv.x, lv.y, lv.z, lv.w};
         const float rr[4] = {rv.x, rv.y, rv.z, rv.w};
-        float acc[4];
-        const float c0[4] = {cf[0].x, cf[0].y, cf[0].z, cf[0].w};
-        const float pr[4] = {prev.x, prev.y, prev.z, prev.w};
-        (void)pr;
-#pragma unroll
-        for (int i = 0; i < 4; ++i) {
-            acc[i] = c0[i] * cc[i];
-            if constexpr (WAVE) acc[i] = fma(2.0f, cc[i], acc[i]) - pr[i];
+        const float4 w0 = coef(0);
+        float2 a0 = __fmul2_rn(make_float2(w0.x, w0.y), make_float2(cv.x, cv.y));
+        float2 a1 = __fmul2_rn(make_float2(w0.z, w0.w), make_float2(cv.z, cv.w));
+        if constexpr (WAVE) {
+            a0 = __fadd2_rn(__ffma2_rn(make_float2(2.0f, 2.0f), make_float2(cv.x, cv.y), a0), make_float2(-prev.x, -prev.y));
+            a1 = __fadd2_rn(__ffma2_rn(make_float2(2.0f, 2.0f), make_float2(cv.z, cv.w), a1), make_float2(-prev.z, -prev.w));
         }
 #pragma unroll
         for (int d = 1; d <= R; ++d) {
+            const float4 wx = coef(3 * d - 2), wy = coef(3 * d - 1), wz = coef(3 * d);
             const float4 yu = *reinterpret_cast<const float4 *>(C - d * W);
             const float4 yd = *reinterpret_cast<const float4 *>(C + d * W);
-            const float4 zd = *reinterpret_cast<const float4 *>(plane_at(-d) + r * W + c);
-            const float4 zu = *reinterpret_cast<const float4 *>(plane_at(d) + r * W + c);
-            const float yuu[4] = {yu.x, yu.y, yu.z, yu.w}, ydd[4] = {yd.x, yd.y, yd.z, yd.w};
-            const float zdd[4] = {zd.x, zd.y, zd.z, zd.w}, zuu[4] = {zu.x, zu.y, zu.z, zu.w};
-            const float4 wx = cf[3 * d - 2], wy = cf[3 * d - 1], wz = cf[3 * d];
-            const float wxx[4] = {wx.x, wx.y, wx.z, wx.w}, wyy[4] = {wy.x, wy.y, wy.z, wy.w};
-            const float wzz[4] = {wz.x, wz.y, wz.z, wz.w};
+            const float4 zd = *reinterpret_cast<const float4 *>(buf + pl[R - d] + rc);
+            const float4 zu = *reinterpret_cast<const float4 *>(buf + pl[R + d] + rc);
+            float xs[4];
 #pragma unroll
             for (int i = 0; i < 4; ++i) {
                 const float xl = i - d >= 0 ? cc[i - d] : ll[i - d + 4];
                 const float xr = i + d < 4 ? cc[i + d] : rr[i + d - 4];
-                acc[i] = fma(wxx[i], xl + xr, acc[i]);
-                acc[i] = fma(wyy[i], yuu[i] + ydd[i], acc[i]);
-                acc[i] = fma(wzz[i], zdd[i] + zuu[i], acc[i]);
+                xs[i] = xl + xr;
             }
+            a0 = __ffma2_rn(make_float2(wx.x, wx.y), make_float2(xs[0], xs[1]), a0);
+            a1 = __ffma2_rn(make_float2(wx.z, wx.w), make_float2(xs[2], xs[3]), a1);
+            a0 = __ffma2_rn(make_float2(wy.x, wy.y), __fadd2_rn(make_float2(yu.x, yu.y), make_float2(yd.x, yd.y)), a0);
+            a1 = __ffma2_rn(make_float2(wy.z, wy.w), __fadd2_rn(make_float2(yu.z, yu.w), make_float2(yd.z, yd.w)), a1);
+            a0 = __ffma2_rn(make_float2(wz.x, wz.y), __fadd2_rn(make_float2(zd.x, zd.y), make_float2(zu.x, zu.y)), a0);
+            a1 = __ffma2_rn(make_float2(wz.z, wz.w), __fadd2_rn(make_float2(zd.z, zd.w), make_float2(zu.z, zu.w)), a1);
         }
-        return make_float4(acc[0], acc[1], acc[2], acc[3]);
-    };
-    auto load_cf = [&](float4 (&cf)[13], int64_t off, bool on) {
-#pragma unroll
-        for (int t = 0; t < 13; ++t)
-            cf[t] = on ? __ldg(reinterpret_cast<const float4 *>(a.W + t * nf + off)) : make_float4(0.f, 0.f, 0.f, 0.f);
+        return make_float4(a0.x, a0.y, a1.x, a1.y);
     };
 
+    // ring slots, advanced by one per step (no division in the loop):
+    // s_in = level-0 slot of plane q, s_p = u^{t-1} slot of plane q,
+    // s1c = level-1 slot of plane q - R
+    int s_in = 0, s_p = 0, s1c = NS1 - R;   // plane qs - R sits in level-1 slot (-R) mod NS1
+    uint32_t par = 0;                        // phase of level-0 slot s_in's barrier
     bool stop = false;
-    for (int q = qs; q < qe && !stop; ++q) {
-        const int pc1 = q - R, pc2 = q - 2 * R;   // planes of level 1 and 2 in this step
-        const bool l1on = q >= qs + 2 * R && (unsigned)pc1 < (unsigned)g.nz;
-        const bool l2on = q >= qs + 4 * R;        // pc2 in [z0, z1)
-        // coefficients, issued before the wait: level 2 (owned vector) and
-        // the first level-1 vector
-        float4 cfa[13], cf2[13];
-        load_cf(cf2, (int64_t)(pc2 + R) * sz + g2, l2on && in2);
-        load_cf(cfa, (int64_t)(pc1 + R) * sz + g1[0], l1on && in1[0]);
-        bad |= !pv::mbar_wait_or_abort(&bars[(q - qs) % NS0], (uint32_t)(((q - qs) / NS0) & 1), wlim, &abort_word);
+    // steps qs .. qe: level 1 at plane q - R while level-0 plane q exists
+    // (q < qe), level 2 at plane q - 2R - 1 (the last step has no level 1)
+    for (int q = qs; q <= qe && !stop; ++q) {
+        // the 13 coefficient vectors of this step's point (level 1: plane
+        // q - R, level 2: plane q - 2R - 1), issued before the wait and the
+        // barrier so that their latency overlaps them
+        float4 cf[NPF];
+        const int pc = lev1 ? q - R : q - 2 * R - 1;
+        const float *const cfp = a.W + ((int64_t)(pc + R) * sz + (lev1 ? g1 : g2));
+        {
+            const bool on = lev1 ? (in1 && q >= qs + 2 * R && q < qe && (unsigned)pc < (unsigned)g.nz)
+                                 : (in2 && q >= qs + 4 * R + 1);
+#pragma unroll
+            for (int t = 0; t < NPF; ++t)
+                cf[t] = on ? __ldg(reinterpret_cast<const float4 *>(cfp + t * nf)) : make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+        if (q < qe) bad |= !pv::mbar_wait_or_abort(&bars[s_in], par, wlim, &abort_word);
         if ((q - qs) % 8 == 7) stop = __syncthreads_or(bad);
         else __syncthreads();
         if (tid == 0 && q + PD < qe) issue(q + PD);
-        // ---- level 1 at plane pc1 (level-1 tile), into level-1 slot of pc1
-        auto l0_at = [&](int d) -> const float * {
-            return s0 + ((q - R + d - qs + NS0 * 4) % NS0) * P0;   // level-0 plane pc1 + d
-        };
-        float *const l1_out = s1 + ((pc1 - qs + NS1 * 4) % NS1) * P1;
-        const float *const upl = sp + ((q - qs) % NSP) * P1;
+        if (lev1) {
+            // ---- level 1 at plane pc1 (level-1 tile), into level-1 slot s1c
+            const int pc1 = q - R;
+            const bool l1on = q >= qs + 2 * R && q < qe;
+            if (l1on && act1) {
+                uint32_t pl0[2 * R + 1];   // level-0 planes pc1 - R .. pc1 + R = q - 2R .. q
 #pragma unroll
-        for (int u = 0; u < NK1; ++u) {
-            if (!act1[u]) continue;
-            float4 cf[13];
-            if (u == 0) {
-#pragma unroll
-                for (int t = 0; t < 13; ++t) cf[t] = cfa[t];
-            } else {
-                load_cf(cf, (int64_t)(pc1 + R) * sz + g1[u], l1on && in1[u]);
+                for (int i = 0; i <= 2 * R; ++i) {
+                    int sl = s_in - 2 * R + i;
+                    sl += sl < 0 ? NS0 : 0;
+                    pl0[i] = (uint32_t)(sl * P0);
+                }
+                float4 prev = make_float4(0.f, 0.f, 0.f, 0.f);
+                if constexpr (WAVE) prev = *reinterpret_cast<const float4 *>(sp + s_p * P1 + r1 * TX1 + c1);
+                float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+                if (in1 && (unsigned)pc1 < (unsigned)g.nz)
+                    v = update(s0, pl0, TX0, r1 + R, c1 + R, cf, cfp, prev);
+                *reinterpret_cast<float4 *>(s1 + s1c * P1 + r1 * TX1 + c1) = v;
+                if (own1 && (unsigned)pc1 - (unsigned)z0 < (unsigned)(z1 - z0)) {
+                    const int64_t o = (int64_t)(pc1 + R) * sz + g1;
+                    if (a.out_prev && dbg_store_ok(a.dbg, g, o, V)) *reinterpret_cast<float4 *>(a.out_prev + o) = v;
+                    if (a.trace && pc1 == a.rcv_z) {
+                        float *tr = a.trace + (int64_t)(py1 - R) * g.nx + (px1 - R);
+                        tr[0] = v.x; tr[1] = v.y; tr[2] = v.z; tr[3] = v.w;
+                    }
+                }
             }
-            float4 prev = make_float4(0.f, 0.f, 0.f, 0.f);
-            if constexpr (WAVE) prev = *reinterpret_cast<const float4 *>(upl + r1[u] * TX1 + c1[u]);
-            float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-            if (l1on && in1[u]) v = update(l0_at, TX0, r1[u] + R, c1[u] + R, cf, prev);
-            *reinterpret_cast<float4 *>(l1_out + r1[u] * TX1 + c1[u]) = v;
-            if (own1[u] && (unsigned)pc1 - (unsigned)z0 < (unsigned)(z1 - z0)) {
-                const int64_t o = (int64_t)(pc1 + R) * sz + g1[u];
-                if (a.out_prev && dbg_store_ok(a.dbg, g, o, V)) *reinterpret_cast<float4 *>(a.out_prev + o) = v;
-                if (a.trace && pc1 == a.rcv_z) {
-                    float *tr = a.trace + (int64_t)(yo - R + r1[u] - R) * g.nx + (xo - R + c1[u] - R);
+        } else {
+            // ---- level 2 at plane pc2 (owned tile): level-1 planes pc2-R..pc2+R
+            const int pc2 = q - 2 * R - 1;
+            if (q >= qs + 4 * R + 1 && in2) {
+                uint32_t pl1[2 * R + 1];   // level-1 planes pc2 - R .. pc2 + R = q - 3R - 1 .. q - R - 1
+#pragma unroll
+                for (int i = 0; i <= 2 * R; ++i) {
+                    int sl = s1c - 2 * R - 1 + i;
+                    sl += sl < 0 ? NS1 : 0;
+                    pl1[i] = (uint32_t)(sl * P1);
+                }
+                float4 prev = make_float4(0.f, 0.f, 0.f, 0.f);
+                if constexpr (WAVE) {   // level 0 at plane pc2 = q - 2R - 1 (tile offset 2R)
+                    int sl = s_in - 2 * R - 1;
+                    sl += sl < 0 ? NS0 : 0;
+                    prev = *reinterpret_cast<const float4 *>(s0 + sl * P0 + (r2 + 2 * R) * TX0 + c2 + 2 * R);
+                }
+                const float4 v = update(s1, pl1, TX1, r2 + R, c2 + R, cf, cfp, prev);
+                const int64_t o = (int64_t)(pc2 + R) * sz + g2;
+                if (dbg_store_ok(a.dbg, g, o, V)) *reinterpret_cast<float4 *>(a.out + o) = v;
+                if (a.trace && pc2 == a.rcv_z) {
+                    float *tr = a.trace + plane_elems + (int64_t)(py2 - R) * g.nx + (px2 - R);
                     tr[0] = v.x; tr[1] = v.y; tr[2] = v.z; tr[3] = v.w;
                 }
             }
         }
-        __syncthreads();
-        // ---- level 2 at plane pc2 (owned tile): level-1 planes pc2-R..pc2+R
-        if (l2on && in2) {
-            auto l1_at = [&](int d) -> const float * { return s1 + ((pc2 + d - qs + NS1 * 4) % NS1) * P1; };
-            float4 prev = make_float4(0.f, 0.f, 0.f, 0.f);
-            if constexpr (WAVE)   // level 0 at plane pc2, the owned point (tile offset 2R)
-                prev = *reinterpret_cast<const float4 *>(s0 + ((pc2 - qs) % NS0) * P0 + (r2 + 2 * R) * TX0 + c2 + 2 * R);
-            const float4 v = update(l1_at, TX1, r2 + R, c2 + R, cf2, prev);
-            const int64_t o = (int64_t)(pc2 + R) * sz + g2;
-            if (dbg_store_ok(a.dbg, g, o, V)) *reinterpret_cast<float4 *>(a.out + o) = v;
-            if (a.trace && pc2 == a.rcv_z) {
-                float *tr = a.trace + plane_elems + (int64_t)(py2 - R) * g.nx + (px2 - R);
-                tr[0] = v.x; tr[1] = v.y; tr[2] = v.z; tr[3] = v.w;
-            }
-        }
+        // advance the ring slots
+        if (++s_in == NS0) { s_in = 0; par ^= 1u; }
+        if (++s_p == NSP) s_p = 0;
+        if (++s1c == NS1) s1c = 0;
     }
     if (__syncthreads_or(bad) && tid == 0) {
         for (int qq = max(last_issued - PD + 1, qs); qq <= last_issued; ++qq)
@@ -287,7 +330,7 @@ inline cudaError_t launch_blk25(int kind, const BlockedArgs<float> &a, cudaStrea
         const int chunk = (a.g.nz + nzc - 1) / nzc;
         if (nzc > 1 && chunk < 16 * R) break;
         const int64_t ctas = tiles * ((a.g.nz + chunk - 1) / chunk);
-        const double cost = (double)((ctas + resident - 1) / resident) * (chunk + 4 * R);
+        const double cost = (double)((ctas + resident - 1) / resident) * (chunk + 4 * R + 1);
         if (cost < best_cost * 0.999) { best_cost = cost; best = nzc; }
     }
     BlockedArgs<float> b = a;

@@ -184,16 +184,20 @@ def dram_bytes_per_lup(kind: int, word: int, B: int = 1) -> float:
 def two_level_block(kind: int) -> dict:
     """On-chip working set of one CTA of the two-level pass of the 13-array
     kinds (scheme 4, FP32): an owned 64 x 16 tile, level 1 on it with an
-    R = 4 halo (72 x 24), level 0 with a 2R halo (80 x 32); plane rings of
-    2R + 1 + 2 level-0 planes, 2R + 1 level-1 planes and, for the wave kind,
-    3 planes of u^{t-1} beside level 0; one mbarrier per level-0 slot, the
-    abort word, alignment slack."""
+    R = 4 halo (72 x 24, one 4-point vector per thread of 14 warps), level
+    2 on the owned tile (8 warps), level 0 with a 2R halo (80 x 32).  Level
+    2 runs one plane behind level 1's output, so the rings hold 2R + 2 + 1
+    level-0 planes (one in flight), 2R + 2 level-1 planes and, for the wave
+    kind, 2 planes of u^{t-1} beside level 0; one mbarrier per level-0
+    slot, the abort word, alignment slack."""
     R, word = 4, 4
     TXO, TYO = 64, 16
     P1 = (TXO + 2 * R) * (TYO + 2 * R)
     P0 = (TXO + 4 * R) * (TYO + 4 * R)
-    ns0 = 2 * R + 1 + 2
+    pd = 1                                         # level-0 planes in flight
+    ns0 = 2 * R + 2 + pd
     wave = _SECOND_ORDER[kind]
-    smem = word * (ns0 * P0 + (3 * P1 if wave else 0) + (2 * R + 1) * P1) + 8 * ns0 + 16 + 128
-    return {"smem_bytes": smem, "threads": 256, "computed": (TXO + 2 * R, TYO + 2 * R), "owned": (TXO, TYO),
+    smem = word * (ns0 * P0 + ((pd + 1) * P1 if wave else 0) + (2 * R + 2) * P1) + 8 * ns0 + 16 + 128
+    threads = 32 * (-(-((TXO + 2 * R) // 4 * (TYO + 2 * R)) // 32) + TXO // 4 * TYO // 32)
+    return {"smem_bytes": smem, "threads": threads, "computed": (TXO + 2 * R, TYO + 2 * R), "owned": (TXO, TYO),
             "fits": smem <= SMEM_PER_CTA, "redundancy": ((TXO + 2 * R) * (TYO + 2 * R) + TXO * TYO) / (2.0 * TXO * TYO)}
