@@ -89,10 +89,10 @@ enum stencil_option {
        shared-memory planes with diamond (split) tiles in y and overlapped x,
        3 = register wavefront with overlapped tiles (7-point kinds; FP32
        depths 1-4, FP64 depths 1-2; needs an even padded row length, else
-       the plan runs plain passes), 4 = two-level pass of the 13-array
-       25-point kinds (W25_VAR, J25_VAR; FP32, depth 2, nx a multiple of 4):
-       plane rings of both levels in shared memory, level-0 planes and
-       u^{t-1} staged by TMA. */
+       the plan runs plain passes), 4 = two-level pass of the 25-point
+       kinds W25_VAR, J25_VAR and W25_CONST (FP32, depth 2, nx a multiple
+       of 4): plane rings of both levels in shared memory, level-0 planes
+       and u^{t-1} staged by TMA, the warps split by level. */
     STENCIL_OPT_SCHEME = 2,
     /* Read-only: bytes of device scratch the plan holds. */
     STENCIL_OPT_SCRATCH_BYTES = 3,
@@ -325,8 +325,8 @@ int stencil_debug_bad_store(stencil_plan_t plan, int64_t *index);
  * overlapped halo of a blocked pass), and the x and y extent of the points it
  * owns.  Served for the register wavefront (scheme 3, variant 0 = its
  * default tile or 10-12, every depth it supports: 1-4 FP32, 1-2 FP64, 7-point
- * kinds), the two-level pass of the 13-array kinds (scheme 4, levels 2,
- * FP32) and the vectorised one-level sweep (levels 1, variants 13-16);
+ * kinds), the two-level pass of the 25-point kinds (scheme 4: W25_VAR,
+ * J25_VAR, W25_CONST; levels 2, FP32) and the vectorised one-level sweep (levels 1, variants 13-16);
  * STENCIL_EUNSUPPORTED for other families, STENCIL_EINVAL for a bad
  * argument.  Performs no CUDA call. */
 int stencil_pass_info(int kind, int dtype, int levels, int scheme, int variant, int64_t *info);

@@ -1,5 +1,6 @@
 // blk25_impl.cuh -- temporally blocked pass of the 13-array 25-point kinds
-// (Fig. 1d structure, R = 4): two time levels per sweep over HBM, FP32.
+// (Fig. 1d structure, R = 4) and of the constant wave (Fig. 1e form): two
+// time levels per sweep over HBM, FP32.
 // Included by plainv_f32.cu (TMA / mbarrier helpers, tensor maps, the
 // bounded-wait counter of that translation unit).
 //
@@ -32,8 +33,13 @@
 // Level 2 and, for the next pass's u^{t-1}, level 1 are written for the owned
 // points; the receiver trace of both levels as well.
 //
+// The constant wave (W25_CONST) runs the same pass with its 5 folded
+// weights in registers and no coefficient arrays.
+//
 // Measured (512^3, FP32, T = 64): 81 GLUP/s for W25_VAR and 86 for J25_VAR,
-// against 103 and 112 for the one-level TMA sweep, so it is not the default.
+// against 103 and 112 for the one-level TMA sweep, so it is not the default;
+// W25_CONST (T = 100) 190-194 against 438: one 4-point vector per warp and
+// a barrier per step leave its short steps latency-bound.
 // Earlier forms: one 256-thread CTA doing both levels in turn with all 13
 // coefficient vectors prefetched (72 / 76 GLUP/s; 245 registers and 196 KB
 // of rings leave 8 warps per SM, 28% issue activity); the same split by
@@ -54,17 +60,18 @@ constexpr int NVO = TXO / V, NPO = NVO * TYO;  // owned vectors per row / per pl
 constexpr int NW1 = (NP1 + 31) / 32;           // level-1 warps (14)
 constexpr int NW2 = NPO / 32;                  // level-2 warps (8)
 constexpr int NT = 32 * (NW1 + NW2);           // threads (704)
-// level-0 planes in flight: one (a step takes several microseconds, far
-// longer than a plane's copy), which keeps the wave kind's rings under
-// the 196 KB shared-memory carve-out and leaves L1 room for the
-// coefficient loads in flight
-constexpr int PD = 1;
+// level-0 planes in flight: one for the 13-array kinds (a step there takes
+// several microseconds, far longer than a plane's copy, and one plane keeps
+// the wave kind's rings under the 196 KB shared-memory carve-out, leaving
+// L1 room for the coefficient loads in flight); two for the constant wave,
+// whose short steps would otherwise wait for every copy
+constexpr int pd_of(int kind) { return kind == W25_CONST ? 2 : 1; }
 // level 2 updates plane q - 2R - 1 in step q, one plane behind the level-1
 // plane q - R written in the same step, so the two levels need no barrier
 // between them: level 0 keeps planes q - 2R - 1 .. q + PD, level 1 planes
 // q - 3R - 1 .. q - R
-constexpr int NS0 = 2 * R + 2 + PD;            // level-0 slots (12)
-constexpr int NSP = PD + 1;                    // u^{t-1} slots
+constexpr int ns0_of(int kind) { return 2 * R + 2 + pd_of(kind); }   // level-0 slots
+constexpr int nsp_of(int kind) { return pd_of(kind) + 1; }           // u^{t-1} slots
 constexpr int NS1 = 2 * R + 2;                 // level-1 slots (10)
 constexpr int P0 = TX0 * TY0, P1 = TX1 * TY1;  // plane sizes (floats)
 static_assert((P0 * 4) % 128 == 0 && (P1 * 4) % 128 == 0, "128-byte aligned planes");
@@ -74,8 +81,10 @@ static_assert(NPO % 32 == 0, "whole level-2 warps");
 // J25_VAR GLUP/s: 0 -> 76 / 81, 4 -> 81 / 86, 7 -> 82 / 72, 13 -> 50 / 54
 // (the 80 registers a 704-thread CTA allows then spill)
 constexpr int NPF = 4;
-constexpr size_t smem_of(bool wave) {
-    return 4 * ((size_t)NS0 * P0 + (wave ? (size_t)NSP * P1 : 0) + (size_t)NS1 * P1) + 8 * NS0 + 16 + 128;
+constexpr size_t smem_of(int kind) {
+    const bool wave = kind != J25_VAR;
+    return 4 * ((size_t)ns0_of(kind) * P0 + (wave ? (size_t)nsp_of(kind) * P1 : 0) + (size_t)NS1 * P1) +
+           8 * ns0_of(kind) + 16 + 128;
 }
 }  // namespace b25
 
@@ -85,6 +94,8 @@ blk25_kernel(const BlockedArgs<float> a, const __grid_constant__ CUtensorMap tm_
              const __grid_constant__ CUtensorMap tm_p) {
     using namespace b25;
     constexpr bool WAVE = KindTraits<KIND>::WAVE;
+    constexpr bool CW = KIND == W25_CONST;   // constant weights: no coefficient arrays
+    constexpr int PD = pd_of(KIND), NS0 = ns0_of(KIND), NSP = nsp_of(KIND);
     extern __shared__ __align__(128) unsigned char smem_raw[];
     float *const s0 = reinterpret_cast<float *>((reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
     float *const sp = s0 + NS0 * P0;                      // u^{t-1} slots (wave kind)
@@ -147,11 +158,18 @@ blk25_kernel(const BlockedArgs<float> a, const __grid_constant__ CUtensorMap tm_
     // step's barrier; the rest are read from cfp (array 0 at the point) at
     // the start of the update, so that their latency overlaps the first
     // terms
+    // constant wave: the folded weights s0 .. s4
+    float sc[R + 1];
+#pragma unroll
+    for (int d = 0; d <= R; ++d) sc[d] = (float)a.s.c[d];
+    (void)sc;
     auto update = [&](const float *buf, const uint32_t (&pl)[2 * R + 1], int W, int r, int c, const float4 (&cf)[NPF],
                       const float *cfp, float4 prev) -> float4 {
         float4 cl[NPF < 13 ? 13 - NPF : 1];
+        if constexpr (!CW) {
 #pragma unroll
-        for (int t = NPF; t < 13; ++t) cl[t - NPF] = __ldg(reinterpret_cast<const float4 *>(cfp + t * nf));
+            for (int t = NPF; t < 13; ++t) cl[t - NPF] = __ldg(reinterpret_cast<const float4 *>(cfp + t * nf));
+        }
         auto coef = [&](int t) { return t < NPF ? cf[t] : cl[t - NPF]; };
         const int rc = r * W + c;
         const float *C = buf + pl[R] + rc;
@@ -161,6 +179,35 @@ blk25_kernel(const BlockedArgs<float> a, const __grid_constant__ CUtensorMap tm_
         const float cc[4] = {cv.x, cv.y, cv.z, cv.w};
         const float ll[4] = {lv.x, lv.y, lv.z, lv.w};
         const float rr[4] = {rv.x, rv.y, rv.z, rv.w};
+        if constexpr (CW) {
+            // the constant wave (weights folded on the host: s0 = 2 + alpha w0,
+            // s_d = alpha w_d): s0 u - u^{t-1} + sum_d s_d ((x pair + y pair) + z pair)
+            const float2 s0 = make_float2(sc[0], sc[0]);
+            float2 a0 = __ffma2_rn(s0, make_float2(cv.x, cv.y), make_float2(-prev.x, -prev.y));
+            float2 a1 = __ffma2_rn(s0, make_float2(cv.z, cv.w), make_float2(-prev.z, -prev.w));
+#pragma unroll
+            for (int d = 1; d <= R; ++d) {
+                const float4 yu = *reinterpret_cast<const float4 *>(C - d * W);
+                const float4 yd = *reinterpret_cast<const float4 *>(C + d * W);
+                const float4 zd = *reinterpret_cast<const float4 *>(buf + pl[R - d] + rc);
+                const float4 zu = *reinterpret_cast<const float4 *>(buf + pl[R + d] + rc);
+                float xs[4];
+#pragma unroll
+                for (int i = 0; i < 4; ++i) {
+                    const float xl = i - d >= 0 ? cc[i - d] : ll[i - d + 4];
+                    const float xr = i + d < 4 ? cc[i + d] : rr[i + d - 4];
+                    xs[i] = xl + xr;
+                }
+                const float2 sd = make_float2(sc[d], sc[d]);
+                const float2 t0 = __fadd2_rn(__fadd2_rn(make_float2(xs[0], xs[1]), __fadd2_rn(make_float2(yu.x, yu.y), make_float2(yd.x, yd.y))),
+                                             __fadd2_rn(make_float2(zd.x, zd.y), make_float2(zu.x, zu.y)));
+                const float2 t1 = __fadd2_rn(__fadd2_rn(make_float2(xs[2], xs[3]), __fadd2_rn(make_float2(yu.z, yu.w), make_float2(yd.z, yd.w))),
+                                             __fadd2_rn(make_float2(zd.z, zd.w), make_float2(zu.z, zu.w)));
+                a0 = __ffma2_rn(sd, t0, a0);
+                a1 = __ffma2_rn(sd, t1, a1);
+            }
+            return make_float4(a0.x, a0.y, a1.x, a1.y);
+        }
         const float4 w0 = coef(0);
         float2 a0 = __fmul2_rn(make_float2(w0.x, w0.y), make_float2(cv.x, cv.y));
         float2 a1 = __fmul2_rn(make_float2(w0.z, w0.w), make_float2(cv.z, cv.w));
@@ -206,8 +253,8 @@ blk25_kernel(const BlockedArgs<float> a, const __grid_constant__ CUtensorMap tm_
         // barrier so that their latency overlaps them
         float4 cf[NPF];
         const int pc = lev1 ? q - R : q - 2 * R - 1;
-        const float *const cfp = a.W + ((int64_t)(pc + R) * sz + (lev1 ? g1 : g2));
-        {
+        const float *const cfp = CW ? nullptr : a.W + ((int64_t)(pc + R) * sz + (lev1 ? g1 : g2));
+        if constexpr (!CW) {
             const bool on = lev1 ? (in1 && q >= qs + 2 * R && q < qe && (unsigned)pc < (unsigned)g.nz)
                                  : (in2 && q >= qs + 4 * R + 1);
 #pragma unroll
@@ -283,18 +330,19 @@ blk25_kernel(const BlockedArgs<float> a, const __grid_constant__ CUtensorMap tm_
     }
 }
 
-// Whether the two-level pass serves the plan: FP32, 13-array kinds, 2
-// levels, whole 4-point vectors along x, planes below 2^30 points.
+// Whether the two-level pass serves the plan: FP32, the 13-array kinds and
+// the constant wave, 2 levels, whole 4-point vectors along x, planes below
+// 2^30 points.
 inline bool blk25_supported(int kind, int levels, const Geom &g) {
-    return (kind == W25_VAR || kind == J25_VAR) && levels == 2 && g.nx % 4 == 0 &&
+    return (kind == W25_VAR || kind == J25_VAR || kind == W25_CONST) && levels == 2 && g.nx % 4 == 0 &&
            (int64_t)g.px * g.py < ((int64_t)1 << 30);
 }
 
 // Resources (as stencil_pass_info reports them).
 inline bool blk25_info(int kind, int64_t *info) {
     using namespace b25;
-    if (kind != W25_VAR && kind != J25_VAR) return false;
-    info[0] = (int64_t)smem_of(kind == W25_VAR);
+    if (kind != W25_VAR && kind != J25_VAR && kind != W25_CONST) return false;
+    info[0] = (int64_t)smem_of(kind);
     info[1] = NT;
     info[2] = TX1;
     info[3] = TY1;
@@ -305,16 +353,16 @@ inline bool blk25_info(int kind, int64_t *info) {
 
 inline cudaError_t launch_blk25(int kind, const BlockedArgs<float> &a, cudaStream_t st, int num_sms) {
     using namespace b25;
-    const bool wave = kind == W25_VAR;
+    const bool wave = kind != J25_VAR;   // W25_VAR, W25_CONST: second order in time
     CUtensorMap tm_u, tm_p;
     memset(&tm_u, 0, sizeof(tm_u));
     memset(&tm_p, 0, sizeof(tm_p));
     cudaError_t e = pv::make_tmap(&tm_u, a.u, 4, a.g, TX0, TY0);
     if (e == cudaSuccess && wave) e = pv::make_tmap(&tm_p, a.u_prev, 4, a.g, TX1, TY1);
     if (e != cudaSuccess) return e;
-    const size_t smem = smem_of(wave);
-    auto kern = wave ? blk25_kernel<W25_VAR> : blk25_kernel<J25_VAR>;
-    static_assert(smem_of(true) <= 227 * 1024, "shared memory per CTA");
+    const size_t smem = smem_of(kind);
+    auto kern = kind == W25_VAR ? blk25_kernel<W25_VAR> : kind == W25_CONST ? blk25_kernel<W25_CONST> : blk25_kernel<J25_VAR>;
+    static_assert(smem_of(W25_VAR) <= 227 * 1024 && smem_of(W25_CONST) <= 227 * 1024, "shared memory per CTA");
     e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     int per_sm = 0;

@@ -186,15 +186,16 @@ def two_level_block(kind: int) -> dict:
     kinds (scheme 4, FP32): an owned 64 x 16 tile, level 1 on it with an
     R = 4 halo (72 x 24, one 4-point vector per thread of 14 warps), level
     2 on the owned tile (8 warps), level 0 with a 2R halo (80 x 32).  Level
-    2 runs one plane behind level 1's output, so the rings hold 2R + 2 + 1
-    level-0 planes (one in flight), 2R + 2 level-1 planes and, for the wave
-    kind, 2 planes of u^{t-1} beside level 0; one mbarrier per level-0
-    slot, the abort word, alignment slack."""
+    2 runs one plane behind level 1's output, so the rings hold 2R + 2 + PD
+    level-0 planes (PD in flight: 1, 2 for the constant wave), 2R + 2
+    level-1 planes and, for the wave kinds, PD + 1 planes of u^{t-1} beside
+    level 0; one mbarrier per level-0 slot, the abort word, alignment
+    slack."""
     R, word = 4, 4
     TXO, TYO = 64, 16
     P1 = (TXO + 2 * R) * (TYO + 2 * R)
     P0 = (TXO + 4 * R) * (TYO + 4 * R)
-    pd = 1                                         # level-0 planes in flight
+    pd = 2 if kind == W25_CONST else 1             # level-0 planes in flight
     ns0 = 2 * R + 2 + pd
     wave = _SECOND_ORDER[kind]
     smem = word * (ns0 * P0 + ((pd + 1) * P1 if wave else 0) + (2 * R + 2) * P1) + 8 * ns0 + 16 + 128

@@ -47,7 +47,7 @@ def model_candidates(kind: int, dtype: int):
         out.append((1, 0, v, m))
     for v in range(1, 10):
         out.append((1, 0, v, {"family": "streaming tile", "fits": True, "redundancy": 1.0}))
-    if kind in (st.W25_VAR, st.J25_VAR) and dtype == st.F32:
+    if kind in (st.W25_VAR, st.J25_VAR, st.W25_CONST) and dtype == st.F32:
         m = pm.two_level_block(kind)
         m["family"] = "two-level 13-array pass"
         out.append((2, 4, 0, m))

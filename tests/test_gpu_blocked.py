@@ -185,12 +185,12 @@ def test_tune_forward_picks_a_valid_configuration(st, kind, dtype):
     plan.close()
 
 
-# ---- two-level pass of the 13-array 25-point kinds (scheme 4)
+# ---- two-level pass of the 13-array 25-point kinds and the constant wave (scheme 4)
 
 B25_SHAPES = [(136, 45, 40), (64, 19, 11), (200, 33, 70), (8, 7, 5)]
 
 
-@pytest.mark.parametrize("kind", [4, 5])
+@pytest.mark.parametrize("kind", [3, 4, 5])
 @pytest.mark.parametrize("shape", B25_SHAPES)
 @pytest.mark.parametrize("T", [9, 4, 2])
 def test_two_level_25pt_pass_fp32(st, kind, shape, T):

@@ -98,7 +98,7 @@ def test_block_model_reproduces_profiled_shared_memory(e):
 
 
 def test_two_level_model_matches_library(st):
-    for kind in (4, 5):
+    for kind in (3, 4, 5):
         ref = st.pass_info(kind, 1, 2, 4, 0)
         m = pm.two_level_block(kind)
         assert (m["smem_bytes"], m["threads"], tuple(m["computed"]), tuple(m["owned"])) == (
