@@ -130,3 +130,22 @@ def test_schedule_leaves_state_in_caller_buffers(st, kind, b, dtype):
             assert ncopy <= (2 if T == 1 else 1)
         else:
             assert ops == []
+
+
+def _header_enum(prefix):
+    src = open(os.path.join(ROOT, "include", "stencil.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return {m.group(1): int(m.group(2)) for m in re.finditer(r"\b" + prefix + r"([A-Z0-9_]+)\s*=\s*(-?\d+)", src)}
+
+
+def test_binding_option_constants_match_header(st):
+    """Every STENCIL_OPT_* value of the header is the binding's OPT_* constant
+    of the same name (and the binding defines no other)."""
+    hdr = _header_enum("STENCIL_OPT_")
+    assert hdr and hdr == {k[4:]: v for k, v in vars(st).items() if k.startswith("OPT_")}
+
+
+def test_binding_status_constants_match_header(st):
+    hdr = _header_enum("STENCIL_")
+    for name in ("OK", "EINVAL", "EUNSUPPORTED", "ENOMEM", "ECUDA", "ETIMEOUT"):
+        assert getattr(st, name) == hdr[name], name
