@@ -152,14 +152,16 @@ enum stencil_option {
     STENCIL_OPT_TEST_SKIP_COPY = 8,
     /* Time levels per pass of stencil_adjoint (Sect. 4.1 wavefront applied
        to the transposed sweep): 1 = one level per pass, 2 = passes of two
-       levels for the 7-point kinds (the register wavefront's adjoint; each
-       pass reads lam^{t+1} and the coefficients once and writes lam^t and
-       lam^{t-1}; EUNSUPPORTED for other kinds or where the wavefront does
-       not serve the geometry).  With a gradient, levels are paired only
+       levels for the 7-point kinds (the register wavefront's adjoint) and,
+       in FP32, the 13-array kinds W25_VAR and J25_VAR (the two-level pass's
+       adjoint, nx a multiple of 4); each pass reads lam^{t+1} (and
+       lam^{t+2}) and the coefficients once and writes lam^t and lam^{t-1};
+       EUNSUPPORTED for other kinds or geometries the pass does not serve.  With a gradient, levels are paired only
        inside a gradient batch (STENCIL_OPT_GRAD_BATCH >= 2); with batch 1
-       every pass is one level.  0 = default: 2 in FP32 where served
+       every pass is one level.  0 = default: 2 for the FP32 7-point kinds
        (measured at 512^3: 7-point variable 259 vs 129 GLUP/s, constant 789
-       vs 584), 1 in FP64 (bound by the FP64 pipe either way).  Passes run
+       vs 584), else 1 (FP64 is bound by the FP64 pipe either way; the
+       13-array kinds' pass measures 37-39 vs 91-94 GLUP/s).  Passes run
        the plan's register wavefront tile (variants 10-12), else the 64x32
        tile of 2 rows per thread (variable kind) or the 64x64 tile
        (constant kind).  Reading it gives the depth the adjoint runs. */

@@ -274,18 +274,24 @@ bool pass_supported(const stencil_plan_s *p, int levels) {
     return blocked_supported(p->kind, p->dtype, levels);
 }
 
-// Adjoint passes of depth 2 (the register wavefront's adjoint, 7-point
-// kinds, both levels written): served where the wavefront serves a forward
-// pass of depth 2 on the plan's geometry.
+// Adjoint passes of depth 2 (both levels written): the register
+// wavefront's adjoint for the 7-point kinds where the wavefront serves a
+// forward pass of depth 2 on the plan's geometry; the two-level pass's
+// adjoint for the 13-array kinds in FP32 where it serves the forward.
 bool adj_pass_supported(const stencil_plan_s *p) {
-    return (p->kind == J7_CONST || p->kind == J7_VAR) && wavefront_supported(p->kind, p->dtype, 2, p->g);
+    if (p->kind == J7_CONST || p->kind == J7_VAR) return wavefront_supported(p->kind, p->dtype, 2, p->g);
+    return (p->kind == W25_VAR || p->kind == J25_VAR) && p->dtype == STENCIL_F32 &&
+           blk25_supported_f32(p->kind, 2, p->g);
 }
 
-// Default adjoint depth: 2 in FP32 (measured at 512^3, T = 64: J7_VAR 259 vs
-// 129 GLUP/s, J7_CONST 789 vs 584), 1 in FP64 (FP64-pipe bound: 54.0 vs
-// 55.3 for J7_VAR).
+// Default adjoint depth: 2 for the FP32 7-point kinds (measured at 512^3,
+// T = 64: J7_VAR 259 vs 129 GLUP/s, J7_CONST 789 vs 584), else 1 (FP64 is
+// bound by the FP64 pipe: 54.0 vs 55.3 for J7_VAR; the 13-array kinds' pass
+// gathers 29 coefficient vectors per point vector and is slower than their
+// one-level adjoint).
 int effective_adj_block(const stencil_plan_s *p) {
-    const int b = p->adj_tb > 0 ? p->adj_tb : (p->dtype == STENCIL_F32 ? 2 : 1);
+    const bool r1 = p->kind == J7_CONST || p->kind == J7_VAR;
+    const int b = p->adj_tb > 0 ? p->adj_tb : (p->dtype == STENCIL_F32 && r1 ? 2 : 1);
     return (b == 2 && adj_pass_supported(p)) ? 2 : 1;
 }
 
@@ -382,15 +388,17 @@ cudaError_t plain_step(stencil_plan_s *p, bool adjoint, const Scalars &s, const 
     return launch_plain<T>(p->kind, adjoint, a, st, p->num_sms);
 }
 
-// One depth-2 adjoint pass of the 7-point kinds: lam^{t+1} (in) gives
-// lam^t (into out1, if not null) and lam^{t-1} (into out2); inj1 is the
-// residual plane of the first level (the second level's is the plane before
-// it in the residual stack), added on plane rcv_z.
+// One depth-2 adjoint pass: lam^{t+1} (in, with lam^{t+2} in in_p for the
+// second-order kinds) gives lam^t (into out1, if not null) and lam^{t-1}
+// (into out2); inj1 is the residual plane of the first level (the second
+// level's is the plane before it in the residual stack), added on plane
+// rcv_z.
 template <typename T>
-cudaError_t adjoint_pair(stencil_plan_s *p, const Scalars &s, const stencil_coeffs_t *coeffs, const void *in,
-                         void *out1, void *out2, const T *inj1, int64_t rcv_z, cudaStream_t st) {
+cudaError_t adjoint_pair(stencil_plan_s *p, const Scalars &s, const stencil_coeffs_t *coeffs, const void *in_p,
+                         const void *in, void *out1, void *out2, const T *inj1, int64_t rcv_z, cudaStream_t st) {
     BlockedArgs<T> a;
     memset(&a, 0, sizeof(a));
+    a.u_prev = (const T *)in_p;   // lam^{t+2} (second-order kinds)
     a.u = (const T *)in;
     a.out_prev = (T *)out1;
     a.out = (T *)out2;
@@ -403,7 +411,9 @@ cudaError_t adjoint_pair(stencil_plan_s *p, const Scalars &s, const stencil_coef
     a.wait_limit = p->wait_limit;
     a.inject = inj1;
     a.inject_step = -(int64_t)p->g.nx * p->g.ny;
-    return launch_wavefront_adj<T>(p->kind, a, adj_tile(p), st, p->num_sms);
+    if (p->kind == J7_CONST || p->kind == J7_VAR) return launch_wavefront_adj<T>(p->kind, a, adj_tile(p), st, p->num_sms);
+    if constexpr (sizeof(T) == 4) return launch_blk25_adj_f32(p->kind, a, st, p->num_sms);
+    return cudaErrorNotSupported;
 }
 
 template <typename T>
@@ -455,10 +465,11 @@ int run_program(stencil_plan_s *p, void *pair_p, void *pair_c, const stencil_coe
             if (e != cudaSuccess) return cuda_fail(e);
         } else if (adjoint) {
             // depth-2 adjoint pass: steps j = t+1 and t+2 (residual planes
-            // nsteps-j and nsteps-j-1); only level 2 is kept
+            // nsteps-j and nsteps-j-1); level 1 is kept where the program
+            // needs it (the second-order kinds)
             if (o.levels != 2 || !adj_pass_supported(p)) return STENCIL_EUNSUPPORTED;
             const int64_t j = t + 1;
-            cudaError_t e = adjoint_pair<T>(p, s, coeffs, buf[o.in_c], o.out_p >= 0 ? buf[o.out_p] : nullptr,
+            cudaError_t e = adjoint_pair<T>(p, s, coeffs, buf[o.in_p], buf[o.in_c], o.out_p >= 0 ? buf[o.out_p] : nullptr,
                                             buf[o.out_c], inject ? (const T *)inject + (nsteps - j) * plane : nullptr,
                                             rcv_z, st);
             if (e != cudaSuccess) return cuda_fail(e);
@@ -594,7 +605,7 @@ int run_adjoint_ring(stencil_plan_s *p, void *lam_next, void *lam, const stencil
         // writes lam^{m-j} and lam^{m-j-1} into their ring slots
         const int n = (pairs && j + 1 <= nsteps && ga.nsteps + 2 <= G) ? 2 : 1;
         if (n == 2)
-            e = adjoint_pair<T>(p, s, coeffs, level(j - 1), level(j), level(j + 1), inj, rcv_z, st);
+            e = adjoint_pair<T>(p, s, coeffs, level(j - 2), level(j - 1), level(j), level(j + 1), inj, rcv_z, st);
         else
             e = plain_step<T>(p, true, s, coeffs, level(j - 2), level(j - 1), level(j), nullptr, inj, rcv_z, st);
         if (e != cudaSuccess) return cuda_fail(e);

@@ -88,13 +88,24 @@ constexpr size_t smem_of(int kind) {
 }
 }  // namespace b25
 
-template <int KIND>
+// ADJ: the adjoint pass of the 13-array kinds (lam^t = g^t + A^T lam^{t+1}
+// [+ 2 lam^{t+1} - lam^{t+2} for the wave kind]; a.u = lam^{t+1}, a.u_prev =
+// lam^{t+2}): the transposed update gathers every term's coefficient at its
+// source point, (A^T y)(q) = sum_k A_k(q - o_k) y(q - o_k) -- for the x terms
+// three aligned vectors of the axis array around the point, for y and z
+// the vectors of the rows and planes +-d -- read from global memory at
+// use (L1 / L2 serve the overlap between neighbouring points).  The residual
+// plane of level k (a.inject + (k-1) a.inject_step) is added on plane
+// rcv_z at every computed interior point, the halo'd level-1 points
+// included.  Both levels are written (out_prev = level 1, out = level 2).
+template <int KIND, bool ADJ = false>
 __global__ void __launch_bounds__(b25::NT, 1)
 blk25_kernel(const BlockedArgs<float> a, const __grid_constant__ CUtensorMap tm_u,
              const __grid_constant__ CUtensorMap tm_p) {
     using namespace b25;
     constexpr bool WAVE = KindTraits<KIND>::WAVE;
     constexpr bool CW = KIND == W25_CONST;   // constant weights: no coefficient arrays
+    static_assert(!(ADJ && CW), "the constant wave is symmetric: its adjoint is the forward pass");
     constexpr int PD = pd_of(KIND), NS0 = ns0_of(KIND), NSP = nsp_of(KIND);
     extern __shared__ __align__(128) unsigned char smem_raw[];
     float *const s0 = reinterpret_cast<float *>((reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
@@ -239,6 +250,59 @@ blk25_kernel(const BlockedArgs<float> a, const __grid_constant__ CUtensorMap tm_
         return make_float4(a0.x, a0.y, a1.x, a1.y);
     };
 
+    // transposed update (ADJ) at a 4-point vector: tile row r, column c of
+    // the ring planes as in update; Wp = array 0 at the vector's first point
+    auto update_adj = [&](const float *buf, const uint32_t (&pl)[2 * R + 1], int W, int r, int c, const float *Wp,
+                          float4 prev) -> float4 {
+        auto ld = [](const float *p) { return __ldg(reinterpret_cast<const float4 *>(p)); };
+        auto el = [](const float4 &v, int i) { return i == 0 ? v.x : i == 1 ? v.y : i == 2 ? v.z : v.w; };
+        const int rc = r * W + c;
+        const float *C = buf + pl[R] + rc;
+        const float4 cv = *reinterpret_cast<const float4 *>(C);
+        const float4 lv = *reinterpret_cast<const float4 *>(C - V);
+        const float4 rv = *reinterpret_cast<const float4 *>(C + V);
+        const float4 w0 = ld(Wp);
+        float acc[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            acc[i] = el(w0, i) * el(cv, i);
+            if constexpr (WAVE) acc[i] = fma(2.0f, el(cv, i), acc[i]) - el(prev, i);
+        }
+#pragma unroll
+        for (int d = 1; d <= R; ++d) {
+            const float *wx = Wp + (3 * d - 2) * nf, *wy = Wp + (3 * d - 1) * nf, *wz = Wp + (3 * d) * nf;
+            const float4 xa = ld(wx - V), xb = ld(wx), xc = ld(wx + V);          // x axis array, columns c-4 .. c+7
+            const float4 ya = ld(wy - d * sy), yb = ld(wy + d * sy);            // rows -d, +d
+            const float4 za = ld(wz - d * sz), zb = ld(wz + d * sz);            // planes -d, +d
+            const float4 yu = *reinterpret_cast<const float4 *>(C - d * W);
+            const float4 yd = *reinterpret_cast<const float4 *>(C + d * W);
+            const float4 zd = *reinterpret_cast<const float4 *>(buf + pl[R - d] + rc);
+            const float4 zu = *reinterpret_cast<const float4 *>(buf + pl[R + d] + rc);
+#pragma unroll
+            for (int i = 0; i < 4; ++i) {
+                const float wl = i - d >= 0 ? el(xb, i - d) : el(xa, i - d + 4);
+                const float ll_ = i - d >= 0 ? el(cv, i - d) : el(lv, i - d + 4);
+                const float wr = i + d < 4 ? el(xb, i + d) : el(xc, i + d - 4);
+                const float rr_ = i + d < 4 ? el(cv, i + d) : el(rv, i + d - 4);
+                acc[i] = fma(wl, ll_, acc[i]);
+                acc[i] = fma(wr, rr_, acc[i]);
+                acc[i] = fma(el(ya, i), el(yu, i), acc[i]);
+                acc[i] = fma(el(yb, i), el(yd, i), acc[i]);
+                acc[i] = fma(el(za, i), el(zd, i), acc[i]);
+                acc[i] = fma(el(zb, i), el(zu, i), acc[i]);
+            }
+        }
+        return make_float4(acc[0], acc[1], acc[2], acc[3]);
+    };
+    (void)update_adj;
+    // residual of level k on the receiver plane (adjoint), 4 interior points
+    // of tile row py, column px (padded)
+    auto inject = [&](float4 &v, int k, int py, int px) {
+        const float *inj = a.inject + (k - 1) * a.inject_step + (int64_t)(py - R) * g.nx + (px - R);
+        v.x += inj[0]; v.y += inj[1]; v.z += inj[2]; v.w += inj[3];
+    };
+    (void)inject;
+
     // ring slots, advanced by one per step (no division in the loop):
     // s_in = level-0 slot of plane q, s_p = u^{t-1} slot of plane q,
     // s1c = level-1 slot of plane q - R
@@ -254,7 +318,7 @@ blk25_kernel(const BlockedArgs<float> a, const __grid_constant__ CUtensorMap tm_
         float4 cf[NPF];
         const int pc = lev1 ? q - R : q - 2 * R - 1;
         const float *const cfp = CW ? nullptr : a.W + ((int64_t)(pc + R) * sz + (lev1 ? g1 : g2));
-        if constexpr (!CW) {
+        if constexpr (!CW && !ADJ) {
             const bool on = lev1 ? (in1 && q >= qs + 2 * R && q < qe && (unsigned)pc < (unsigned)g.nz)
                                  : (in2 && q >= qs + 4 * R + 1);
 #pragma unroll
@@ -280,8 +344,14 @@ blk25_kernel(const BlockedArgs<float> a, const __grid_constant__ CUtensorMap tm_
                 float4 prev = make_float4(0.f, 0.f, 0.f, 0.f);
                 if constexpr (WAVE) prev = *reinterpret_cast<const float4 *>(sp + s_p * P1 + r1 * TX1 + c1);
                 float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-                if (in1 && (unsigned)pc1 < (unsigned)g.nz)
-                    v = update(s0, pl0, TX0, r1 + R, c1 + R, cf, cfp, prev);
+                if (in1 && (unsigned)pc1 < (unsigned)g.nz) {
+                    if constexpr (ADJ) {
+                        v = update_adj(s0, pl0, TX0, r1 + R, c1 + R, cfp, prev);
+                        if (a.inject && pc1 == a.rcv_z) inject(v, 1, py1, px1);
+                    } else {
+                        v = update(s0, pl0, TX0, r1 + R, c1 + R, cf, cfp, prev);
+                    }
+                }
                 *reinterpret_cast<float4 *>(s1 + s1c * P1 + r1 * TX1 + c1) = v;
                 if (own1 && (unsigned)pc1 - (unsigned)z0 < (unsigned)(z1 - z0)) {
                     const int64_t o = (int64_t)(pc1 + R) * sz + g1;
@@ -309,7 +379,13 @@ blk25_kernel(const BlockedArgs<float> a, const __grid_constant__ CUtensorMap tm_
                     sl += sl < 0 ? NS0 : 0;
                     prev = *reinterpret_cast<const float4 *>(s0 + sl * P0 + (r2 + 2 * R) * TX0 + c2 + 2 * R);
                 }
-                const float4 v = update(s1, pl1, TX1, r2 + R, c2 + R, cf, cfp, prev);
+                float4 v;
+                if constexpr (ADJ) {
+                    v = update_adj(s1, pl1, TX1, r2 + R, c2 + R, cfp, prev);
+                    if (a.inject && pc2 == a.rcv_z) inject(v, 2, py2, px2);
+                } else {
+                    v = update(s1, pl1, TX1, r2 + R, c2 + R, cf, cfp, prev);
+                }
                 const int64_t o = (int64_t)(pc2 + R) * sz + g2;
                 if (dbg_store_ok(a.dbg, g, o, V)) *reinterpret_cast<float4 *>(a.out + o) = v;
                 if (a.trace && pc2 == a.rcv_z) {
@@ -351,7 +427,8 @@ inline bool blk25_info(int kind, int64_t *info) {
     return true;
 }
 
-inline cudaError_t launch_blk25(int kind, const BlockedArgs<float> &a, cudaStream_t st, int num_sms) {
+inline cudaError_t launch_blk25(int kind, const BlockedArgs<float> &a, cudaStream_t st, int num_sms,
+                                bool adjoint = false) {
     using namespace b25;
     const bool wave = kind != J25_VAR;   // W25_VAR, W25_CONST: second order in time
     CUtensorMap tm_u, tm_p;
@@ -361,7 +438,10 @@ inline cudaError_t launch_blk25(int kind, const BlockedArgs<float> &a, cudaStrea
     if (e == cudaSuccess && wave) e = pv::make_tmap(&tm_p, a.u_prev, 4, a.g, TX1, TY1);
     if (e != cudaSuccess) return e;
     const size_t smem = smem_of(kind);
-    auto kern = kind == W25_VAR ? blk25_kernel<W25_VAR> : kind == W25_CONST ? blk25_kernel<W25_CONST> : blk25_kernel<J25_VAR>;
+    if (adjoint && kind == W25_CONST) return cudaErrorNotSupported;
+    auto kern = adjoint ? (kind == W25_VAR ? blk25_kernel<W25_VAR, true> : blk25_kernel<J25_VAR, true>)
+                        : (kind == W25_VAR ? blk25_kernel<W25_VAR> : kind == W25_CONST ? blk25_kernel<W25_CONST>
+                                                                                        : blk25_kernel<J25_VAR>);
     static_assert(smem_of(W25_VAR) <= 227 * 1024 && smem_of(W25_CONST) <= 227 * 1024, "shared memory per CTA");
     e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;

@@ -15,5 +15,8 @@ bool blk25_info_f32(int kind, int64_t *info) { return blk25_info(kind, info); }
 cudaError_t launch_blk25_f32(int kind, const BlockedArgs<float> &a, cudaStream_t st, int num_sms) {
     return launch_blk25(kind, a, st, num_sms);
 }
+cudaError_t launch_blk25_adj_f32(int kind, const BlockedArgs<float> &a, cudaStream_t st, int num_sms) {
+    return launch_blk25(kind, a, st, num_sms, true);
+}
 
 }  // namespace stc

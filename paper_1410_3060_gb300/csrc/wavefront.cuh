@@ -27,6 +27,10 @@ bool wavefront_info_f64(int kind, int levels, int tile, int64_t *info);
 // blk25_impl.cuh).
 bool blk25_supported_f32(int kind, int levels, const Geom &g);
 cudaError_t launch_blk25_f32(int kind, const BlockedArgs<float> &a, cudaStream_t st, int num_sms);
+// Its adjoint (W25_VAR, J25_VAR): lam^{t+1} in a.u, lam^{t+2} in a.u_prev
+// (wave kind), level 1 into a.out_prev, level 2 into a.out, residual planes
+// a.inject / a.inject + a.inject_step on plane a.rcv_z.
+cudaError_t launch_blk25_adj_f32(int kind, const BlockedArgs<float> &a, cudaStream_t st, int num_sms);
 bool blk25_info_f32(int kind, int64_t *info);
 
 }  // namespace stc

@@ -1,5 +1,6 @@
-"""Temporally blocked adjoint of the 7-point kinds (Sect. 4.1 wavefront
-applied to the transposed sweep, two levels per pass) against the FP64
+"""Temporally blocked adjoint (Sect. 4.1 wavefront applied to the
+transposed sweep, two levels per pass: the register wavefront for the
+7-point kinds, the two-level pass for the 13-array kinds) against the FP64
 oracle's adjoint: both levels, residual injection on every level, the
 coefficient gradient in batches that pair levels or not, ragged tiles in x,
 y and z; plus the adjoint identity of the blocked adjoint with the forward."""
@@ -138,16 +139,48 @@ def test_blocked_adjoint_dot_product(st, kind):
     plan.close()
 
 
+# the 13-array kinds in FP32 (the two-level pass's adjoint): nx a multiple of
+# 4, several 64 x 16 tiles with ragged edges, z chunks
+SHAPES25 = [(136, 45, 40), (64, 19, 30), (200, 33, 70)]
+
+
+@pytest.mark.parametrize("kind", [4, 5])
+@pytest.mark.parametrize("shape", SHAPES25)
+@pytest.mark.parametrize("T", [5, 8])
+def test_blocked_adjoint_25pt_matches_oracle(st, kind, shape, T):
+    """The two-level adjoint pass of the 13-array kinds (FP32), no gradient."""
+    (g2, g1, _), (o2, o1, _) = run_case(st, kind, F32, shape, T, None)
+    assert normwise_err(g1, o1) <= 2e-5
+    assert normwise_err(g2, o2) <= 2e-5
+
+
+@pytest.mark.parametrize("kind", [4, 5])
+@pytest.mark.parametrize("grad_batch", [1, 2, 3, 8])
+def test_blocked_adjoint_25pt_gradient(st, kind, grad_batch):
+    """With the FP64 coefficient gradient: levels paired inside gradient
+    batches, against the oracle."""
+    (g2, g1, gg), (o2, o1, og) = run_case(st, kind, F32, (136, 45, 40), 9, grad_batch)
+    assert normwise_err(g1, o1) <= 2e-5
+    assert normwise_err(g2, o2) <= 2e-5
+    assert normwise_err(gg, og) <= 2e-5
+
+
 def test_blocked_adjoint_option(st):
-    """Depth 2 is served for the 7-point kinds only; reading the option gives
-    the depth the adjoint runs."""
+    """Depth 2 is served for the 7-point kinds and, in FP32, the 13-array
+    kinds (default 1 for them); reading the option gives the depth the
+    adjoint runs."""
     p = st.Plan(wl.W25_VAR, 32, 16, 16, F32)
     assert p.get(st.OPT_ADJ_TIME_BLOCK) == 1
-    with pytest.raises(st.StencilError):
-        p.set(st.OPT_ADJ_TIME_BLOCK, 2)
+    p.set(st.OPT_ADJ_TIME_BLOCK, 2)
+    assert p.get(st.OPT_ADJ_TIME_BLOCK) == 2
     with pytest.raises(st.StencilError):
         p.set(st.OPT_ADJ_TIME_BLOCK, 3)
     p.close()
+    for kind, dtype in ((wl.W25_VAR, F64), (wl.W25_CONST, F32), (wl.W25_ALPHA, F32)):
+        p = st.Plan(kind, 32, 16, 16, dtype)
+        with pytest.raises(st.StencilError):
+            p.set(st.OPT_ADJ_TIME_BLOCK, 2)
+        p.close()
     # default: depth 2 in FP32, 1 in FP64
     p = st.Plan(wl.J7_VAR, 32, 16, 16, F32)
     assert p.get(st.OPT_ADJ_TIME_BLOCK) == 2
