@@ -61,8 +61,8 @@ def parse():
                    help="time only the forward+adjoint of the differentiable workload: the 25-point variable wave "
                         "(K = 20), or --kind j7_var (K = 16) (size --n, T --T)")
     p.add_argument("--adjoint", action="store_true",
-                   help="time only the adjoint sweep of a 7-point --kind (size --n, T --T, levels per pass "
-                        "--time-block, default: library choice)")
+                   help="time only the adjoint sweep of a 7-point or 13-array --kind (size --n, T --T, levels "
+                        "per pass --time-block, default: library choice)")
     p.add_argument("--no-variants", action="store_true")
     p.add_argument("--no-cpu", action="store_true")
     p.add_argument("--no-e2e", action="store_true")
@@ -609,7 +609,7 @@ def adjoint_bytes_per_lup(kind, elem, levels):
 
 
 def adjoint_case(torch, st, wl, kind, n, T, dtype, steps, warmup, ws, stream, adj_block=None, hbm_peak=None):
-    """The adjoint sweep of a 7-point kind: one step = T adjoint levels of the
+    """The adjoint sweep of a 7-point or 13-array kind: one step = T adjoint levels of the
     n^3 lattice with a residual plane injected at every level (no
     gradient), lam reset from a device copy before every step (outside the
     events).  GLUP/s = n^3 T / time."""
@@ -618,6 +618,7 @@ def adjoint_case(torch, st, wl, kind, n, T, dtype, steps, warmup, ws, stream, ad
     plan = st.Plan(kind, n, n, n, dtype)
     if adj_block is not None:
         plan.set(st.OPT_ADJ_TIME_BLOCK, adj_block)
+    r7 = kind in (wl.J7_CONST, wl.J7_VAR)
     W = torch.from_numpy(wk.W).to("cuda", tdt) if wk.W is not None else None
     lam0 = torch.from_numpy(wk.u).to("cuda", tdt)
     l2, l1 = torch.zeros_like(lam0), lam0.clone()
@@ -649,7 +650,7 @@ def adjoint_case(torch, st, wl, kind, n, T, dtype, steps, warmup, ws, stream, ad
     res_ = {"kind": wl.KIND_NAMES[kind] + "_adjoint", "n": n, "T": T, "dtype": "f64" if dtype == st.F64 else "f32",
             "adjoint_levels_per_pass": b, "ms_per_step": ms, "glups": lups * ws / (ms * 1e-3) / 1e9,
             "variant": plan.get(st.OPT_VARIANT)}
-    if hbm_peak:
+    if hbm_peak and r7:   # the 13-array kinds' passes are latency-bound: no byte roofline stated
         bpl = adjoint_bytes_per_lup(kind, 4 if dtype == st.F32 else 8, b)
         ach = res_["glups"] / ws * bpl
         res_["roofline"] = {"bound": "hbm", "bytes_per_lup": bpl, "achieved": ach, "peak": hbm_peak, "unit": "GB/s",
@@ -745,8 +746,8 @@ def run_ours(args):
         print(json.dumps({"fwd_adj": r}), flush=True)
         return
     if args.adjoint:
-        if kind not in (wl.J7_CONST, wl.J7_VAR):
-            raise SystemExit("--adjoint: a 7-point kind (j7_const, j7_var)")
+        if kind not in (wl.J7_CONST, wl.J7_VAR, wl.W25_VAR, wl.J25_VAR):
+            raise SystemExit("--adjoint: a 7-point kind or a 13-array kind (j7_const, j7_var, w25_var, j25_var)")
         r = adjoint_case(torch, st, wl, kind, n, T, dtype, args.steps, args.warmup, ws, stream,
                          adj_block=args.time_block, hbm_peak=hbm_peak)
         print(json.dumps({"adjoint": r}), flush=True)
