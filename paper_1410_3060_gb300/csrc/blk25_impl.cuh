@@ -13,11 +13,11 @@
 // (80 x 32).  The warps split by level: 14 warps update one level-1 vector
 // (4 points) each, 8 warps one owned level-2 vector each, and all meet at
 // one barrier per step.  The levels live in shared memory as plane rings:
-//   level 0   2R + 3 slots (the 2R + 1 planes level 1 reads, the plane
-//             level 2 takes as u^{t-1}, one plane in flight), each brought
-//             by one bulk tensor copy (zero fill outside the padded array),
-//             with u^{t-1} of level 1's plane beside it (2 slots) for the
-//             second-order kind;
+//   level 0   2R + 2 + PD slots (the 2R + 1 planes level 1 reads, the
+//             plane level 2 takes as u^{t-1}, PD planes in flight: 1, 2 for
+//             the constant wave), each brought by one bulk tensor copy (zero
+//             fill outside the padded array), with u^{t-1} of level 1's
+//             plane beside it (PD + 1 slots) for the second-order kinds;
 //   level 1   2R + 2 slots (the 2R + 1 planes level 2 reads and the one
 //             level 1 writes), written by the CTA.
 // Every neighbour, in x, y and z, is an aligned 16-byte shared load; the two
@@ -34,12 +34,14 @@
 // points; the receiver trace of both levels as well.
 //
 // The constant wave (W25_CONST) runs the same pass with its 5 folded
-// weights in registers and no coefficient arrays.
+// weights in registers and no coefficient arrays.  The adjoint of the
+// 13-array kinds runs it with the transposed update (see the kernel).
 //
 // Measured (512^3, FP32, T = 64): 81 GLUP/s for W25_VAR and 86 for J25_VAR,
 // against 103 and 112 for the one-level TMA sweep, so it is not the default;
 // W25_CONST (T = 100) 190-194 against 438: one 4-point vector per warp and
-// a barrier per step leave its short steps latency-bound.
+// a barrier per step leave its short steps latency-bound; the adjoint of
+// W25_VAR / J25_VAR 39 / 37 against 91 / 94 for the one-level adjoint.
 // Earlier forms: one 256-thread CTA doing both levels in turn with all 13
 // coefficient vectors prefetched (72 / 76 GLUP/s; 245 registers and 196 KB
 // of rings leave 8 warps per SM, 28% issue activity); the same split by
