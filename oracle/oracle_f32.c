@@ -13,7 +13,7 @@
  * sum rounded to float separately, no multiply-add contraction).  Its
  * difference from the FP64 oracle on the same (FP32-rounded) inputs is the
  * rounding error of an FP32 evaluation, the scale against which the tests
- * judge the error of the GPU's FP32 sweeps.
+ * measure the error of the GPU's FP32 sweeps.
  *
  * Kinds, layout and the time-state convention are those of oracle.c.  The
  * weights w are given in FP64 and rounded to float once.
