@@ -13,7 +13,8 @@ first; then the least redundant tile).  Families the model does not describe
 follow, in the model's byte order as well.  Each candidate is then timed on
 the caller's own data with CUDA events -- the measurement decides, as in the
 paper.  A candidate the library rejects is skipped.  The trial runs advance
-copies of the caller's state, never the caller's buffers.
+copies of the caller's state, never the caller's buffers.  tune_adjoint
+does the same for the levels per adjoint pass (1 or 2).
 """
 from __future__ import annotations
 
@@ -112,3 +113,46 @@ def tune_forward(plan: st.Plan, u_prev, u, w=None, W=None, T: int = 8, candidate
     plan.set(st.OPT_VARIANT, variant)
     del tp, tu
     return {"time_block": b, "scheme": scheme, "variant": variant, "ms": ms, "table": sorted(table)}
+
+
+def tune_adjoint(plan: st.Plan, lam_next, lam, w=None, W=None, T: int = 8, fwd_states=None, residual=None,
+                 rcv_z: int = 0, grad=None, reps: int = 2, stream=None):
+    """Time stencil_adjoint(T) with one and with two levels per pass (where
+    the plan serves two) on copies of (lam_next, lam) and, when a gradient
+    is asked for, into a scratch gradient (the caller's buffers are never
+    written); set the faster depth on the plan (STENCIL_OPT_ADJ_TIME_BLOCK)
+    and return {"adjoint_levels_per_pass", "ms", "table": [(ms, levels), ...]}.
+    The plan must be idle (options are changed between trials)."""
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    tn, tl = lam_next.clone(), lam.clone()
+    tg = torch.zeros_like(grad) if grad is not None else None
+    table = []
+    for b in (1, 2):
+        try:
+            plan.set(st.OPT_ADJ_TIME_BLOCK, b)
+        except st.StencilError:
+            continue                      # depth not served for this kind / dtype / geometry
+        if plan.get(st.OPT_ADJ_TIME_BLOCK) != b:
+            continue
+
+        def run():
+            tn.copy_(lam_next)
+            tl.copy_(lam)
+            plan.adjoint(tn, tl, w, W, T, fwd_states=fwd_states, residual=residual, rcv_z=rcv_z, grad=tg,
+                         stream=s)
+
+        run()                             # warm-up (and first-use setup)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(s)
+        for _ in range(reps):
+            run()
+        e1.record(s)
+        e1.synchronize()
+        table.append((e0.elapsed_time(e1) / reps, b))
+    if not table:
+        raise RuntimeError("no adjoint depth ran")
+    ms, b = min(table)
+    plan.set(st.OPT_ADJ_TIME_BLOCK, b)
+    del tn, tl, tg
+    return {"adjoint_levels_per_pass": b, "ms": ms, "table": sorted(table)}

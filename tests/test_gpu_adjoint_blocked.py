@@ -197,3 +197,48 @@ def test_blocked_adjoint_option(st):
     with pytest.raises(st.StencilError):
         p.set(st.OPT_ADJ_TIME_BLOCK, 2)
     p.close()
+
+
+@pytest.mark.parametrize("kind,dtype,shape", [(2, F32, (66, 40, 30)), (2, F64, (66, 40, 30)),
+                                              (4, F32, (64, 19, 30))])
+def test_tune_adjoint_picks_a_depth_and_leaves_inputs(st, kind, dtype, shape):
+    """tune.tune_adjoint times the served depths on copies: the caller's
+    pair and gradient are untouched, the plan runs the chosen depth, and the
+    adjoint it then computes matches the oracle."""
+    import torch
+    from paper_1410_3060_gb300 import tune
+    rng = np.random.default_rng(90 + kind)
+    T = 6
+    wk = wl.make(kind, shape, T, seed=3)
+    R = wk.R
+    l2, l1 = rand_interior(shape, R, rng), rand_interior(shape, R, rng)
+    states = np.stack([rand_interior(shape, R, rng) for _ in range(T)])
+    res = rng.uniform(-1, 1, size=(T, shape[1], shape[0]))
+    rz = shape[2] // 2
+    k = oracle.NUM_ARRAYS[kind]
+    cast = (lambda a: a.astype(np.float32).astype(np.float64)) if dtype == F32 else (lambda a: a)
+    og = np.zeros((k,) + l1.shape)
+    ol2, ol1 = oracle.adjoint(kind, cast(l2), cast(l1), wk.w, cast(wk.W), T, states=cast(states),
+                              residual=cast(res), rcv_z=rz, grad=og, threads=8)
+    plan = st.Plan(kind, *shape, dtype)
+    plan.set(st.OPT_GRAD_BATCH, 4)
+    gl2, gl1 = to_dev(l2, dtype), to_dev(l1, dtype)
+    W = to_dev(wk.W, dtype)
+    gs = [to_dev(s_, dtype) for s_ in states]
+    gres = to_dev(res, dtype)
+    gg = torch.zeros((k,) + l1.shape, device="cuda", dtype=torch.float64)
+    out = tune.tune_adjoint(plan, gl2, gl1, wk.w, W, T, fwd_states=gs, residual=gres, rcv_z=rz, grad=gg)
+    torch.cuda.synchronize()
+    assert out["adjoint_levels_per_pass"] in (1, 2)
+    assert plan.get(st.OPT_ADJ_TIME_BLOCK) == out["adjoint_levels_per_pass"]
+    assert len(out["table"]) == (2 if (dtype == F32 or kind == 2) else 1)
+    np.testing.assert_array_equal(to_np(gl1), cast(l1))
+    np.testing.assert_array_equal(to_np(gl2), cast(l2))
+    assert not to_np(gg).any()
+    plan.adjoint(gl2, gl1, wk.w, W, T, fwd_states=gs, residual=gres, rcv_z=rz, grad=gg)
+    torch.cuda.synchronize()
+    tol = 1e-12 if dtype == F64 else 2e-5
+    assert normwise_err(to_np(gl1), ol1) <= tol
+    assert normwise_err(to_np(gl2), ol2) <= tol
+    assert normwise_err(to_np(gg), og) <= tol
+    plan.close()
