@@ -310,6 +310,22 @@ int stencil_misfit_static(int dtype, const void *trace, const void *d, int64_t n
  * ops and the total count to *n_ops.  Performs no CUDA call. */
 int stencil_schedule(int kind, int dtype, int64_t T, int b, int32_t *ops, int64_t max_ops, int64_t *n_ops);
 
+/* The host program stencil_adjoint runs for T steps with a gradient in
+ * batches of grad_batch steps (1..16, STENCIL_OPT_GRAD_BATCH >= 2) and
+ * `levels` (1 or 2) levels per pass where the plan allows them (the
+ * adjoint form of the time-loop driver, Sect. 3.1 recursion run backward):
+ * ops receives up to max_ops triples (op, a, b) in issue order, *n_ops the
+ * total count --
+ *   (0, b, 0)  the caller's stream waits for gradient batch b - 2 before
+ *              batch b's first sweep (the sweeps of batch b overwrite the
+ *              ring slots that batch reads);
+ *   (1, j, n)  the sweep of steps j .. j+n-1 (n = 1 or 2; step j produces
+ *              lam^{m-j} into ring slot (j-1) mod (2 grad_batch + 2));
+ *   (2, b, k)  gradient batch b of k steps on the plan's gradient stream.
+ * Host-only (no CUDA call); EINVAL for a bad argument. */
+int stencil_adjoint_schedule(int64_t T, int grad_batch, int levels, int64_t *ops, int64_t max_ops,
+                             int64_t *n_ops);
+
 /* Debug builds (compiled with -DSTENCIL_DEBUG) check every store of a
  * sweep's result: a store whose target is not an interior point of the
  * padded array (a sweep never writes the halo or outside the array) is

@@ -561,6 +561,40 @@ int run_forward_states(stencil_plan_s *p, const void *u_prev, const void *u, con
 // sweeps write the next G (G + 1 + G slots, plus one so that batch b+1's
 // first sweep still sees both inputs), and the first sweep of batch b+2
 // waits for batch b's gradient (ev_grad[b % 2]) before it overwrites them.
+// The host program of the adjoint with gradient batches of G steps: ops in
+// issue order,
+//   {ADJ_WAIT, b, 0}  the caller's stream waits for gradient batch b - 2
+//                     (event ev_grad[b % 2]) before batch b's first sweep;
+//   {ADJ_SWEEP, j, n} the sweep of steps j .. j+n-1 (n = 1, or 2 when pairs
+//                     are allowed and both steps fall into the batch),
+//                     writing lam^{m-j} .. into ring slots (j-1) mod (2G+2);
+//   {ADJ_GRAD, b, k}  gradient batch b over its k steps (ending at the
+//                     last sweep), on the gradient stream.
+// Host logic only (no CUDA call): stencil_adjoint_schedule exposes it.
+enum { ADJ_WAIT = 0, ADJ_SWEEP = 1, ADJ_GRAD = 2 };
+struct AdjOp {
+    int op;
+    int64_t a, b;
+};
+std::vector<AdjOp> adjoint_ring_program(int64_t nsteps, int G, bool pairs) {
+    std::vector<AdjOp> ops;
+    int64_t batch = 0, in_batch = 0;
+    for (int64_t j = 1; j <= nsteps;) {
+        // the first sweep of batch b >= 2 overwrites the levels batch b-2's gradient reads
+        if (in_batch == 0 && batch >= 2) ops.push_back({ADJ_WAIT, batch, 0});
+        const int n = (pairs && j + 1 <= nsteps && in_batch + 2 <= G) ? 2 : 1;
+        ops.push_back({ADJ_SWEEP, j, n});
+        in_batch += n;
+        j += n;
+        if (in_batch == G || j > nsteps) {
+            ops.push_back({ADJ_GRAD, batch, in_batch});
+            ++batch;
+            in_batch = 0;
+        }
+    }
+    return ops;
+}
+
 template <typename T>
 int run_adjoint_ring(stencil_plan_s *p, void *lam_next, void *lam, const stencil_coeffs_t *coeffs, int64_t nsteps,
                      cudaStream_t st, const void *inject, int64_t rcv_z, const void *const *fwd_states,
@@ -593,39 +627,34 @@ int run_adjoint_ring(stencil_plan_s *p, void *lam_next, void *lam, const stencil
         for (int r = 0; r <= 4; ++r) ga.s.c[r] = coeffs->w[r];
     ga.g = p->g;
     int64_t batch = 0;   // batches launched
-    const bool pairs = effective_adj_block(p) == 2;
-    for (int64_t j = 1; j <= nsteps;) {
-        // first sweep of batch b >= 2 overwrites the levels batch b-2's gradient reads
-        if (ga.nsteps == 0 && batch >= 2) {
-            e = cudaStreamWaitEvent(st, p->ev_grad[batch % 2], 0);
-            if (e != cudaSuccess) return cuda_fail(e);
-        }
-        const T *inj = inject ? (const T *)inject + (nsteps - j) * plane : nullptr;
-        // depth-2 pass of steps j, j+1 when both fall into this batch: it
-        // writes lam^{m-j} and lam^{m-j-1} into their ring slots
-        const int n = (pairs && j + 1 <= nsteps && ga.nsteps + 2 <= G) ? 2 : 1;
-        if (n == 2)
-            e = adjoint_pair<T>(p, s, coeffs, level(j - 2), level(j - 1), level(j), level(j + 1), inj, rcv_z, st);
-        else
-            e = plain_step<T>(p, true, s, coeffs, level(j - 2), level(j - 1), level(j), nullptr, inj, rcv_z, st);
-        if (e != cudaSuccess) return cuda_fail(e);
-        for (int i = 0; i < n; ++i) {
-            ga.u[ga.nsteps] = (const T *)fwd_states[nsteps - j - i];
-            ga.lam[ga.nsteps] = (const T *)level(j - 1 + i);
-            ++ga.nsteps;
-        }
-        j += n;
-        if (ga.nsteps == G || j > nsteps) {
+    for (const AdjOp &o : adjoint_ring_program(nsteps, G, effective_adj_block(p) == 2)) {
+        if (o.op == ADJ_WAIT) {
+            e = cudaStreamWaitEvent(st, p->ev_grad[o.a % 2], 0);
+        } else if (o.op == ADJ_SWEEP) {
+            const int64_t j = o.a;
+            const T *inj = inject ? (const T *)inject + (nsteps - j) * plane : nullptr;
+            // a depth-2 pass of steps j, j+1 writes lam^{m-j} and lam^{m-j-1}
+            // into their ring slots
+            if (o.b == 2)
+                e = adjoint_pair<T>(p, s, coeffs, level(j - 2), level(j - 1), level(j), level(j + 1), inj, rcv_z, st);
+            else
+                e = plain_step<T>(p, true, s, coeffs, level(j - 2), level(j - 1), level(j), nullptr, inj, rcv_z, st);
+            for (int64_t i = 0; i < o.b; ++i) {
+                ga.u[ga.nsteps] = (const T *)fwd_states[nsteps - j - i];
+                ga.lam[ga.nsteps] = (const T *)level(j - 1 + i);
+                ++ga.nsteps;
+            }
+        } else {
             // the gradient stream starts this batch once its sweeps (and all
             // earlier work of the caller's stream) are done
             e = cudaEventRecord(p->ev_sweeps, st);
             if (e == cudaSuccess) e = cudaStreamWaitEvent(p->grad_stream, p->ev_sweeps, 0);
             if (e == cudaSuccess) e = launch_grad<T>(p->kind, ga, p->grad_stream);
-            if (e == cudaSuccess) e = cudaEventRecord(p->ev_grad[batch % 2], p->grad_stream);
-            if (e != cudaSuccess) return cuda_fail(e);
-            ++batch;
+            if (e == cudaSuccess) e = cudaEventRecord(p->ev_grad[o.a % 2], p->grad_stream);
+            batch = o.a + 1;
             ga.nsteps = 0;
         }
+        if (e != cudaSuccess) return cuda_fail(e);
     }
     // the caller's stream continues after every gradient batch
     if (batch > 0) {
@@ -1030,6 +1059,22 @@ int stencil_schedule(int kind, int dtype, int64_t T, int b, int32_t *ops, int64_
         const Op &o = prog[(size_t)i];
         const int32_t v[6] = {o.op, o.levels, o.in_p, o.in_c, o.out_p, o.out_c};
         memcpy(ops + 6 * i, v, sizeof(v));
+    }
+    return STENCIL_OK;
+}
+
+int stencil_adjoint_schedule(int64_t T, int grad_batch, int levels, int64_t *ops, int64_t max_ops,
+                             int64_t *n_ops) {
+    if (T < 0 || grad_batch < 1 || grad_batch > GRAD_MAX_STEPS || levels < 1 || levels > 2 || !n_ops ||
+        (max_ops > 0 && !ops))
+        return STENCIL_EINVAL;
+    const std::vector<AdjOp> prog = adjoint_ring_program(T, grad_batch, levels == 2);
+    *n_ops = (int64_t)prog.size();
+    for (int64_t i = 0; i < (int64_t)prog.size() && i < max_ops; ++i) {
+        const AdjOp &o = prog[(size_t)i];
+        ops[3 * i] = o.op;
+        ops[3 * i + 1] = o.a;
+        ops[3 * i + 2] = o.b;
     }
     return STENCIL_OK;
 }

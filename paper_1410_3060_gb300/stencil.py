@@ -31,7 +31,7 @@ EXPORTED = ("stencil_plan", "stencil_plan_set", "stencil_plan_get", "stencil_pla
             "stencil_forward", "stencil_forward_states", "stencil_adjoint", "stencil_axpby",
             "stencil_misfit", "stencil_misfit_static", "stencil_fill_zero", "stencil_schedule", "stencil_fma_peak",
             "stencil_strerror", "stencil_last_cuda_error", "stencil_wait_timeouts", "stencil_check",
-            "stencil_pass_info", "stencil_debug_bad_store")
+            "stencil_pass_info", "stencil_debug_bad_store", "stencil_adjoint_schedule")
 MISFIT_STATIC_MAX_ELEMS = 8192 * 2048
 
 _lock = threading.Lock()
@@ -91,6 +91,7 @@ def lib():
             L.stencil_wait_timeouts.argtypes = [ctypes.POINTER(i64)]
             L.stencil_check.argtypes = [vp, vp]
             L.stencil_pass_info.argtypes = [i32, i32, i32, i32, i32, ctypes.POINTER(i64)]
+            L.stencil_adjoint_schedule.argtypes = [i64, i32, i32, ctypes.POINTER(i64), i64, ctypes.POINTER(i64)]
             L.stencil_debug_bad_store.argtypes = [vp, ctypes.POINTER(i64)]
             for fn in ("stencil_plan", "stencil_plan_set", "stencil_plan_get", "stencil_forward",
                        "stencil_forward_states", "stencil_adjoint", "stencil_axpby", "stencil_misfit",
@@ -125,6 +126,20 @@ def schedule(kind: int, T: int, b: int, dtype: int = F32):
     buf = (ctypes.c_int32 * (6 * max(1, n.value)))()
     _check("stencil_schedule", lib().stencil_schedule(kind, dtype, T, b, buf, n.value, ctypes.byref(n)))
     return [tuple(buf[6 * i:6 * i + 6]) for i in range(n.value)]
+
+
+def adjoint_schedule(T: int, grad_batch: int, levels: int = 1):
+    """The host program stencil_adjoint runs with a gradient in batches of
+    grad_batch steps and `levels` levels per pass (host-only query): a list
+    of (op, a, b) -- (0, b, 0) wait for gradient batch b - 2, (1, j, n) the
+    sweep of steps j .. j+n-1, (2, b, k) gradient batch b of k steps."""
+    n = ctypes.c_int64(0)
+    _check("stencil_adjoint_schedule", lib().stencil_adjoint_schedule(T, grad_batch, levels, None, 0,
+                                                                      ctypes.byref(n)))
+    buf = (ctypes.c_int64 * (3 * max(1, n.value)))()
+    _check("stencil_adjoint_schedule", lib().stencil_adjoint_schedule(T, grad_batch, levels, buf, n.value,
+                                                                      ctypes.byref(n)))
+    return [tuple(buf[3 * i:3 * i + 3]) for i in range(n.value)]
 
 
 def misfit_static(trace, d, residual, loss, stream=None):

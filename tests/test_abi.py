@@ -149,3 +149,60 @@ def test_binding_status_constants_match_header(st):
     hdr = _header_enum("STENCIL_")
     for name in ("OK", "EINVAL", "EUNSUPPORTED", "ENOMEM", "ECUDA", "ETIMEOUT"):
         assert getattr(st, name) == hdr[name], name
+
+
+@pytest.mark.parametrize("levels", [1, 2])
+@pytest.mark.parametrize("G", [1, 2, 3, 4, 7, 8, 16])
+def test_adjoint_schedule_covers_steps_and_keeps_the_ring_safe(st, levels, G):
+    """The adjoint's host program with gradient batches (stencil_adjoint_schedule),
+    checked by simulating its two streams: every step is swept once, in
+    order; a two-level sweep (levels = 2) never straddles a gradient batch
+    and is used wherever two steps fit; each batch holds at most G steps and
+    is waited for before the sweeps of the batch two later start; no sweep
+    overwrites a ring slot that a gradient batch not yet waited for reads,
+    and every sweep still finds its inputs (the two previous levels) in
+    their slots."""
+    NSL = 2 * G + 2
+    for T in range(0, 41):
+        ops = st.adjoint_schedule(T, G, levels)
+        slot_level = {}          # ring slot -> level it holds
+        done_upto = -1           # gradient batches known complete on the sweep stream
+        issued = []              # gradient batches issued: (batch, levels read)
+        pending = []             # steps swept since the last gradient batch
+        next_step, next_batch = 1, 0
+        for op, a, b in ops:
+            if op == 0:          # wait for batch a - 2
+                assert a >= 2 and a == next_batch and not pending
+                done_upto = max(done_upto, a - 2)
+            elif op == 1:        # sweep of steps a .. a+b-1
+                assert a == next_step and b in ((1, 2) if levels == 2 else (1,))
+                if levels == 2 and G >= 2 and len(pending) + 2 <= G and a + 1 <= T:
+                    assert b == 2, "a pair fits"
+                assert len(pending) + b <= G, "a sweep straddles a gradient batch"
+                if len(pending) == 0 and next_batch >= 2:
+                    assert done_upto >= next_batch - 2, "batch two back not waited for"
+                for j in range(a, a + b):
+                    for src in (j - 2, j - 1):          # inputs: levels in the ring or the caller's pair
+                        if src >= 1:
+                            assert slot_level.get((src - 1) % NSL) == src, "input overwritten"
+                    slot = (j - 1) % NSL
+                    for bb, reads in issued:
+                        if bb > done_upto:
+                            assert slot not in {(L - 1) % NSL for L in reads if L >= 1}, \
+                                f"T={T}: step {j} overwrites a slot batch {bb} may still read"
+                    slot_level[slot] = j
+                    pending.append(j)
+                next_step = a + b
+            else:                # gradient batch a of b steps: reads level j-1 of each step j
+                assert a == next_batch and b == len(pending) and 1 <= b <= G
+                issued.append((a, [j - 1 for j in pending]))
+                pending = []
+                next_batch += 1
+        assert next_step == T + 1 and not pending
+        assert sum(k for op, _, k in ops if op == 2) == T
+
+
+def test_adjoint_schedule_rejects_bad_arguments(st):
+    for args in ((-1, 4, 1), (8, 0, 1), (8, 17, 1), (8, 4, 3)):
+        with pytest.raises(st.StencilError):
+            st.adjoint_schedule(*args)
