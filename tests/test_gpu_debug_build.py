@@ -1,6 +1,7 @@
 """Sweeps of every kernel family through the debug build (-DSTENCIL_DEBUG,
-record-and-skip store checks): no store leaves the interior of the padded
-array, and the results still match the oracle.  Runs in a child process
+record-and-skip store checks), the two-level adjoint passes included: no
+store leaves the interior of the padded array, and the forward results
+still match the oracle.  Runs in a child process
 that loads the debug library (STENCIL_LIBRARY)."""
 import os
 import subprocess
@@ -25,6 +26,8 @@ for kind in (3, 4, 5, 6):
     for variant in (1, 13, 15, 16):
         cases.append((kind, st.F32, 1, 0, variant, (64, 21, 19)))
     cases.append((kind, st.F32, 2, 2, 0, (64, 21, 19)))
+for kind in (3, 4, 5):   # the two-level pass (scheme 4)
+    cases.append((kind, st.F32, 2, 4, 0, (64, 21, 19)))
 T = 5
 for kind, dtype, b, scheme, variant, shape in cases:
     wk = wl.make(kind, shape, T, seed=2)
@@ -52,6 +55,21 @@ for kind, dtype, b, scheme, variant, shape in cases:
         plan.adjoint(lam_next, lam, wk.w, W, 2, fwd_states=states, grad=grad)
         plan.check()
         assert plan.debug_bad_store() == -1, ("adjoint", kind, variant)
+    if dtype == st.F32 and ((kind in (1, 2) and (b, scheme) == (2, 3)) or (kind in (4, 5) and scheme == 4)):
+        # adjoint passes of two levels (gradient batches of 2 steps for the
+        # variable kinds): the register wavefront's and the two-level pass's
+        plan.set(st.OPT_ADJ_TIME_BLOCK, 2)
+        assert plan.get(st.OPT_ADJ_TIME_BLOCK) == 2
+        lam = to_dev(wk.u, dtype)
+        lam_next = torch.zeros_like(lam)
+        grad = states = None
+        if st.NUM_ARRAYS[kind]:
+            plan.set(st.OPT_GRAD_BATCH, 2)
+            grad = torch.zeros((st.NUM_ARRAYS[kind],) + plan.padded_shape, device="cuda", dtype=torch.float64)
+            states = [to_dev(wk.u, dtype) for _ in range(4)]
+        plan.adjoint(lam_next, lam, wk.w, W, 4, fwd_states=states, grad=grad)
+        plan.check()
+        assert plan.debug_bad_store() == -1, ("blocked adjoint", kind, scheme)
     plan.close()
 print("debug build ok", len(cases))
 '''
