@@ -142,3 +142,19 @@ def test_tuner_candidates_follow_the_model():
     assert not any(v >= 17 for _, _, v, _ in tune.model_candidates(1, 0))
     c25 = tune.model_candidates(4, 1)
     assert {v for _, _, v, _ in c25 if v >= 13} == {13, 14, 15, 16}
+
+
+def test_two_level_candidates():
+    """The two-level pass (scheme 4, depth 2) is a candidate for the FP32
+    13-array kinds and the constant wave, modelled at half the plain bytes
+    per update, and for no FP64 plan or other kind."""
+    from paper_1410_3060_gb300 import tune
+    for kind in (3, 4, 5):
+        c = [x for x in tune.model_candidates(kind, 1) if x[1] == 4]
+        assert [(b, v) for b, _, v, _ in c] == [(2, 0)]
+        assert c[0][3]["dram_bytes_per_lup"] == pm.dram_bytes_per_lup(kind, 4, 2)
+        assert not any(x[1] == 4 for x in tune.model_candidates(kind, 0))
+    for kind in (1, 2, 6):
+        assert not any(x[1] == 4 for x in tune.model_candidates(kind, 1))
+    # the constant wave keeps two planes in flight: its rings are larger
+    assert pm.two_level_block(3)["smem_bytes"] > pm.two_level_block(4)["smem_bytes"]
